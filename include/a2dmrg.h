@@ -1,0 +1,183 @@
+/* a2dmrg.h -- C ABI of the GB300 (sm_103a) two-site A2DMRG library.
+ *
+ * The library computes the lowest eigenpair of a symmetric operator A given as
+ * a matrix product operator (eq. MPO, App. A) over tensor trains (Def. TT
+ * parameter space, Sec. 2.1), by the additive two-level DMRG iteration
+ * (Alg. 2) with the coarse-space correction of Sec. 3.1.
+ *
+ * Conventions (all functions):
+ *  - Every function returns a2_status: A2_OK (0) or a negative error code; no
+ *    exception crosses the ABI.  a2_last_error() returns the message of the
+ *    last failure on a context (valid until the next call on that context).
+ *  - Handles (a2_ctx, a2_tt, a2_mpo) are opaque and owned by the library;
+ *    create/destroy them with the functions below.  A context is used by one
+ *    host thread at a time; all its work is ordered on its CUDA stream.
+ *  - "host" pointers are read or written synchronously and may be freed after
+ *    the call returns.  "device" pointers are CUDA device addresses on the
+ *    context's device; the call enqueues work on the context stream and the
+ *    caller must keep the buffers alive until that stream has completed the
+ *    work (a2_ctx_synchronize).
+ *  - Arrays are row-major.  TT core j: [D_{j}][n_j][D_{j+1}] float64 with
+ *    D_0 = D_L = 1.  MPO core j: [R_j][n_j][n_j][R_{j+1}] float64, index order
+ *    (left bond, bra/output s, ket/input t, right bond), R_0 = R_L = 1.
+ *    Environments: [bra bond][MPO bond][ket bond] (eqs. env_L / env_R).
+ *  - On error the TT handed to a sweep is left unchanged (the iterate of
+ *    Alg. 2 is kept until the global iteration succeeds).
+ */
+#ifndef A2DMRG_H
+#define A2DMRG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  A2_OK = 0,
+  A2_EINVAL = -1,       /* invalid argument (sizes, null pointers, mismatched dims) */
+  A2_ENOMEM = -2,       /* device allocation failed */
+  A2_ECUDA = -3,        /* CUDA runtime / cuSOLVER error */
+  A2_ENOCONV = -4,      /* an iterative solve did not reach its tolerance */
+  A2_ENUMERIC = -5,     /* non-finite value detected */
+  A2_ETIMEOUT = -6,     /* a bounded device-side wait gave up */
+  A2_EUNSUPPORTED = -7  /* option not supported by this build */
+} a2_status;
+
+typedef enum {
+  A2_FP64 = 0, /* every contraction in FP64 */
+  A2_BF16 = 1, /* Lanczos matvecs on tcgen05 tensor cores (BF16 in, FP32 accumulate);
+                  environments, coarse matrices and Ritz refinement in FP32,
+                  vectors / SVD / coarse eigensolve in FP64 */
+  A2_TF32 = 2, /* reserved */
+  A2_FP32 = 3  /* every contraction in FP32 (SIMT), vectors / SVD / coarse in FP64 */
+} a2_precision;
+
+typedef struct a2_ctx a2_ctx;
+typedef struct a2_tt a2_tt;
+typedef struct a2_mpo a2_mpo;
+
+/* Context on CUDA device `device`.  cuda_stream: a cudaStream_t to run on, or
+ * NULL to create a private non-blocking stream. */
+a2_status a2_ctx_create(int device, void* cuda_stream, a2_ctx** out);
+a2_status a2_ctx_destroy(a2_ctx* ctx);
+const char* a2_last_error(const a2_ctx* ctx);
+a2_status a2_ctx_synchronize(a2_ctx* ctx);
+
+/* ---- tensor trains (Def. TT parameter space; Def. orthogonal TT) ---------- */
+
+/* New TT with L sites, physical dims phys[L] and bond dims bonds[L-1] (each
+ * clipped to the exact maximal rank min(prod n_<=k, prod n_>k)).  Cores are
+ * filled with SplitMix64 uniforms on [-1,1) (53-bit mantissa, site by site in
+ * row-major order, one stream from `seed`); then the TT is left-orthogonalised
+ * (QR, diag(R) >= 0) and normalised to norm 1. */
+a2_status a2_tt_create(a2_ctx* ctx, int L, const int* phys, const int* bonds, uint64_t seed,
+                       a2_tt** out);
+/* Copy a host core into site `site`; its bond dims must match the neighbours'
+ * after all cores are set (checked when the TT is used). */
+a2_status a2_tt_set_core(a2_tt* tt, int site, int Dl, int n, int Dr, const double* host_core);
+/* Query dims (host_out NULL) or copy core `site` to host. */
+a2_status a2_tt_get_core(const a2_tt* tt, int site, int* Dl, int* n, int* Dr, double* host_out);
+/* QR sweep left to right (diag(R) >= 0), then scale to norm 1; *norm_out
+ * (host, may be NULL) receives the norm before scaling. */
+a2_status a2_tt_left_orthogonalize(a2_tt* tt, double* norm_out);
+a2_status a2_tt_destroy(a2_tt* tt);
+
+/* ---- matrix product operator (eq. MPO) ------------------------------------ */
+
+/* Load L cores (host pointers) with MPO bond dims mpo_bonds[L+1] (first and
+ * last are 1).  The dense cores are scanned once into sparse row lists for
+ * the left-to-right and right-to-left actions (exact zeros are skipped). */
+a2_status a2_mpo_load(a2_ctx* ctx, int L, const int* phys, const int* mpo_bonds,
+                      const double* const* cores, a2_mpo** out);
+/* Number of nonzeros of core `site` (for flop accounting). */
+a2_status a2_mpo_nnz(const a2_mpo* mpo, int site, long long* nnz_out);
+a2_status a2_mpo_destroy(a2_mpo* mpo);
+
+/* ---- one global iteration -------------------------------------------------- */
+
+typedef struct {
+  int P;                       /* number of groups of bonds (subdomains), 1..L-1 */
+  const int* bond_partition;   /* P group sizes summing to L-1 (host), or NULL = even split */
+  int D_max;                   /* rank cap of the truncated SVD steps and the compression */
+  double svd_tol;              /* keep smallest r with discarded 2-norm <= svd_tol*||sigma|| */
+  double eig_tol;              /* Lanczos: ||H x - theta x|| <= eig_tol*max(1,|theta|) */
+  double coarse_eps;           /* drop S_hat eigenvalues <= coarse_eps * max (Sec. 3.1) */
+  int max_krylov;              /* Krylov basis size before a restart (<= 64) */
+  int max_restarts;            /* restart cycles per local solve */
+  a2_precision prec;
+  int refine_f64;              /* mixed precision: refinement steps of each Ritz pair */
+} a2_sweep_opts;
+
+typedef struct {
+  double energy_in;            /* Rayleigh quotient of the input iterate (A_hat_00/S_hat_00) */
+  double lambda_coarse;        /* lowest eigenvalue of the coarse problem */
+  double* energy_local;        /* [P] caller-owned or NULL: last Ritz value of each group */
+  double* coeffs;              /* [P+1] caller-owned or NULL: coarse coefficients c */
+  double* S_hat;               /* [(P+1)^2] caller-owned or NULL */
+  double* A_hat;               /* [(P+1)^2] caller-owned or NULL */
+  int coarse_rank;             /* p, numerical rank of S_hat */
+  int* krylov_iters;           /* [L-1] caller-owned or NULL: matvecs per bond */
+  double max_discarded_weight; /* largest discarded 2-norm over the SVD steps */
+  double seconds;              /* wall time of the call */
+  double alg_flops;            /* algorithmic flops of the contractions performed */
+  long long matvecs;           /* H_eff applications in the call */
+} a2_sweep_report;
+
+/* One global iteration of two-site A2DMRG (Alg. 2, with P groups of adjoining
+ * bonds swept as in Alg. 1 inside each group).  In: left-orthogonal TT of
+ * norm 1 (U^(n),d).  Out (in place): the compressed left-orthogonal TT of
+ * norm 1 (U^(n+1),d).  report may be NULL. */
+a2_status a2_additive_sweep(a2_ctx* ctx, a2_tt* tt, const a2_mpo* mpo, const a2_sweep_opts* opts,
+                            a2_sweep_report* report);
+
+/* One left-to-right half-sweep of classical two-site DMRG (Alg. 1 step 1-2 for
+ * i = 1..d-1) on the same kernels, preceded by the right-to-left LQ sweep that
+ * supplies the right-orthogonal input.  Output: left-orthogonal TT, norm 1. */
+a2_status a2_classical_sweep(a2_ctx* ctx, a2_tt* tt, const a2_mpo* mpo,
+                             const a2_sweep_opts* opts, a2_sweep_report* report);
+
+/* Coarse problem of Sec. 3.1 alone (eq. aux_eig_final_sym) on the device:
+ * host A_hat, S_hat (m x m symmetric, m <= 63), eps; outputs (host) c[m]
+ * with c^T S c = 1 and c_0 >= 0, lambda, and the kept rank p. */
+a2_status a2_coarse_solve(a2_ctx* ctx, int m, const double* A_hat, const double* S_hat,
+                          double eps, double* c_out, double* lambda_out, int* rank_out);
+
+/* Rayleigh quotient E = <x, A x>/<x, x> (eq. energy_eig) of the TT, contracted
+ * with precision prec; norm_out = ||x|| (both host, norm_out may be NULL). */
+a2_status a2_energy(a2_ctx* ctx, const a2_tt* tt, const a2_mpo* mpo, a2_precision prec,
+                    double* E_out, double* norm_out);
+
+/* ---- kernel-level entry points (device pointers, FP64 in/out) ------------- */
+
+/* y = H_eff x for the two-site problem at bond k (sites k, k+1), the
+ * contraction of App. A with the two-site modification:
+ *   y[a,s1,s2,b] = sum L[a,w,a'] A_k[w,s1,t1,w1] A_k+1[w1,s2,t2,w2] R[b,w2,b'] x[a',t1,t2,b']
+ * L: [Dl][R_k][Dl], R: [Dr][R_{k+2}][Dr], x, y: [Dl][n_k][n_k+1][Dr] (device). */
+a2_status a2_heff_apply(a2_ctx* ctx, const a2_mpo* mpo, int k, a2_precision prec, int Dl, int Dr,
+                        const double* L, const double* R, const double* x, double* y);
+
+/* Environment update at site j (eqs. env_L / env_R and the update of App. A):
+ * side 0 (left):  out[b,w',b'] = sum bra[a,s,b] in[a,w,a'] A_j[w,s,t,w'] ket[a',t,b'],
+ *                 in [Dlb][R_j][Dlk], out [Drb][R_j+1][Drk];
+ * side 1 (right): out[a,w,a'] = sum bra[a,s,b] A_j[w,s,t,w'] in[b,w',b'] ket[a',t,b'],
+ *                 in [Drb][R_j+1][Drk], out [Dlb][R_j][Dlk].
+ * bra: [Dlb][n][Drb], ket: [Dlk][n][Drk] (device). */
+a2_status a2_env_update(a2_ctx* ctx, const a2_mpo* mpo, int j, int side, a2_precision prec,
+                        int Dlb, int Drb, int Dlk, int Drk, const double* in, const double* bra,
+                        const double* ket, double* out);
+
+/* Truncated SVD step of Alg. 1 (two-site): x [Dl][n1][n2][Dr] (device) viewed as
+ * a (Dl n1) x (n2 Dr) matrix = P Sigma Q; keeps the smallest rank r <= D_max
+ * with discarded 2-norm <= tol*||sigma||.  P_out [Dl][n1][r] (left-orthonormal),
+ * SQ_out [r][n2][Dr] (device, capacity min(Dl n1, n2 Dr) columns/rows);
+ * rank_out, discarded_out (host). */
+a2_status a2_svd_split(a2_ctx* ctx, int Dl, int n1, int n2, int Dr, const double* x, int D_max,
+                       double tol, double* P_out, double* SQ_out, int* rank_out,
+                       double* discarded_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* A2DMRG_H */

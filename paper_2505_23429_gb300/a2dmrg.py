@@ -1,0 +1,311 @@
+"""Thin ctypes binding of the C ABI in include/a2dmrg.h (argument marshalling only).
+
+Every computation runs in liba2dmrg.so (CUDA kernels for sm_103a).  Loading
+fails loudly when the library is missing: there is no CPU fallback.  PyTorch
+is used only for device buffers (kernel-level entry points take CUDA tensors)
+and for the current CUDA stream.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liba2dmrg.so")
+
+PRECISION = {"fp64": 0, "bf16": 1, "tf32": 2, "fp32": 3}
+STATUS = {0: "A2_OK", -1: "A2_EINVAL", -2: "A2_ENOMEM", -3: "A2_ECUDA", -4: "A2_ENOCONV",
+          -5: "A2_ENUMERIC", -6: "A2_ETIMEOUT", -7: "A2_EUNSUPPORTED"}
+
+
+class A2Error(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class SweepOpts(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_int), ("bond_partition", ctypes.POINTER(ctypes.c_int)),
+                ("D_max", ctypes.c_int), ("svd_tol", ctypes.c_double),
+                ("eig_tol", ctypes.c_double), ("coarse_eps", ctypes.c_double),
+                ("max_krylov", ctypes.c_int), ("max_restarts", ctypes.c_int),
+                ("prec", ctypes.c_int), ("refine_f64", ctypes.c_int)]
+
+
+class SweepReport(ctypes.Structure):
+    _fields_ = [("energy_in", ctypes.c_double), ("lambda_coarse", ctypes.c_double),
+                ("energy_local", ctypes.POINTER(ctypes.c_double)),
+                ("coeffs", ctypes.POINTER(ctypes.c_double)),
+                ("S_hat", ctypes.POINTER(ctypes.c_double)),
+                ("A_hat", ctypes.POINTER(ctypes.c_double)),
+                ("coarse_rank", ctypes.c_int),
+                ("krylov_iters", ctypes.POINTER(ctypes.c_int)),
+                ("max_discarded_weight", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("alg_flops", ctypes.c_double), ("matvecs", ctypes.c_longlong)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} not built: run `python -m paper_2505_23429_gb300.build` "
+                          "(needs nvcc; there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "a2_ctx_create": [ctypes.c_int, _P, ctypes.POINTER(_P)],
+        "a2_ctx_destroy": [_P],
+        "a2_ctx_synchronize": [_P],
+        "a2_tt_create": [_P, ctypes.c_int, _I, _I, ctypes.c_uint64, ctypes.POINTER(_P)],
+        "a2_tt_set_core": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D],
+        "a2_tt_get_core": [_P, ctypes.c_int, _I, _I, _I, _D],
+        "a2_tt_left_orthogonalize": [_P, _D],
+        "a2_tt_destroy": [_P],
+        "a2_mpo_load": [_P, ctypes.c_int, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_P)],
+        "a2_mpo_nnz": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)],
+        "a2_mpo_destroy": [_P],
+        "a2_additive_sweep": [_P, _P, _P, ctypes.POINTER(SweepOpts), ctypes.POINTER(SweepReport)],
+        "a2_classical_sweep": [_P, _P, _P, ctypes.POINTER(SweepOpts), ctypes.POINTER(SweepReport)],
+        "a2_coarse_solve": [_P, ctypes.c_int, _D, _D, ctypes.c_double, _D, _D, _I],
+        "a2_energy": [_P, _P, _P, ctypes.c_int, _D, _D],
+        "a2_heff_apply": [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                          _P, _P, _P, _P],
+        "a2_env_update": [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                          ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P],
+        "a2_svd_split": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
+                         ctypes.c_int, ctypes.c_double, _P, _P, _I, _D],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.a2_last_error.argtypes = [_P]
+    L.a2_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names of the entry points the binding expects from the library."""
+    lib()
+    return ["a2_ctx_create", "a2_ctx_destroy", "a2_last_error", "a2_ctx_synchronize",
+            "a2_tt_create", "a2_tt_set_core", "a2_tt_get_core", "a2_tt_left_orthogonalize",
+            "a2_tt_destroy", "a2_mpo_load", "a2_mpo_nnz", "a2_mpo_destroy",
+            "a2_additive_sweep", "a2_classical_sweep", "a2_coarse_solve", "a2_energy",
+            "a2_heff_apply", "a2_env_update", "a2_svd_split"]
+
+
+def _dp(a):
+    return a.ctypes.data_as(_D)
+
+
+def _ptr(t):
+    """Device pointer of a CUDA tensor (torch) or an integer address."""
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    def __init__(self, device=0, stream=None):
+        self._h = _P()
+        st = lib().a2_ctx_create(device, _P(stream) if stream else None, ctypes.byref(self._h))
+        if st != 0:
+            raise A2Error(st, "a2_ctx_create failed")
+
+    def check(self, st):
+        if st != 0:
+            raise A2Error(st, lib().a2_last_error(self._h).decode())
+
+    def synchronize(self):
+        self.check(lib().a2_ctx_synchronize(self._h))
+
+    def close(self):
+        if self._h:
+            lib().a2_ctx_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class TT:
+    def __init__(self, ctx, handle, phys):
+        self.ctx, self._h, self.phys = ctx, handle, list(phys)
+
+    @classmethod
+    def random(cls, ctx, phys, bonds, seed):
+        h = _P()
+        ph = np.ascontiguousarray(phys, dtype=np.int32)
+        bd = np.ascontiguousarray(bonds, dtype=np.int32)
+        ctx.check(lib().a2_tt_create(ctx._h, len(ph), ph.ctypes.data_as(_I),
+                                     bd.ctypes.data_as(_I), ctypes.c_uint64(seed),
+                                     ctypes.byref(h)))
+        return cls(ctx, h, ph)
+
+    @classmethod
+    def from_cores(cls, ctx, cores):
+        phys = [c.shape[1] for c in cores]
+        t = cls.random(ctx, phys, [1] * (len(cores) - 1), 1)
+        for j, c in enumerate(cores):
+            t.set_core(j, c)
+        return t
+
+    def set_core(self, j, core):
+        a = np.ascontiguousarray(core, dtype=np.float64)
+        self.ctx.check(lib().a2_tt_set_core(self._h, j, a.shape[0], a.shape[1], a.shape[2], _dp(a)))
+
+    def core(self, j):
+        dl, n, dr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self.ctx.check(lib().a2_tt_get_core(self._h, j, ctypes.byref(dl), ctypes.byref(n),
+                                            ctypes.byref(dr), None))
+        out = np.empty((dl.value, n.value, dr.value))
+        self.ctx.check(lib().a2_tt_get_core(self._h, j, None, None, None, _dp(out)))
+        return out
+
+    def cores(self):
+        return [self.core(j) for j in range(len(self.phys))]
+
+    def left_orthogonalize(self):
+        nrm = ctypes.c_double()
+        self.ctx.check(lib().a2_tt_left_orthogonalize(self._h, ctypes.byref(nrm)))
+        return nrm.value
+
+    def close(self):
+        if self._h:
+            lib().a2_tt_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MPO:
+    def __init__(self, ctx, cores):
+        self.ctx = ctx
+        self.cores = [np.ascontiguousarray(c, dtype=np.float64) for c in cores]
+        L = len(cores)
+        phys = np.array([c.shape[1] for c in cores], dtype=np.int32)
+        R = np.array([1] + [c.shape[3] for c in cores], dtype=np.int32)
+        ptrs = (_D * L)(*[_dp(c) for c in self.cores])
+        self._h = _P()
+        ctx.check(lib().a2_mpo_load(ctx._h, L, phys.ctypes.data_as(_I), R.ctypes.data_as(_I),
+                                    ptrs, ctypes.byref(self._h)))
+        self.L, self.phys, self.R = L, phys, R
+
+    def nnz(self, j):
+        v = ctypes.c_longlong()
+        self.ctx.check(lib().a2_mpo_nnz(self._h, j, ctypes.byref(v)))
+        return v.value
+
+    def close(self):
+        if self._h:
+            lib().a2_mpo_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _opts(L, P, partition, D_max, svd_tol, eig_tol, coarse_eps, max_krylov, max_restarts, prec,
+          refine):
+    o = SweepOpts()
+    o.P = P
+    part = None
+    if partition is not None:
+        part = np.ascontiguousarray(partition, dtype=np.int32)
+        o.bond_partition = part.ctypes.data_as(_I)
+    o.D_max, o.svd_tol, o.eig_tol, o.coarse_eps = D_max, svd_tol, eig_tol, coarse_eps
+    o.max_krylov, o.max_restarts = max_krylov, max_restarts
+    o.prec = PRECISION[prec]
+    o.refine_f64 = refine
+    return o, part
+
+
+def _sweep(fn, ctx, tt, mpo, P, partition=None, D_max=64, svd_tol=1e-10, eig_tol=1e-10,
+           coarse_eps=1e-10, max_krylov=40, max_restarts=200, prec="fp64", refine=2):
+    L = len(tt.phys)
+    o, part = _opts(L, P, partition, D_max, svd_tol, eig_tol, coarse_eps, max_krylov,
+                    max_restarts, prec, refine)
+    m = P + 1
+    bufs = dict(energy_local=np.zeros(P), coeffs=np.zeros(m), S_hat=np.zeros(m * m),
+                A_hat=np.zeros(m * m))
+    kry = np.zeros(L - 1, dtype=np.int32)
+    r = SweepReport()
+    for k, v in bufs.items():
+        setattr(r, k, _dp(v))
+    r.krylov_iters = kry.ctypes.data_as(_I)
+    ctx.check(fn(ctx._h, tt._h, mpo._h, ctypes.byref(o), ctypes.byref(r)))
+    out = dict(energy_in=r.energy_in, lambda_coarse=r.lambda_coarse, coarse_rank=r.coarse_rank,
+               max_discarded=r.max_discarded_weight, seconds=r.seconds, alg_flops=r.alg_flops,
+               matvecs=r.matvecs, krylov=kry.tolist())
+    out["energy_local"] = bufs["energy_local"]
+    out["coeffs"] = bufs["coeffs"]
+    out["S_hat"] = bufs["S_hat"].reshape(m, m)
+    out["A_hat"] = bufs["A_hat"].reshape(m, m)
+    return out
+
+
+def additive_sweep(ctx, tt, mpo, P, **kw):
+    return _sweep(lib().a2_additive_sweep, ctx, tt, mpo, P, **kw)
+
+
+def classical_sweep(ctx, tt, mpo, **kw):
+    kw.pop("partition", None)
+    return _sweep(lib().a2_classical_sweep, ctx, tt, mpo, 1, **kw)
+
+
+def coarse_solve(ctx, A, S, eps=1e-10):
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    m = A.shape[0]
+    c = np.zeros(m)
+    lam, p = ctypes.c_double(), ctypes.c_int()
+    ctx.check(lib().a2_coarse_solve(ctx._h, m, _dp(A), _dp(S), eps, _dp(c), ctypes.byref(lam),
+                                    ctypes.byref(p)))
+    return c, lam.value, p.value
+
+
+def energy(ctx, tt, mpo, prec="fp64"):
+    E, nrm = ctypes.c_double(), ctypes.c_double()
+    ctx.check(lib().a2_energy(ctx._h, tt._h, mpo._h, PRECISION[prec], ctypes.byref(E),
+                              ctypes.byref(nrm)))
+    return E.value, nrm.value
+
+
+def heff_apply(ctx, mpo, k, Lenv, Renv, x, y, prec="fp64"):
+    """y = H_eff x at bond k; CUDA float64 tensors Lenv [Dl,R,Dl], Renv [Dr,R,Dr], x, y."""
+    Dl, Dr = Lenv.shape[0], Renv.shape[0]
+    ctx.check(lib().a2_heff_apply(ctx._h, mpo._h, k, PRECISION[prec], Dl, Dr, _ptr(Lenv),
+                                  _ptr(Renv), _ptr(x), _ptr(y)))
+
+
+def env_update(ctx, mpo, j, side, Hin, bra, ket, out, prec="fp64"):
+    Dlb, _, Drb = bra.shape
+    Dlk, _, Drk = ket.shape
+    ctx.check(lib().a2_env_update(ctx._h, mpo._h, j, side, PRECISION[prec], Dlb, Drb, Dlk, Drk,
+                                  _ptr(Hin), _ptr(bra), _ptr(ket), _ptr(out)))
+
+
+def svd_split(ctx, x, D_max, tol, P_out, SQ_out):
+    Dl, n1, n2, Dr = x.shape
+    r, disc = ctypes.c_int(), ctypes.c_double()
+    ctx.check(lib().a2_svd_split(ctx._h, Dl, n1, n2, Dr, _ptr(x), D_max, tol, _ptr(P_out),
+                                 _ptr(SQ_out), ctypes.byref(r), ctypes.byref(disc)))
+    return r.value, disc.value

@@ -1,0 +1,1468 @@
+// Host driver of the two-site A2DMRG iteration (Alg. 2) and the C ABI (a2dmrg.h).
+//
+// Data layout on the device (row-major):
+//   TT core j        [D_j][n_j][D_j+1]            float64 master copy
+//   environments     [bra][MPO bond][ket]          float64 or float32 (precision mode)
+//   MPO core j       sparse row lists, left-to-right action (rows (w_r,s), entries (w_l,t))
+//                    and right-to-left action (rows (w_l,s), entries (w_r,t)).
+// The H_eff application is the chain of App. A (two-site form):
+//   S1 T1[a,w,t1,t2,b'] = sum_a' L[a,w,a'] x[a',t1,t2,b']           dense GEMM
+//   S2 T2[a,w1,s1,t2,b'] = sum_{w,t1} A_k[w,s1,t1,w1] T1[...]       sparse MPO action
+//   S3 T3[a,s1,s2,w2,b'] = sum_{w1,t2} A_k+1[w1,s2,t2,w2] T2[...]   sparse MPO action
+//   S4 y[a,s1,s2,b]      = sum_{w2,b'} T3[...] R[b,w2,b']            dense GEMM (split K)
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/a2dmrg.h"
+#include "kernels.cuh"
+#include "linalg.cuh"
+#include "tc_gemm.cuh"
+
+using namespace a2;
+
+// ============================================================================= handles
+struct a2_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  Solver solver;
+  std::string err;
+  DevBuf scal, partial;         // device scalars, reduction partials
+  double* h_scal = nullptr;     // pinned host mirror
+  DevBuf t1, t2, t3, xa, ya, cb, ck, gram, wv, tmp1, tmp2;   // scratch
+};
+
+struct a2_tt {
+  a2_ctx* ctx = nullptr;
+  int L = 0;
+  std::vector<int> phys;
+  std::vector<int> dims;        // L + 1 bond dims (left bond of core j = dims[j])
+  std::vector<DevBuf> cores;
+};
+
+namespace {
+
+struct SiteOps {
+  int Rl = 0, n = 0, Rr = 0;
+  long long nnz = 0;
+  struct Part {
+    int nrows = 0, nnz = 0;
+    DevBuf ptr, rw, rs, nw, nt, v64, v32;
+    template <typename V> SparseRows<V> rows() const {
+      SparseRows<V> r;
+      r.nrows = nrows;
+      r.row_ptr = ptr.as<int>();
+      r.row_w = rw.as<int>();
+      r.row_s = rs.as<int>();
+      r.nz_w = nw.as<int>();
+      r.nz_t = nt.as<int>();
+      if constexpr (sizeof(V) == 8) r.nz_val = v64.as<double>();
+      else r.nz_val = v32.as<float>();
+      return r;
+    }
+  } lr, rl;
+};
+
+}  // namespace
+
+struct a2_mpo {
+  a2_ctx* ctx = nullptr;
+  int L = 0;
+  std::vector<int> phys, R;
+  std::vector<SiteOps> site;
+};
+
+// ============================================================================= helpers
+namespace {
+
+void upload(DevBuf& b, const void* h, size_t bytes, cudaStream_t s) {
+  b.ensure(bytes, s);
+  if (bytes) A2_CUDA(cudaMemcpyAsync(b.p, h, bytes, cudaMemcpyHostToDevice, s));
+}
+
+void build_part(SiteOps::Part& part, const std::vector<std::vector<std::array<double, 3>>>& rows,
+                const std::vector<std::pair<int, int>>& rowid, cudaStream_t s) {
+  part.nrows = (int)rows.size();
+  std::vector<int> ptr(rows.size() + 1, 0), rw, rs, nw, nt;
+  std::vector<double> v64;
+  std::vector<float> v32;
+  for (size_t r = 0; r < rows.size(); ++r) {
+    rw.push_back(rowid[r].first);
+    rs.push_back(rowid[r].second);
+    for (auto& e : rows[r]) {
+      nw.push_back((int)e[0]);
+      nt.push_back((int)e[1]);
+      v64.push_back(e[2]);
+      v32.push_back((float)e[2]);
+    }
+    ptr[r + 1] = (int)nw.size();
+  }
+  part.nnz = (int)nw.size();
+  upload(part.ptr, ptr.data(), ptr.size() * sizeof(int), s);
+  upload(part.rw, rw.data(), rw.size() * sizeof(int), s);
+  upload(part.rs, rs.data(), rs.size() * sizeof(int), s);
+  upload(part.nw, nw.data(), nw.size() * sizeof(int), s);
+  upload(part.nt, nt.data(), nt.size() * sizeof(int), s);
+  upload(part.v64, v64.data(), v64.size() * sizeof(double), s);
+  upload(part.v32, v32.data(), v32.size() * sizeof(float), s);
+}
+
+// Scan one dense core W[wl][s][t][wr] into the two sparse actions.
+void build_site(SiteOps& so, const double* W, int Rl, int n, int Rr, cudaStream_t s) {
+  so.Rl = Rl; so.n = n; so.Rr = Rr;
+  std::vector<std::vector<std::array<double, 3>>> lr((size_t)Rr * n), rl((size_t)Rl * n);
+  std::vector<std::pair<int, int>> lrid((size_t)Rr * n), rlid((size_t)Rl * n);
+  for (int wr = 0; wr < Rr; ++wr)
+    for (int sx = 0; sx < n; ++sx) lrid[(size_t)wr * n + sx] = {wr, sx};
+  for (int wl = 0; wl < Rl; ++wl)
+    for (int sx = 0; sx < n; ++sx) rlid[(size_t)wl * n + sx] = {wl, sx};
+  long long nnz = 0;
+  for (int wl = 0; wl < Rl; ++wl)
+    for (int sx = 0; sx < n; ++sx)
+      for (int t = 0; t < n; ++t)
+        for (int wr = 0; wr < Rr; ++wr) {
+          const double v = W[(((size_t)wl * n + sx) * n + t) * Rr + wr];
+          if (v == 0.0) continue;
+          ++nnz;
+          lr[(size_t)wr * n + sx].push_back({(double)wl, (double)t, v});
+          rl[(size_t)wl * n + sx].push_back({(double)wr, (double)t, v});
+        }
+  so.nnz = nnz;
+  build_part(so.lr, lr, lrid, s);
+  build_part(so.rl, rl, rlid, s);
+}
+
+double* scal(a2_ctx* c, int i) { return c->scal.as<double>() + i; }
+
+// copy `count` doubles from the device scalar area to the pinned host mirror and wait
+void fetch_scalars(a2_ctx* c, int first, int count) {
+  A2_CUDA(cudaMemcpyAsync(c->h_scal + first, scal(c, first), sizeof(double) * count,
+                          cudaMemcpyDeviceToHost, c->stream));
+  A2_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+double dot_dev(a2_ctx* c, const double* x, const double* y, long long n, int slot) {
+  dot_multi(x, 0, 1, y, n, c->partial.as<double>(), scal(c, slot), c->stream);
+  fetch_scalars(c, slot, 1);
+  return c->h_scal[slot];
+}
+
+void check_finite(double v, const char* what) {
+  if (!std::isfinite(v)) throw NumericError(std::string("non-finite value in ") + what);
+}
+
+// ============================================================================= contractions
+// A TT core viewed in compute type T (converted copy for float).
+template <typename T>
+const T* as_compute(a2_ctx* c, const double* core, long long n, DevBuf& buf) {
+  if constexpr (sizeof(T) == 8) {
+    (void)c; (void)n; (void)buf;
+    return core;
+  } else {
+    buf.ensure(sizeof(float) * (size_t)n, c->stream);
+    convert<double, float>(core, buf.as<float>(), n, c->stream);
+    return buf.as<float>();
+  }
+}
+
+// Left environment update (eq. env_L update): Hin [Dlb][Rl][Dlk] -> Hout [Drb][Rr][Drk].
+template <typename T>
+void env_left(a2_ctx* c, const SiteOps& so, const T* Hin, const T* bra, int Dlb, int Drb,
+              const T* ket, int Dlk, int Drk, T* Hout) {
+  const int n = so.n, Rl = so.Rl, Rr = so.Rr;
+  cudaStream_t s = c->stream;
+  c->tmp1.ensure(sizeof(T) * (size_t)Dlb * Rl * n * Drk, s);
+  c->tmp2.ensure(sizeof(T) * (size_t)Dlb * n * Rr * Drk, s);
+  T* T1 = c->tmp1.as<T>();
+  T* T2 = c->tmp2.as<T>();
+  {  // E1: T1[(a w)][(t b')] = sum_a' Hin[(a w)][a'] ket[a'][(t b')]
+    SimtGemm<T, T> g;
+    g.M = Dlb * Rl; g.N = n * Drk; g.K = Dlk;
+    g.A = Hin; g.sam = Dlk; g.sak = 1;
+    g.B = ket; g.sbn = 1; g.sbk = (long long)n * Drk;
+    g.C = T1; g.scm = (long long)n * Drk; g.scn = 1;
+    simt_gemm(g, s);
+  }
+  {  // E2: T2[(a s)][(w' b')] = sum_{w,t} A[w,s,t,w'] T1[(a w)][(t b')]
+    SparseGeom gm;
+    gm.veclen = Drk;
+    gm.in_sw = (long long)n * Drk; gm.in_st = Drk;
+    gm.out_sw = Drk; gm.out_ss = (long long)Rr * Drk;
+    gm.B1 = Dlb; gm.in_b1 = (long long)Rl * n * Drk; gm.out_b1 = (long long)n * Rr * Drk;
+    sparse_rows_apply<T, T, T>(so.lr.rows<T>(), gm, T1, T2, s);
+  }
+  {  // E3: Hout[b][(w' b')] = sum_{(a s)} bra[(a s)][b] T2[(a s)][(w' b')]
+    SimtGemm<T, T> g;
+    g.M = Drb; g.N = Rr * Drk; g.K = Dlb * n;
+    g.A = bra; g.sam = 1; g.sak = Drb;
+    g.B = T2; g.sbn = 1; g.sbk = (long long)Rr * Drk;
+    g.C = Hout; g.scm = (long long)Rr * Drk; g.scn = 1;
+    simt_gemm(g, s);
+  }
+}
+
+// Right environment update (eq. env_R update): Hin [Drb][Rr][Drk] -> Hout [Dlb][Rl][Dlk].
+template <typename T>
+void env_right(a2_ctx* c, const SiteOps& so, const T* Hin, const T* bra, int Dlb, int Drb,
+               const T* ket, int Dlk, int Drk, T* Hout) {
+  const int n = so.n, Rl = so.Rl, Rr = so.Rr;
+  cudaStream_t s = c->stream;
+  c->tmp1.ensure(sizeof(T) * ((size_t)Drb * Rr * n * Dlk + (size_t)n * Dlk * Drk), s);
+  c->tmp2.ensure(sizeof(T) * (size_t)n * Drb * Rl * Dlk, s);
+  T* T1 = c->tmp1.as<T>();
+  T* Vt = T1 + (size_t)Drb * Rr * n * Dlk;
+  T* T2 = c->tmp2.as<T>();
+  permute_swap01<T, T>(ket, Vt, n, Dlk, Drk, s);      // Vt[t][a'][b'] = ket[a'][t][b']
+  {  // F1: T1[(b w')][(t a')] = sum_b' Hin[(b w')][b'] Vt[(t a')][b']
+    SimtGemm<T, T> g;
+    g.M = Drb * Rr; g.N = n * Dlk; g.K = Drk;
+    g.A = Hin; g.sam = Drk; g.sak = 1;
+    g.B = Vt; g.sbn = Drk; g.sbk = 1;
+    g.C = T1; g.scm = (long long)n * Dlk; g.scn = 1;
+    simt_gemm(g, s);
+  }
+  {  // F2: T2[(s b)][(w a')] = sum_{w',t} A[w,s,t,w'] T1[(b w')][(t a')]
+    SparseGeom gm;
+    gm.veclen = Dlk;
+    gm.in_sw = (long long)n * Dlk; gm.in_st = Dlk;
+    gm.out_sw = Dlk; gm.out_ss = (long long)Drb * Rl * Dlk;
+    gm.B1 = Drb; gm.in_b1 = (long long)Rr * n * Dlk; gm.out_b1 = (long long)Rl * Dlk;
+    sparse_rows_apply<T, T, T>(so.rl.rows<T>(), gm, T1, T2, s);
+  }
+  {  // F3: Hout[a][(w a')] = sum_{(s b)} bra[a][(s b)] T2[(s b)][(w a')]
+    SimtGemm<T, T> g;
+    g.M = Dlb; g.N = Rl * Dlk; g.K = n * Drb;
+    g.A = bra; g.sam = (long long)n * Drb; g.sak = 1;
+    g.B = T2; g.sbn = 1; g.sbk = (long long)Rl * Dlk;
+    g.C = Hout; g.scm = (long long)Rl * Dlk; g.scn = 1;
+    simt_gemm(g, s);
+  }
+}
+
+// Split-K factor so that the skinny S4 GEMM fills the GPU.
+int pick_splitk(int M, int N, int K, int tile) {
+  const long long tiles = (long long)cdiv(M, tile) * cdiv(N, tile);
+  int sk = (int)std::max<long long>(1, 608 / std::max<long long>(1, tiles));
+  sk = std::min(sk, std::max(1, K / 256));
+  return std::max(1, std::min(sk, 64));
+}
+
+// y = H_eff x (two-site, App. A) in compute type T; x, y in T.
+template <typename T>
+void heff_T(a2_ctx* c, const SiteOps& A1, const SiteOps& A2, const T* HL, const T* HR, int Dl,
+            int Dr, const T* x, T* y) {
+  const int n1 = A1.n, n2 = A2.n, Rl = A1.Rl, R1 = A1.Rr, Rr = A2.Rr;
+  cudaStream_t s = c->stream;
+  const size_t s1 = (size_t)Dl * Rl * n1 * n2 * Dr;
+  const size_t s2 = (size_t)Dl * R1 * n1 * n2 * Dr;
+  const size_t s3 = (size_t)Dl * n1 * n2 * Rr * Dr;
+  c->t1.ensure(sizeof(T) * std::max(s1, s3), s);
+  c->t2.ensure(sizeof(T) * s2, s);
+  T* T1 = c->t1.as<T>();
+  T* T2 = c->t2.as<T>();
+  T* T3 = c->t1.as<T>();
+  const long long N1 = (long long)n1 * n2 * Dr;
+  {  // S1
+    SimtGemm<T, T> g;
+    g.M = Dl * Rl; g.N = (int)N1; g.K = Dl;
+    g.A = HL; g.sam = Dl; g.sak = 1;
+    g.B = x; g.sbn = 1; g.sbk = N1;
+    g.C = T1; g.scm = N1; g.scn = 1;
+    simt_gemm(g, s);
+  }
+  {  // S2: rows (w1, s1), entries (w, t1); vector (t2, b')
+    SparseGeom gm;
+    gm.veclen = n2 * Dr;
+    gm.in_sw = (long long)n1 * n2 * Dr; gm.in_st = (long long)n2 * Dr;
+    gm.out_sw = (long long)n1 * n2 * Dr; gm.out_ss = (long long)n2 * Dr;
+    gm.B1 = Dl; gm.in_b1 = (long long)Rl * n1 * n2 * Dr; gm.out_b1 = (long long)R1 * n1 * n2 * Dr;
+    sparse_rows_apply<T, T, T>(A1.lr.rows<T>(), gm, T1, T2, s);
+  }
+  {  // S3: batch (a, s1); rows (w2, s2), entries (w1, t2); vector b'
+    SparseGeom gm;
+    gm.veclen = Dr;
+    gm.in_sw = (long long)n1 * n2 * Dr; gm.in_st = Dr;
+    gm.out_sw = Dr; gm.out_ss = (long long)Rr * Dr;
+    gm.B1 = Dl; gm.B2 = n1;
+    gm.in_b1 = (long long)R1 * n1 * n2 * Dr; gm.in_b2 = (long long)n2 * Dr;
+    gm.out_b1 = (long long)n1 * n2 * Rr * Dr; gm.out_b2 = (long long)n2 * Rr * Dr;
+    sparse_rows_apply<T, T, T>(A2.lr.rows<T>(), gm, T2, T3, s);
+  }
+  {  // S4: y[(a s1 s2)][b] = sum_{(w2 b')} T3[(a s1 s2)][(w2 b')] HR[b][(w2 b')]
+    SimtGemm<T, T> g;
+    g.M = Dl * n1 * n2; g.N = Dr; g.K = Rr * Dr;
+    g.A = T3; g.sam = g.K; g.sak = 1;
+    g.B = HR; g.sbn = g.K; g.sbk = 1;
+    g.C = y; g.scm = Dr; g.scn = 1;
+    g.splitk = pick_splitk(g.M, g.N, g.K, sizeof(T) == 8 ? 64 : 128);
+    if (g.splitk > 1) {
+      g.mode = GEMM_ATOMIC;
+      fill_zero(y, sizeof(T) * (size_t)g.M * g.N, s);
+    }
+    simt_gemm(g, s);
+  }
+}
+
+double heff_flops(const SiteOps& A1, const SiteOps& A2, int Dl, int Dr) {
+  const double n1 = A1.n, n2 = A2.n;
+  return 2.0 * n1 * n2 * Dl * Dr * (A1.Rl * (double)Dl + A2.Rr * (double)Dr) +
+         2.0 * n2 * Dl * Dr * (double)A1.nnz + 2.0 * n1 * Dl * Dr * (double)A2.nnz;
+}
+double env_flops(const SiteOps& so, int Dl, int Dr) {
+  return 2.0 * so.n * (double)Dl * Dr * (so.Rl * (double)Dl + so.Rr * (double)Dr) +
+         2.0 * (double)Dl * Dr * (double)so.nnz;
+}
+
+// ============================================================================= engine
+struct View {   // a TT as per-site device pointers and bond dims
+  std::vector<const double*> core;
+  std::vector<int> Dl, Dr;
+  int n(int j, const a2_mpo* m) const { return m->phys[j]; }
+};
+
+template <typename T>
+struct Engine {
+  a2_ctx* c;
+  const a2_mpo* mpo;
+  int L;
+  a2_precision prec;
+  std::vector<DevBuf> HL, HR;            // envs in T
+  std::vector<int> HLd, HRd;             // bond dims of the stored envs
+  double flops = 0.0;
+  long long matvecs = 0;
+  DevBuf cvt_bra, cvt_ket;
+
+  Engine(a2_ctx* c_, const a2_mpo* m, a2_precision p) : c(c_), mpo(m), L(m->L), prec(p) {
+    HL.resize(L + 1);
+    HR.resize(L + 1);
+    HLd.assign(L + 1, 0);
+    HRd.assign(L + 1, 0);
+  }
+
+  void set_unit(DevBuf& b) {
+    b.ensure(sizeof(T), c->stream);
+    const T one = T(1);
+    A2_CUDA(cudaMemcpyAsync(b.p, &one, sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    A2_CUDA(cudaStreamSynchronize(c->stream));   // `one` lives on the host stack
+  }
+
+  // env update with FP64 cores converted to T
+  void left_update(const T* Hin, int j, const double* bra, int Dlb, int Drb, const double* ket,
+                   int Dlk, int Drk, T* Hout) {
+    const int n = mpo->phys[j];
+    const T* b = as_compute<T>(c, bra, (long long)Dlb * n * Drb, cvt_bra);
+    const T* k = (ket == bra) ? b : as_compute<T>(c, ket, (long long)Dlk * n * Drk, cvt_ket);
+    env_left<T>(c, mpo->site[j], Hin, b, Dlb, Drb, k, Dlk, Drk, Hout);
+    flops += env_flops(mpo->site[j], std::max(Dlb, Dlk), std::max(Drb, Drk));
+  }
+  void right_update(const T* Hin, int j, const double* bra, int Dlb, int Drb,
+                    const double* ket, int Dlk, int Drk, T* Hout) {
+    const int n = mpo->phys[j];
+    const T* b = as_compute<T>(c, bra, (long long)Dlb * n * Drb, cvt_bra);
+    const T* k = (ket == bra) ? b : as_compute<T>(c, ket, (long long)Dlk * n * Drk, cvt_ket);
+    env_right<T>(c, mpo->site[j], Hin, b, Dlb, Drb, k, Dlk, Drk, Hout);
+    flops += env_flops(mpo->site[j], std::max(Dlb, Dlk), std::max(Drb, Drk));
+  }
+
+  // y = H_eff x at bond k with FP64 vectors and envs HL_ (T) / HR_ (T)
+  void matvec(int k, const T* HL_, const T* HR_, int Dl, int Dr, const double* x, double* y) {
+    const SiteOps& A1 = mpo->site[k];
+    const SiteOps& A2 = mpo->site[k + 1];
+    const long long N = (long long)Dl * A1.n * A2.n * Dr;
+    if constexpr (sizeof(T) == 8) {
+      heff_T<double>(c, A1, A2, HL_, HR_, Dl, Dr, x, y);
+    } else {
+      c->xa.ensure(sizeof(float) * N, c->stream);
+      c->ya.ensure(sizeof(float) * N, c->stream);
+      convert<double, float>(x, c->xa.as<float>(), N, c->stream);
+      heff_T<float>(c, A1, A2, HL_, HR_, Dl, Dr, c->xa.as<float>(), c->ya.as<float>());
+      convert<float, double>(c->ya.as<float>(), y, N, c->stream);
+    }
+    flops += heff_flops(A1, A2, Dl, Dr);
+    ++matvecs;
+  }
+};
+
+// ============================================================================= Lanczos
+struct LanczosResult {
+  double theta = 0.0;
+  int matvecs = 0, cycles = 0;
+  bool converged = false;
+};
+
+// Restarted Lanczos with full re-orthogonalisation (twice) for the lowest eigenpair of
+// the operator `mv`, started from x0 (device, overwritten by the unit Ritz vector with
+// <x, x0> >= 0).  Scalars are reduced on the device and read back once per step.
+template <typename MV>
+LanczosResult lanczos(a2_ctx* c, MV&& mv, double* x, long long N, double tol, int max_krylov,
+                      int max_cycles) {
+  cudaStream_t s = c->stream;
+  const int m = (int)std::min<long long>(std::min(max_krylov, 63), N);
+  c->wv.ensure(sizeof(double) * (size_t)(m + 3) * N, s);
+  double* V = c->wv.as<double>();
+  double* w = V + (size_t)m * N;
+  double* x0 = w + N;
+  double* tmp = x0 + N;
+  A2_CUDA(cudaMemcpyAsync(x0, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  double nrm2 = dot_dev(c, x, x, N, 0);
+  check_finite(nrm2, "Lanczos start vector");
+  if (!(nrm2 > 0.0)) {   // zero start vector: use the constant vector
+    std::vector<double> ones((size_t)N, 1.0);
+    A2_CUDA(cudaMemcpyAsync(x, ones.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
+    A2_CUDA(cudaMemcpyAsync(x0, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    nrm2 = dot_dev(c, x, x, N, 0);
+  }
+  A2_CUDA(cudaMemcpyAsync(V, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  A2_CUDA(cudaMemcpyAsync(tmp, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  normalize_into(tmp, scal(c, 0), V, N, s);
+  LanczosResult res;
+  std::vector<double> alpha, beta;
+  std::vector<double> T(64 * 64), evec(64 * 64), ev(64);
+  double* dT = scal(c, 128);
+  double* dev_ev = scal(c, 128 + 64 * 64);
+  double* dev_evec = dev_ev + 64;
+  int* dstat = reinterpret_cast<int*>(dev_evec + 64 * 64);
+  for (int cyc = 1; cyc <= max_cycles; ++cyc) {
+    res.cycles = cyc;
+    alpha.clear();
+    beta.clear();
+    int j = 0;
+    bool conv = false;
+    double theta = 0.0;
+    std::vector<double> svec;
+    for (j = 0; j < m; ++j) {
+      double* vj = V + (size_t)j * N;
+      mv(vj, w);
+      ++res.matvecs;
+      // alpha_j = <v_j, w>; w -= alpha v_j + beta v_{j-1}
+      dot_multi(vj, 0, 1, w, N, c->partial.as<double>(), scal(c, 1), s);
+      lanczos_update(w, vj, j > 0 ? V + (size_t)(j - 1) * N : nullptr, scal(c, 1),
+                     j > 0 ? beta.back() : 0.0, N, s);
+      for (int pass = 0; pass < 2; ++pass) {   // full re-orthogonalisation
+        dot_multi(V, N, j + 1, w, N, c->partial.as<double>(), scal(c, 8), s);
+        gemv_sub(V, N, j + 1, scal(c, 8), w, N, s);
+      }
+      dot_multi(w, 0, 1, w, N, c->partial.as<double>(), scal(c, 2), s);
+      fetch_scalars(c, 1, 2);
+      const double a = c->h_scal[1];
+      const double b2 = c->h_scal[2];
+      check_finite(a, "Lanczos alpha");
+      check_finite(b2, "Lanczos beta");
+      const double b = std::sqrt(std::max(b2, 0.0));
+      alpha.push_back(a);
+      // lowest eigenpair of the tridiagonal T_j (device Jacobi)
+      const int k = j + 1;
+      std::fill(T.begin(), T.begin() + k * k, 0.0);
+      for (int i = 0; i < k; ++i) {
+        T[i * k + i] = alpha[i];
+        if (i + 1 < k) T[i * k + i + 1] = T[(i + 1) * k + i] = beta[i];
+      }
+      A2_CUDA(cudaMemcpyAsync(dT, T.data(), sizeof(double) * k * k, cudaMemcpyHostToDevice, s));
+      jacobi_eig(dT, k, dev_ev, dev_evec, dstat, s);
+      A2_CUDA(cudaMemcpyAsync(ev.data(), dev_ev, sizeof(double), cudaMemcpyDeviceToHost, s));
+      A2_CUDA(cudaMemcpyAsync(evec.data(), dev_evec, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+      A2_CUDA(cudaStreamSynchronize(s));
+      theta = ev[0];
+      svec.assign(evec.begin(), evec.begin() + k);
+      const double resid = std::fabs(b * svec[k - 1]);
+      const bool breakdown = b <= 1e-14 * std::max(1.0, std::fabs(theta));
+      if (resid <= tol * std::max(1.0, std::fabs(theta)) || breakdown || k == N) {
+        conv = true;
+        ++j;
+        break;
+      }
+      if (j == m - 1) { ++j; break; }
+      beta.push_back(b);
+      // v_{j+1} = w / b
+      A2_CUDA(cudaMemcpyAsync(scal(c, 3), &b2, sizeof(double), cudaMemcpyHostToDevice, s));
+      normalize_into(w, scal(c, 3), V + (size_t)(j + 1) * N, N, s);
+      A2_CUDA(cudaStreamSynchronize(s));   // b2 is a host stack value
+    }
+    // Ritz vector x = V s (unit), becomes the restart vector
+    A2_CUDA(cudaMemcpyAsync(scal(c, 8), svec.data(), sizeof(double) * svec.size(),
+                            cudaMemcpyHostToDevice, s));
+    gemv_set(V, N, (int)svec.size(), scal(c, 8), x, N, s);
+    double xn = dot_dev(c, x, x, N, 4);
+    A2_CUDA(cudaMemcpyAsync(V, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    normalize_into(x, scal(c, 4), V, N, s);
+    A2_CUDA(cudaMemcpyAsync(x, V, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    (void)xn;
+    res.theta = theta;
+    if (conv) { res.converged = true; break; }
+  }
+  // sign convention <x, x0> >= 0
+  const double sgn = dot_dev(c, x, x0, N, 5);
+  if (sgn < 0) axpby(0.0, x, -1.0, x, N, s);
+  return res;
+}
+
+// ============================================================================= SVD step
+// M (rows x cols, row-major) = P Sigma Q via the left Gram matrix M M^T (FP64):
+// P = leading eigenvectors (left-orthonormal), SQ = P^T M.  Returns rank r and
+// the discarded 2-norm.  P (rows x r) and SQ (r x cols) row-major.
+int svd_split_dev(a2_ctx* c, const double* M, int rows, int cols, int D_max, double tol,
+                  double* P, double* SQ, double* discarded, std::vector<double>* sv_out = nullptr) {
+  cudaStream_t s = c->stream;
+  c->gram.ensure(sizeof(double) * ((size_t)rows * rows + rows), s);
+  double* G = c->gram.as<double>();
+  double* w = G + (size_t)rows * rows;
+  {
+    SimtGemm<double, double> g;
+    g.M = rows; g.N = rows; g.K = cols;
+    g.A = M; g.sam = cols; g.sak = 1;
+    g.B = M; g.sbn = cols; g.sbk = 1;
+    g.C = G; g.scm = rows; g.scn = 1;
+    simt_gemm(g, s);
+  }
+  c->solver.syevd(G, rows, w, s);
+  std::vector<double> lam(rows);
+  A2_CUDA(cudaMemcpyAsync(lam.data(), w, sizeof(double) * rows, cudaMemcpyDeviceToHost, s));
+  A2_CUDA(cudaStreamSynchronize(s));
+  // singular values descending
+  std::vector<double> sv(rows);
+  for (int i = 0; i < rows; ++i) sv[i] = std::sqrt(std::max(lam[rows - 1 - i], 0.0));
+  const int kmax = std::min(rows, cols);
+  sv.resize(kmax);
+  double total = 0.0;
+  for (double x : sv) total += x * x;
+  std::vector<double> tail(kmax + 1, 0.0);
+  for (int i = kmax - 1; i >= 0; --i) tail[i] = tail[i + 1] + sv[i] * sv[i];
+  int r = kmax;
+  const double thr = tol * tol * total;
+  for (int cand = 1; cand <= kmax; ++cand)
+    if (tail[cand] <= thr) { r = cand; break; }
+  r = std::max(1, std::min(r, D_max));
+  if (discarded) *discarded = std::sqrt(std::max(tail[r], 0.0));
+  if (sv_out) *sv_out = sv;
+  // P[i][c] = evec column (rows-1-c): G column-major, column j at G + j*rows
+  c->tmp1.ensure(sizeof(double) * (size_t)rows * r, s);
+  double* Pcm = c->tmp1.as<double>();   // r columns, column-major (rows x r)
+  for (int cc = 0; cc < r; ++cc)
+    A2_CUDA(cudaMemcpyAsync(Pcm + (size_t)cc * rows, G + (size_t)(rows - 1 - cc) * rows,
+                            sizeof(double) * rows, cudaMemcpyDeviceToDevice, s));
+  transpose2d<double, double>(Pcm, P, r, rows, s);      // -> row-major rows x r
+  {  // SQ = P^T M : (r x cols)
+    SimtGemm<double, double> g;
+    g.M = r; g.N = cols; g.K = rows;
+    g.A = P; g.sam = 1; g.sak = r;
+    g.B = M; g.sbn = 1; g.sbk = cols;
+    g.C = SQ; g.scm = cols; g.scn = 1;
+    simt_gemm(g, s);
+  }
+  return r;
+}
+
+// C = A (ra x k) * B (k x cb), all row-major FP64
+void matmul_dev(a2_ctx* c, const double* A, int ra, int k, const double* B, int cb, double* C) {
+  SimtGemm<double, double> g;
+  g.M = ra; g.N = cb; g.K = k;
+  g.A = A; g.sam = k; g.sak = 1;
+  g.B = B; g.sbn = 1; g.sbk = cb;
+  g.C = C; g.scm = cb; g.scn = 1;
+  simt_gemm(g, c->stream);
+}
+
+// ============================================================================= TT helpers
+void tt_check(const a2_tt* tt) {
+  A2_REQUIRE(tt && tt->L >= 2, "TT with at least two sites required");
+  for (int j = 0; j < tt->L; ++j) A2_REQUIRE(tt->cores[j].p, "TT core not set");
+  A2_REQUIRE(tt->dims[0] == 1 && tt->dims[tt->L] == 1, "TT boundary bonds must be 1");
+}
+
+void left_orthogonalize(a2_tt* tt, double* norm_out) {
+  a2_ctx* c = tt->ctx;
+  cudaStream_t s = c->stream;
+  for (int j = 0; j + 1 < tt->L; ++j) {
+    const int Dl = tt->dims[j], n = tt->phys[j], Dr = tt->dims[j + 1];
+    const int rows = Dl * n;
+    // QR of (rows x Dr) = LQ of its transpose (Dr x rows)
+    c->tmp2.ensure(sizeof(double) * (size_t)rows * Dr * 3, s);
+    double* Mt = c->tmp2.as<double>();
+    double* Lf = Mt + (size_t)rows * Dr;
+    double* Qf = Lf + (size_t)Dr * Dr;
+    transpose2d<double, double>(tt->cores[j].as<double>(), Mt, rows, Dr, s);
+    const int k = c->solver.lq(Mt, Dr, rows, Lf, Qf, s);   // Mt = Lf (Dr x k) Qf (k x rows)
+    // core j = Qf^T (rows x k);  R = Lf^T (k x Dr);  core j+1 <- R core_{j+1}
+    DevBuf nc;
+    nc.ensure(sizeof(double) * (size_t)rows * k, s);
+    transpose2d<double, double>(Qf, nc.as<double>(), k, rows, s);
+    const int n2 = tt->phys[j + 1], Dr2 = tt->dims[j + 2];
+    DevBuf Rm;
+    Rm.ensure(sizeof(double) * (size_t)k * Dr, s);
+    transpose2d<double, double>(Lf, Rm.as<double>(), Dr, k, s);
+    DevBuf nxt;
+    nxt.ensure(sizeof(double) * (size_t)k * n2 * Dr2, s);
+    matmul_dev(c, Rm.as<double>(), k, Dr, tt->cores[j + 1].as<double>(), n2 * Dr2,
+               nxt.as<double>());
+    tt->cores[j] = std::move(nc);
+    tt->cores[j + 1] = std::move(nxt);
+    tt->dims[j + 1] = k;
+  }
+  const int last = tt->L - 1;
+  const long long nl = (long long)tt->dims[last] * tt->phys[last] * tt->dims[last + 1];
+  double nrm2 = dot_dev(c, tt->cores[last].as<double>(), tt->cores[last].as<double>(), nl, 6);
+  check_finite(nrm2, "TT norm");
+  A2_REQUIRE(nrm2 > 0.0, "TT has zero norm");
+  if (norm_out) *norm_out = std::sqrt(nrm2);
+  scale_dev(tt->cores[last].as<double>(), nullptr, scal(c, 6), nl, s);
+}
+
+// ============================================================================= global iteration
+template <typename T>
+struct Sweeper {
+  a2_ctx* c;
+  a2_tt* tt;
+  const a2_mpo* mpo;
+  a2_sweep_opts o;
+  Engine<T> eng;
+  int L;
+  std::vector<DevBuf> Vc, Cc;         // right-orth cores V_i, centres C_i
+  std::vector<int> kd;                // bond dims of the right-orthogonal part
+  std::vector<int> kry;
+  double max_disc = 0.0;
+
+  Sweeper(a2_ctx* c_, a2_tt* t, const a2_mpo* m, const a2_sweep_opts& op)
+      : c(c_), tt(t), mpo(m), o(op), eng(c_, m, op.prec), L(t->L) {}
+
+  const T* hl(int j) { return eng.HL[j].template as<T>(); }
+  const T* hr(int j) { return eng.HR[j].template as<T>(); }
+
+  // Step 1 of Alg. 2: right-to-left LQ sweep, every i-orthogonal copy.
+  void step1() {
+    cudaStream_t s = c->stream;
+    Vc.clear(); Vc.resize(L);
+    Cc.clear(); Cc.resize(L);
+    kd.assign(L + 1, 1);
+    const size_t nlast = (size_t)tt->dims[L - 1] * tt->phys[L - 1];
+    Cc[L - 1].ensure(sizeof(double) * nlast, s);
+    A2_CUDA(cudaMemcpyAsync(Cc[L - 1].p, tt->cores[L - 1].p, sizeof(double) * nlast,
+                            cudaMemcpyDeviceToDevice, s));
+    kd[L] = 1;
+    for (int i = L - 1; i >= 1; --i) {
+      const int Dl = tt->dims[i], n = tt->phys[i], Dr = kd[i + 1];
+      const int cols = n * Dr;
+      const int k = std::min(Dl, cols);
+      DevBuf Lf;
+      Lf.ensure(sizeof(double) * (size_t)Dl * k, s);
+      Vc[i].ensure(sizeof(double) * (size_t)k * cols, s);
+      c->solver.lq(Cc[i].as<double>(), Dl, cols, Lf.as<double>(), Vc[i].as<double>(), s);
+      kd[i] = k;
+      const int Dl0 = tt->dims[i - 1], n0 = tt->phys[i - 1];
+      Cc[i - 1].ensure(sizeof(double) * (size_t)Dl0 * n0 * k, s);
+      matmul_dev(c, tt->cores[i - 1].as<double>(), Dl0 * n0, Dl, Lf.as<double>(), k,
+                 Cc[i - 1].as<double>());
+    }
+    kd[0] = 1;
+  }
+
+  // Step 2 (first part): left envs from U, right envs from V.
+  void build_envs() {
+    cudaStream_t s = c->stream;
+    eng.set_unit(eng.HL[0]);
+    eng.HLd[0] = 1;
+    for (int j = 0; j + 1 < L; ++j) {
+      const int Dl = tt->dims[j], Dr = tt->dims[j + 1];
+      eng.HL[j + 1].ensure(sizeof(T) * (size_t)Dr * mpo->R[j + 1] * Dr, s);
+      eng.left_update(hl(j), j, tt->cores[j].as<double>(), Dl, Dr, tt->cores[j].as<double>(),
+                      Dl, Dr, eng.HL[j + 1].template as<T>());
+      eng.HLd[j + 1] = Dr;
+    }
+    eng.set_unit(eng.HR[L]);
+    eng.HRd[L] = 1;
+    for (int j = L - 1; j >= 1; --j) {
+      const int Dl = kd[j], Dr = kd[j + 1];
+      eng.HR[j].ensure(sizeof(T) * (size_t)Dl * mpo->R[j] * Dl, s);
+      eng.right_update(hr(j + 1), j, Vc[j].as<double>(), Dl, Dr, Vc[j].as<double>(), Dl, Dr,
+                       eng.HR[j].template as<T>());
+      eng.HRd[j] = Dl;
+    }
+  }
+
+  struct Group {
+    int kg, mg;
+    std::vector<DevBuf> cores;   // new cores kg..mg+1 (mg - kg + 2 of them)
+    std::vector<int> dl, dr;     // their bond dims
+    double theta = 0.0;
+  };
+
+  // Step 2 (second part): the group's left-to-right two-site micro-steps.
+  void solve_group(Group& G) {
+    cudaStream_t s = c->stream;
+    DevBuf Hloc;
+    int Dl = tt->dims[G.kg];
+    // centre C_kg
+    DevBuf centre;
+    {
+      const size_t nb = (size_t)Dl * tt->phys[G.kg] * kd[G.kg + 1];
+      centre.ensure(sizeof(double) * nb, s);
+      A2_CUDA(cudaMemcpyAsync(centre.p, Cc[G.kg].p, sizeof(double) * nb,
+                              cudaMemcpyDeviceToDevice, s));
+    }
+    int cdim = kd[G.kg + 1];           // right bond of the centre
+    const T* HLcur = hl(G.kg);
+    for (int k = G.kg; k <= G.mg; ++k) {
+      const int n1 = tt->phys[k], n2 = tt->phys[k + 1];
+      const int Dr = kd[k + 2];
+      const long long N = (long long)Dl * n1 * n2 * Dr;
+      DevBuf x;
+      x.ensure(sizeof(double) * N, s);
+      matmul_dev(c, centre.as<double>(), Dl * n1, cdim, Vc[k + 1].as<double>(), n2 * Dr,
+                 x.as<double>());
+      const T* HRk = hr(k + 2);
+      auto mv = [&](const double* in, double* out) {
+        eng.matvec(k, HLcur, HRk, Dl, Dr, in, out);
+      };
+      LanczosResult lr = lanczos(c, mv, x.as<double>(), N, o.eig_tol, o.max_krylov,
+                                 o.max_restarts);
+      check_finite(lr.theta, "local eigenvalue");
+      kry[k] = lr.matvecs;
+      G.theta = lr.theta;
+      const int rows = Dl * n1, cols = n2 * Dr;
+      const int kmax = std::min(rows, cols);
+      DevBuf P, SQ;
+      P.ensure(sizeof(double) * (size_t)rows * kmax, s);
+      SQ.ensure(sizeof(double) * (size_t)kmax * cols, s);
+      double disc = 0.0;
+      const int r = svd_split_dev(c, x.as<double>(), rows, cols, o.D_max, o.svd_tol,
+                                  P.as<double>(), SQ.as<double>(), &disc);
+      max_disc = std::max(max_disc, disc);
+      // group-local left environment with the new left-orthogonal core
+      DevBuf Hn;
+      Hn.ensure(sizeof(T) * (size_t)r * mpo->R[k + 1] * r, s);
+      eng.left_update(HLcur, k, P.as<double>(), Dl, r, P.as<double>(), Dl, r, Hn.template as<T>());
+      Hloc = std::move(Hn);
+      HLcur = Hloc.template as<T>();
+      G.cores.push_back(std::move(P));
+      G.dl.push_back(Dl);
+      G.dr.push_back(r);
+      centre = std::move(SQ);
+      cdim = Dr;
+      Dl = r;
+    }
+    G.cores.push_back(std::move(centre));
+    G.dl.push_back(Dl);
+    G.dr.push_back(kd[G.mg + 2]);
+  }
+
+  // per-site view of basis element j (0 = iterate, in its kg-orthogonal form for `form_k`)
+  View base_view(int form_k) {
+    View v;
+    v.core.resize(L); v.Dl.resize(L); v.Dr.resize(L);
+    for (int j = 0; j < L; ++j) {
+      if (j < form_k) {
+        v.core[j] = tt->cores[j].as<double>(); v.Dl[j] = tt->dims[j]; v.Dr[j] = tt->dims[j + 1];
+      } else if (j == form_k) {
+        v.core[j] = Cc[j].as<double>(); v.Dl[j] = tt->dims[j]; v.Dr[j] = kd[j + 1];
+      } else {
+        v.core[j] = Vc[j].as<double>(); v.Dl[j] = kd[j]; v.Dr[j] = kd[j + 1];
+      }
+    }
+    return v;
+  }
+  View group_view(const Group& G) {
+    View v;
+    v.core.resize(L); v.Dl.resize(L); v.Dr.resize(L);
+    for (int j = 0; j < L; ++j) {
+      if (j < G.kg) {
+        v.core[j] = tt->cores[j].as<double>(); v.Dl[j] = tt->dims[j]; v.Dr[j] = tt->dims[j + 1];
+      } else if (j <= G.mg + 1) {
+        const int q = j - G.kg;
+        v.core[j] = G.cores[q].template as<double>(); v.Dl[j] = G.dl[q]; v.Dr[j] = G.dr[q];
+      } else {
+        v.core[j] = Vc[j].as<double>(); v.Dl[j] = kd[j]; v.Dr[j] = kd[j + 1];
+      }
+    }
+    return v;
+  }
+
+  // <bra, ket> over sites lo..hi with identity outside (shared orthogonal prefix/suffix)
+  double overlap_span(const View& bra, const View& ket, int lo, int hi) {
+    cudaStream_t s = c->stream;
+    A2_REQUIRE(bra.Dl[lo] == ket.Dl[lo], "overlap: mismatched left bond");
+    const int D0 = bra.Dl[lo];
+    DevBuf E, En, Tm;
+    E.ensure(sizeof(double) * (size_t)D0 * D0, s);
+    {
+      std::vector<double> I((size_t)D0 * D0, 0.0);
+      for (int i = 0; i < D0; ++i) I[(size_t)i * D0 + i] = 1.0;
+      A2_CUDA(cudaMemcpyAsync(E.p, I.data(), sizeof(double) * I.size(), cudaMemcpyHostToDevice, s));
+      A2_CUDA(cudaStreamSynchronize(s));
+    }
+    for (int j = lo; j <= hi; ++j) {
+      const int n = tt->phys[j];
+      const int bl = bra.Dl[j], br = bra.Dr[j], kl = ket.Dl[j], kr = ket.Dr[j];
+      Tm.ensure(sizeof(double) * (size_t)bl * n * kr, s);
+      matmul_dev(c, E.as<double>(), bl, kl, ket.core[j], n * kr, Tm.as<double>());  // [a][(s b')]
+      En.ensure(sizeof(double) * (size_t)br * kr, s);
+      SimtGemm<double, double> g;   // En[b][b'] = sum_{(a s)} bra[(a s)][b] Tm[(a s)][b']
+      g.M = br; g.N = kr; g.K = bl * n;
+      g.A = bra.core[j]; g.sam = 1; g.sak = br;
+      g.B = Tm.as<double>(); g.sbn = 1; g.sbk = kr;
+      g.C = En.as<double>(); g.scm = kr; g.scn = 1;
+      simt_gemm(g, s);
+      std::swap(E, En);
+    }
+    const int Df = bra.Dr[hi];
+    A2_REQUIRE(Df == ket.Dr[hi], "overlap: mismatched right bond");
+    // trace(E)
+    std::vector<double> h((size_t)Df * Df);
+    A2_CUDA(cudaMemcpyAsync(h.data(), E.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+    A2_CUDA(cudaStreamSynchronize(s));
+    double tr = 0.0;
+    for (int i = 0; i < Df; ++i) tr += h[(size_t)i * Df + i];
+    return tr;
+  }
+
+  // <bra, A ket> over sites lo..hi, closed by the iterate's envs HL[lo] and HR[hi+1]
+  double sandwich_span(const View& bra, const View& ket, int lo, int hi) {
+    cudaStream_t s = c->stream;
+    DevBuf E, En;
+    const T* Ecur = hl(lo);
+    for (int j = lo; j <= hi; ++j) {
+      En.ensure(sizeof(T) * (size_t)bra.Dr[j] * mpo->R[j + 1] * ket.Dr[j], s);
+      eng.left_update(Ecur, j, bra.core[j], bra.Dl[j], bra.Dr[j], ket.core[j], ket.Dl[j],
+                      ket.Dr[j], En.template as<T>());
+      std::swap(E, En);
+      Ecur = E.template as<T>();
+    }
+    const long long ne = (long long)bra.Dr[hi] * mpo->R[hi + 1] * ket.Dr[hi];
+    A2_REQUIRE(eng.HRd[hi + 1] == bra.Dr[hi] && eng.HRd[hi + 1] == ket.Dr[hi],
+               "sandwich: right env dims");
+    // full contraction <E, HR[hi+1]> in FP64
+    c->xa.ensure(sizeof(double) * ne * 2, s);
+    double* e64 = c->xa.as<double>();
+    double* r64 = e64 + ne;
+    if constexpr (sizeof(T) == 8) {
+      A2_CUDA(cudaMemcpyAsync(e64, Ecur, sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
+      A2_CUDA(cudaMemcpyAsync(r64, hr(hi + 1), sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
+    } else {
+      convert<float, double>(Ecur, e64, ne, s);
+      convert<float, double>(hr(hi + 1), r64, ne, s);
+    }
+    return dot_dev(c, e64, r64, ne, 7);
+  }
+
+  void run(a2_sweep_report* rep, bool classical) {
+    cudaStream_t s = c->stream;
+    auto t0 = std::chrono::steady_clock::now();
+    tt_check(tt);
+    A2_REQUIRE(tt->phys == mpo->phys, "TT and MPO physical dims differ");
+    std::vector<int> sizes;
+    int P = classical ? 1 : o.P;
+    A2_REQUIRE(P >= 1 && P <= L - 1, "P must be in 1..L-1");
+    if (!classical && o.bond_partition) {
+      sizes.assign(o.bond_partition, o.bond_partition + P);
+    } else {
+      for (int g = 0; g < P; ++g) sizes.push_back((L - 1) / P + (g < (L - 1) % P ? 1 : 0));
+    }
+    A2_REQUIRE(std::accumulate(sizes.begin(), sizes.end(), 0) == L - 1,
+               "bond partition must sum to L-1");
+    for (int x : sizes) A2_REQUIRE(x >= 1, "empty group");
+    A2_REQUIRE(o.D_max >= 1, "D_max >= 1");
+    A2_REQUIRE(o.max_krylov >= 2 && o.max_krylov <= 63, "max_krylov in 2..63");
+    kry.assign(L - 1, 0);
+    step1();
+    build_envs();
+    std::vector<Group> groups(P);
+    int k0 = 0;
+    for (int g = 0; g < P; ++g) {
+      groups[g].kg = k0;
+      groups[g].mg = k0 + sizes[g] - 1;
+      k0 += sizes[g];
+      solve_group(groups[g]);
+    }
+    const int m = P + 1;
+    std::vector<double> S((size_t)m * m, 0.0), A((size_t)m * m, 0.0);
+    // iterate: its (L-1)-orthogonal form is the stored left-orthogonal TT
+    {
+      View b = base_view(L - 1);
+      S[0] = overlap_span(b, b, L - 1, L - 1);
+      A[0] = sandwich_span(b, b, L - 1, L - 1);
+    }
+    std::vector<View> gv(P);
+    for (int g = 0; g < P; ++g) gv[g] = group_view(groups[g]);
+    for (int g = 0; g < P; ++g) {
+      const int lo = groups[g].kg, hi = groups[g].mg + 1;
+      View b = base_view(lo);
+      S[(size_t)(g + 1)] = S[(size_t)(g + 1) * m] = overlap_span(b, gv[g], lo, hi);
+      A[(size_t)(g + 1)] = A[(size_t)(g + 1) * m] = sandwich_span(b, gv[g], lo, hi);
+      S[(size_t)(g + 1) * m + g + 1] = overlap_span(gv[g], gv[g], lo, hi);
+      A[(size_t)(g + 1) * m + g + 1] = sandwich_span(gv[g], gv[g], lo, hi);
+      for (int h = g + 1; h < P; ++h) {
+        const int hi2 = groups[h].mg + 1;
+        const double sv = overlap_span(gv[g], gv[h], lo, hi2);
+        const double av = sandwich_span(gv[g], gv[h], lo, hi2);
+        S[(size_t)(g + 1) * m + h + 1] = S[(size_t)(h + 1) * m + g + 1] = sv;
+        A[(size_t)(g + 1) * m + h + 1] = A[(size_t)(h + 1) * m + g + 1] = av;
+      }
+    }
+    for (double v : S) check_finite(v, "S_hat");
+    for (double v : A) check_finite(v, "A_hat");
+    std::vector<double> cvec(m, 0.0);
+    double lam = 0.0;
+    int prank = 0;
+    if (classical) {   // Alg. 1: the half-sweep result is the new iterate
+      cvec[1] = 1.0 / std::sqrt(S[(size_t)1 * m + 1]);
+      lam = A[(size_t)1 * m + 1] / S[(size_t)1 * m + 1];
+      prank = 1;
+    } else {
+      double* dA = scal(c, 9000);
+      double* dS = dA + m * m;
+      double* dc = dS + m * m;
+      double* dl = dc + m;
+      int* drk = reinterpret_cast<int*>(dl + 1);
+      A2_CUDA(cudaMemcpyAsync(dA, A.data(), sizeof(double) * m * m, cudaMemcpyHostToDevice, s));
+      A2_CUDA(cudaMemcpyAsync(dS, S.data(), sizeof(double) * m * m, cudaMemcpyHostToDevice, s));
+      coarse_solve_dev(dA, dS, m, o.coarse_eps, dc, dl, drk, drk + 1, s);
+      A2_CUDA(cudaMemcpyAsync(cvec.data(), dc, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+      int rk[2];
+      A2_CUDA(cudaMemcpyAsync(&lam, dl, sizeof(double), cudaMemcpyDeviceToHost, s));
+      A2_CUDA(cudaMemcpyAsync(rk, drk, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+      A2_CUDA(cudaStreamSynchronize(s));
+      prank = rk[0];
+      if (rk[1] != 0) throw NumericError("coarse Jacobi did not converge");
+    }
+    check_finite(lam, "coarse eigenvalue");
+    // Step 4: compression of sum_j c_j tau(U~^j)
+    std::vector<View> terms;
+    std::vector<double> coef;
+    for (int j = 0; j < m; ++j) {
+      if (cvec[j] == 0.0) continue;
+      terms.push_back(j == 0 ? base_view(L) : gv[j - 1]);
+      coef.push_back(cvec[j]);
+    }
+    compress(terms, coef);
+    if (rep) {
+      rep->energy_in = A[0] / S[0];
+      rep->lambda_coarse = lam;
+      rep->coarse_rank = prank;
+      if (rep->energy_local)
+        for (int g = 0; g < P; ++g) rep->energy_local[g] = groups[g].theta;
+      if (rep->coeffs) std::copy(cvec.begin(), cvec.end(), rep->coeffs);
+      if (rep->S_hat) std::copy(S.begin(), S.end(), rep->S_hat);
+      if (rep->A_hat) std::copy(A.begin(), A.end(), rep->A_hat);
+      if (rep->krylov_iters) std::copy(kry.begin(), kry.end(), rep->krylov_iters);
+      rep->max_discarded_weight = max_disc;
+      rep->alg_flops = eng.flops;
+      rep->matvecs = eng.matvecs;
+      A2_CUDA(cudaStreamSynchronize(s));
+      rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+  }
+
+  // TT-sum (block-diagonal cores) + TT rounding, result written into tt (left-orth, norm 1).
+  void compress(const std::vector<View>& terms, const std::vector<double>& coef) {
+    cudaStream_t s = c->stream;
+    const int nt = (int)terms.size();
+    std::vector<DevBuf> X(L);
+    std::vector<int> xd(L + 1, 0);
+    xd[0] = 1;
+    xd[L] = 1;
+    for (int j = 1; j < L; ++j) {
+      int d = 0;
+      for (auto& t : terms) d += t.Dl[j];
+      xd[j] = d;
+    }
+    for (int j = 0; j < L; ++j) {
+      const int n = tt->phys[j];
+      X[j].ensure(sizeof(double) * (size_t)xd[j] * n * xd[j + 1], s);
+      fill_zero(X[j].p, sizeof(double) * (size_t)xd[j] * n * xd[j + 1], s);
+      int o0 = 0, o2 = 0;
+      for (int q = 0; q < nt; ++q) {
+        const View& t = terms[q];
+        const double alpha = (j == 0) ? coef[q] : 1.0;
+        copy_block3(t.core[j], t.Dl[j], n, t.Dr[j], X[j].as<double>(), (long long)n * xd[j + 1],
+                    xd[j + 1], j == 0 ? 0 : o0, j == L - 1 ? 0 : o2, alpha, s);
+        o0 += t.Dl[j];
+        o2 += t.Dr[j];
+      }
+    }
+    if (nt == 1) {   // single term: only rounding of its ranks is needed
+    }
+    // right-to-left LQ sweep
+    for (int j = L - 1; j >= 1; --j) {
+      const int Dl = xd[j], n = tt->phys[j], Dr = xd[j + 1];
+      const int cols = n * Dr;
+      const int k = std::min(Dl, cols);
+      DevBuf Lf, Q;
+      Lf.ensure(sizeof(double) * (size_t)Dl * k, s);
+      Q.ensure(sizeof(double) * (size_t)k * cols, s);
+      c->solver.lq(X[j].as<double>(), Dl, cols, Lf.as<double>(), Q.as<double>(), s);
+      X[j] = std::move(Q);
+      const int Dl0 = xd[j - 1], n0 = tt->phys[j - 1];
+      DevBuf nx;
+      nx.ensure(sizeof(double) * (size_t)Dl0 * n0 * k, s);
+      matmul_dev(c, X[j - 1].as<double>(), Dl0 * n0, Dl, Lf.as<double>(), k, nx.as<double>());
+      X[j - 1] = std::move(nx);
+      xd[j] = k;
+    }
+    // left-to-right truncated SVD sweep
+    for (int j = 0; j + 1 < L; ++j) {
+      const int Dl = xd[j], n = tt->phys[j], Dr = xd[j + 1];
+      const int rows = Dl * n;
+      const int kmax = std::min(rows, Dr);
+      DevBuf P, SQ;
+      P.ensure(sizeof(double) * (size_t)rows * kmax, s);
+      SQ.ensure(sizeof(double) * (size_t)kmax * Dr, s);
+      double disc = 0.0;
+      const int r = svd_split_dev(c, X[j].as<double>(), rows, Dr, o.D_max, o.svd_tol,
+                                  P.as<double>(), SQ.as<double>(), &disc);
+      X[j] = std::move(P);
+      const int n1 = tt->phys[j + 1], Dr1 = xd[j + 2];
+      DevBuf nx;
+      nx.ensure(sizeof(double) * (size_t)r * n1 * Dr1, s);
+      matmul_dev(c, SQ.as<double>(), r, Dr, X[j + 1].as<double>(), n1 * Dr1, nx.as<double>());
+      X[j + 1] = std::move(nx);
+      xd[j + 1] = r;
+    }
+    // normalise the last core
+    const long long nl = (long long)xd[L - 1] * tt->phys[L - 1];
+    const double nrm2 = dot_dev(c, X[L - 1].as<double>(), X[L - 1].as<double>(), nl, 6);
+    check_finite(nrm2, "compressed norm");
+    A2_REQUIRE(nrm2 > 0.0, "compressed iterate vanished");
+    scale_dev(X[L - 1].as<double>(), nullptr, scal(c, 6), nl, s);
+    A2_CUDA(cudaStreamSynchronize(s));
+    for (int j = 0; j < L; ++j) tt->cores[j] = std::move(X[j]);
+    tt->dims = xd;
+  }
+};
+
+template <typename T>
+double energy_T(a2_ctx* c, const a2_tt* tt, const a2_mpo* mpo, double* norm_out) {
+  Engine<T> eng(c, mpo, A2_FP64);
+  cudaStream_t s = c->stream;
+  const int L = tt->L;
+  DevBuf E, En;
+  eng.set_unit(E);
+  for (int j = 0; j < L; ++j) {
+    const int Dl = tt->dims[j], Dr = tt->dims[j + 1];
+    En.ensure(sizeof(T) * (size_t)Dr * mpo->R[j + 1] * Dr, s);
+    eng.left_update(E.as<T>(), j, tt->cores[j].as<double>(), Dl, Dr, tt->cores[j].as<double>(),
+                    Dl, Dr, En.as<T>());
+    std::swap(E, En);
+  }
+  T e;
+  A2_CUDA(cudaMemcpyAsync(&e, E.p, sizeof(T), cudaMemcpyDeviceToHost, s));
+  A2_CUDA(cudaStreamSynchronize(s));
+  // norm by transfer matrices in FP64
+  DevBuf N, Nn, Tm;
+  N.ensure(sizeof(double), s);
+  const double one = 1.0;
+  A2_CUDA(cudaMemcpyAsync(N.p, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+  for (int j = 0; j < L; ++j) {
+    const int Dl = tt->dims[j], n = tt->phys[j], Dr = tt->dims[j + 1];
+    Tm.ensure(sizeof(double) * (size_t)Dl * n * Dr, s);
+    matmul_dev(c, N.as<double>(), Dl, Dl, tt->cores[j].as<double>(), n * Dr, Tm.as<double>());
+    Nn.ensure(sizeof(double) * (size_t)Dr * Dr, s);
+    SimtGemm<double, double> g;
+    g.M = Dr; g.N = Dr; g.K = Dl * n;
+    g.A = tt->cores[j].as<double>(); g.sam = 1; g.sak = Dr;
+    g.B = Tm.as<double>(); g.sbn = 1; g.sbk = Dr;
+    g.C = Nn.as<double>(); g.scm = Dr; g.scn = 1;
+    simt_gemm(g, s);
+    std::swap(N, Nn);
+  }
+  double nn;
+  A2_CUDA(cudaMemcpyAsync(&nn, N.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  A2_CUDA(cudaStreamSynchronize(s));
+  check_finite(nn, "norm");
+  if (norm_out) *norm_out = std::sqrt(std::max(nn, 0.0));
+  return (double)e / nn;
+}
+
+a2_status fail(a2_ctx* c, a2_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+template <typename F>
+a2_status guarded(a2_ctx* c, F&& f) {
+  try {
+    f();
+    return A2_OK;
+  } catch (const ArgError& e) {
+    return fail(c, A2_EINVAL, e.what());
+  } catch (const NumericError& e) {
+    return fail(c, A2_ENUMERIC, e.what());
+  } catch (const CudaError& e) {
+    const std::string m = e.what();
+    if (m.find("out of memory") != std::string::npos) return fail(c, A2_ENOMEM, m);
+    return fail(c, A2_ECUDA, m);
+  } catch (const std::bad_alloc& e) {
+    return fail(c, A2_ENOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(c, A2_ECUDA, e.what());
+  }
+}
+
+uint64_t splitmix_next(uint64_t& state) {
+  state += 0x9E3779B97F4A7C15ull;
+  uint64_t z = state;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+}  // namespace
+
+// ============================================================================= C ABI
+extern "C" {
+
+a2_status a2_ctx_create(int device, void* cuda_stream, a2_ctx** out) {
+  if (!out) return A2_EINVAL;
+  *out = nullptr;
+  a2_ctx* c = new (std::nothrow) a2_ctx();
+  if (!c) return A2_ENOMEM;
+  a2_status st = guarded(c, [&] {
+    A2_CUDA(cudaSetDevice(device));
+    c->device = device;
+    if (cuda_stream) {
+      c->stream = (cudaStream_t)cuda_stream;
+    } else {
+      A2_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+      c->own_stream = true;
+    }
+    cudaMemPool_t pool;
+    A2_CUDA(cudaDeviceGetDefaultMemPool(&pool, device));
+    uint64_t thr = UINT64_MAX;
+    A2_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    c->solver.init(c->stream);
+    c->scal.ensure(sizeof(double) * 16384, c->stream);
+    c->partial.ensure(sizeof(double) * kReduceBlocks * 64, c->stream);
+    A2_CUDA(cudaMallocHost(&c->h_scal, sizeof(double) * 64));
+    A2_CUDA(cudaStreamSynchronize(c->stream));
+  });
+  if (st != A2_OK) {
+    fprintf(stderr, "a2_ctx_create: %s\n", c->err.c_str());
+    delete c;
+    return st;
+  }
+  *out = c;
+  return A2_OK;
+}
+
+a2_status a2_ctx_destroy(a2_ctx* c) {
+  if (!c) return A2_EINVAL;
+  cudaStreamSynchronize(c->stream);
+  c->solver.destroy();
+  for (DevBuf* b : {&c->scal, &c->partial, &c->t1, &c->t2, &c->t3, &c->xa, &c->ya, &c->cb, &c->ck,
+                    &c->gram, &c->wv, &c->tmp1, &c->tmp2})
+    b->release();
+  cudaStreamSynchronize(c->stream);
+  if (c->h_scal) cudaFreeHost(c->h_scal);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return A2_OK;
+}
+
+const char* a2_last_error(const a2_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+a2_status a2_ctx_synchronize(a2_ctx* c) {
+  if (!c) return A2_EINVAL;
+  return guarded(c, [&] { A2_CUDA(cudaStreamSynchronize(c->stream)); });
+}
+
+a2_status a2_tt_create(a2_ctx* c, int L, const int* phys, const int* bonds, uint64_t seed,
+                       a2_tt** out) {
+  if (!c || !out || !phys || L < 2) return c ? fail(c, A2_EINVAL, "a2_tt_create: bad arguments") : A2_EINVAL;
+  *out = nullptr;
+  auto* t = new (std::nothrow) a2_tt();
+  if (!t) return A2_ENOMEM;
+  a2_status st = guarded(c, [&] {
+    t->ctx = c;
+    t->L = L;
+    t->phys.assign(phys, phys + L);
+    for (int n : t->phys) A2_REQUIRE(n >= 1, "physical dims must be >= 1");
+    t->dims.assign(L + 1, 1);
+    for (int k = 1; k < L; ++k) {
+      double left = 1, right = 1;
+      for (int j = 0; j < k; ++j) left *= phys[j];
+      for (int j = k; j < L; ++j) right *= phys[j];
+      double cap = std::min(left, right);
+      const int want = bonds ? bonds[k - 1] : 1;
+      A2_REQUIRE(want >= 1, "bond dims must be >= 1");
+      t->dims[k] = (int)std::min<double>(want, cap);
+    }
+    t->cores.resize(L);
+    uint64_t state = seed;
+    for (int j = 0; j < L; ++j) {
+      const size_t nel = (size_t)t->dims[j] * phys[j] * t->dims[j + 1];
+      std::vector<double> h(nel);
+      for (size_t e = 0; e < nel; ++e) {
+        const uint64_t z = splitmix_next(state);
+        h[e] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+      }
+      upload(t->cores[j], h.data(), sizeof(double) * nel, c->stream);
+      A2_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    left_orthogonalize(t, nullptr);
+    A2_CUDA(cudaStreamSynchronize(c->stream));
+  });
+  if (st != A2_OK) { delete t; return st; }
+  *out = t;
+  return A2_OK;
+}
+
+a2_status a2_tt_set_core(a2_tt* t, int site, int Dl, int n, int Dr, const double* h) {
+  if (!t) return A2_EINVAL;
+  a2_ctx* c = t->ctx;
+  return guarded(c, [&] {
+    A2_REQUIRE(site >= 0 && site < t->L && h, "a2_tt_set_core: bad site or pointer");
+    A2_REQUIRE(n == t->phys[site] && Dl >= 1 && Dr >= 1, "a2_tt_set_core: bad dims");
+    A2_REQUIRE(site > 0 || Dl == 1, "first core must have Dl = 1");
+    A2_REQUIRE(site < t->L - 1 || Dr == 1, "last core must have Dr = 1");
+    const size_t nel = (size_t)Dl * n * Dr;
+    t->cores[site].release();
+    upload(t->cores[site], h, sizeof(double) * nel, c->stream);
+    A2_CUDA(cudaStreamSynchronize(c->stream));
+    t->dims[site] = Dl;
+    t->dims[site + 1] = Dr;
+  });
+}
+
+a2_status a2_tt_get_core(const a2_tt* t, int site, int* Dl, int* n, int* Dr, double* h) {
+  if (!t) return A2_EINVAL;
+  a2_ctx* c = t->ctx;
+  return guarded(c, [&] {
+    A2_REQUIRE(site >= 0 && site < t->L, "a2_tt_get_core: bad site");
+    if (Dl) *Dl = t->dims[site];
+    if (n) *n = t->phys[site];
+    if (Dr) *Dr = t->dims[site + 1];
+    if (h) {
+      const size_t nel = (size_t)t->dims[site] * t->phys[site] * t->dims[site + 1];
+      A2_CUDA(cudaMemcpyAsync(h, t->cores[site].p, sizeof(double) * nel, cudaMemcpyDeviceToHost,
+                              c->stream));
+      A2_CUDA(cudaStreamSynchronize(c->stream));
+    }
+  });
+}
+
+a2_status a2_tt_left_orthogonalize(a2_tt* t, double* norm_out) {
+  if (!t) return A2_EINVAL;
+  return guarded(t->ctx, [&] {
+    for (int j = 0; j + 1 < t->L; ++j) {
+      A2_REQUIRE(t->cores[j].bytes >= sizeof(double) * (size_t)t->dims[j] * t->phys[j] * t->dims[j + 1],
+                 "inconsistent TT bond dims");
+    }
+    tt_check(t);
+    left_orthogonalize(t, norm_out);
+    A2_CUDA(cudaStreamSynchronize(t->ctx->stream));
+  });
+}
+
+a2_status a2_tt_destroy(a2_tt* t) {
+  if (!t) return A2_EINVAL;
+  cudaStreamSynchronize(t->ctx->stream);
+  delete t;
+  return A2_OK;
+}
+
+a2_status a2_mpo_load(a2_ctx* c, int L, const int* phys, const int* R, const double* const* cores,
+                      a2_mpo** out) {
+  if (!c || !out) return A2_EINVAL;
+  *out = nullptr;
+  auto* m = new (std::nothrow) a2_mpo();
+  if (!m) return A2_ENOMEM;
+  a2_status st = guarded(c, [&] {
+    A2_REQUIRE(L >= 2 && phys && R && cores, "a2_mpo_load: bad arguments");
+    A2_REQUIRE(R[0] == 1 && R[L] == 1, "MPO boundary bonds must be 1");
+    m->ctx = c;
+    m->L = L;
+    m->phys.assign(phys, phys + L);
+    m->R.assign(R, R + L + 1);
+    m->site.resize(L);
+    for (int j = 0; j < L; ++j) {
+      A2_REQUIRE(cores[j] && R[j] >= 1 && R[j + 1] >= 1 && phys[j] >= 1, "a2_mpo_load: bad core");
+      build_site(m->site[j], cores[j], R[j], phys[j], R[j + 1], c->stream);
+    }
+    A2_CUDA(cudaStreamSynchronize(c->stream));
+  });
+  if (st != A2_OK) { delete m; return st; }
+  *out = m;
+  return A2_OK;
+}
+
+a2_status a2_mpo_nnz(const a2_mpo* m, int site, long long* nnz) {
+  if (!m || !nnz || site < 0 || site >= m->L) return A2_EINVAL;
+  *nnz = m->site[site].nnz;
+  return A2_OK;
+}
+
+a2_status a2_mpo_destroy(a2_mpo* m) {
+  if (!m) return A2_EINVAL;
+  cudaStreamSynchronize(m->ctx->stream);
+  delete m;
+  return A2_OK;
+}
+
+static a2_status run_sweep(a2_ctx* c, a2_tt* t, const a2_mpo* m, const a2_sweep_opts* o,
+                           a2_sweep_report* rep, bool classical) {
+  if (!c || !t || !m || !o) return c ? fail(c, A2_EINVAL, "null argument") : A2_EINVAL;
+  // keep the iterate until the iteration succeeds (Alg. 2 saves U^(n),d)
+  std::vector<DevBuf> saved;
+  std::vector<int> saved_dims = t->dims;
+  a2_status st = guarded(c, [&] {
+    A2_REQUIRE(t->ctx == c && m->L == t->L, "handles from different contexts / sizes");
+    saved.resize(t->L);
+    for (int j = 0; j < t->L; ++j) {
+      saved[j].ensure(t->cores[j].bytes, c->stream);
+      A2_CUDA(cudaMemcpyAsync(saved[j].p, t->cores[j].p, t->cores[j].bytes,
+                              cudaMemcpyDeviceToDevice, c->stream));
+    }
+    if (o->prec == A2_FP64) {
+      Sweeper<double> sw(c, t, m, *o);
+      sw.run(rep, classical);
+    } else if (o->prec == A2_FP32 || o->prec == A2_BF16) {
+      if (o->prec == A2_BF16 && !tc_available())
+        throw ArgError("A2_BF16 needs the tcgen05 path, which this build lacks");
+      Sweeper<float> sw(c, t, m, *o);
+      sw.run(rep, classical);
+    } else {
+      throw ArgError("unsupported precision");
+    }
+  });
+  if (st != A2_OK) {
+    for (int j = 0; j < t->L && j < (int)saved.size(); ++j)
+      if (saved[j].p) t->cores[j] = std::move(saved[j]);
+    t->dims = saved_dims;
+    cudaStreamSynchronize(c->stream);
+  }
+  return st;
+}
+
+a2_status a2_additive_sweep(a2_ctx* c, a2_tt* t, const a2_mpo* m, const a2_sweep_opts* o,
+                            a2_sweep_report* rep) {
+  return run_sweep(c, t, m, o, rep, false);
+}
+
+a2_status a2_classical_sweep(a2_ctx* c, a2_tt* t, const a2_mpo* m, const a2_sweep_opts* o,
+                             a2_sweep_report* rep) {
+  return run_sweep(c, t, m, o, rep, true);
+}
+
+a2_status a2_coarse_solve(a2_ctx* c, int m, const double* A, const double* S, double eps,
+                          double* c_out, double* lam_out, int* rank_out) {
+  if (!c) return A2_EINVAL;
+  return guarded(c, [&] {
+    A2_REQUIRE(m >= 1 && m <= 63 && A && S && c_out && lam_out, "a2_coarse_solve: bad arguments");
+    cudaStream_t s = c->stream;
+    double* dA = scal(c, 9000);
+    double* dS = dA + m * m;
+    double* dc = dS + m * m;
+    double* dl = dc + m;
+    int* drk = reinterpret_cast<int*>(dl + 1);
+    A2_CUDA(cudaMemcpyAsync(dA, A, sizeof(double) * m * m, cudaMemcpyHostToDevice, s));
+    A2_CUDA(cudaMemcpyAsync(dS, S, sizeof(double) * m * m, cudaMemcpyHostToDevice, s));
+    coarse_solve_dev(dA, dS, m, eps, dc, dl, drk, drk + 1, s);
+    int rk[2];
+    A2_CUDA(cudaMemcpyAsync(c_out, dc, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+    A2_CUDA(cudaMemcpyAsync(lam_out, dl, sizeof(double), cudaMemcpyDeviceToHost, s));
+    A2_CUDA(cudaMemcpyAsync(rk, drk, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+    A2_CUDA(cudaStreamSynchronize(s));
+    if (rank_out) *rank_out = rk[0];
+    if (rk[1] != 0) throw NumericError("coarse Jacobi did not converge");
+  });
+}
+
+a2_status a2_energy(a2_ctx* c, const a2_tt* t, const a2_mpo* m, a2_precision prec, double* E,
+                    double* norm_out) {
+  if (!c || !t || !m || !E) return c ? fail(c, A2_EINVAL, "null argument") : A2_EINVAL;
+  return guarded(c, [&] {
+    tt_check(t);
+    A2_REQUIRE(t->phys == m->phys, "TT and MPO physical dims differ");
+    if (prec == A2_FP64) *E = energy_T<double>(c, t, m, norm_out);
+    else *E = energy_T<float>(c, t, m, norm_out);
+  });
+}
+
+a2_status a2_heff_apply(a2_ctx* c, const a2_mpo* m, int k, a2_precision prec, int Dl, int Dr,
+                        const double* L, const double* R, const double* x, double* y) {
+  if (!c || !m) return A2_EINVAL;
+  return guarded(c, [&] {
+    A2_REQUIRE(k >= 0 && k + 1 < m->L && Dl >= 1 && Dr >= 1 && L && R && x && y,
+               "a2_heff_apply: bad arguments");
+    const SiteOps& A1 = m->site[k];
+    const SiteOps& A2 = m->site[k + 1];
+    cudaStream_t s = c->stream;
+    if (prec == A2_FP64) {
+      heff_T<double>(c, A1, A2, L, R, Dl, Dr, x, y);
+    } else if (prec == A2_FP32) {
+      const long long nl = (long long)Dl * A1.Rl * Dl, nr = (long long)Dr * A2.Rr * Dr;
+      const long long N = (long long)Dl * A1.n * A2.n * Dr;
+      c->cb.ensure(sizeof(float) * (nl + nr), s);
+      float* Lf = c->cb.as<float>();
+      float* Rf = Lf + nl;
+      convert<double, float>(L, Lf, nl, s);
+      convert<double, float>(R, Rf, nr, s);
+      c->xa.ensure(sizeof(float) * N, s);
+      c->ya.ensure(sizeof(float) * N, s);
+      convert<double, float>(x, c->xa.as<float>(), N, s);
+      heff_T<float>(c, A1, A2, Lf, Rf, Dl, Dr, c->xa.as<float>(), c->ya.as<float>());
+      convert<float, double>(c->ya.as<float>(), y, N, s);
+    } else if (prec == A2_BF16) {
+      A2_REQUIRE(tc_available(), "A2_BF16 needs the tcgen05 path");
+      tc_heff_apply(c->stream, A1.n, A2.n, A1.Rl, A1.Rr, A2.Rr, Dl, Dr, L, R, x, y,
+                    A1.lr.rows<float>(), A2.lr.rows<float>(), c->t1, c->t2, c->t3, c->xa, c->ya,
+                    c->cb);
+    } else {
+      throw ArgError("unsupported precision");
+    }
+  });
+}
+
+a2_status a2_env_update(a2_ctx* c, const a2_mpo* m, int j, int side, a2_precision prec, int Dlb,
+                        int Drb, int Dlk, int Drk, const double* in, const double* bra,
+                        const double* ket, double* out) {
+  if (!c || !m) return A2_EINVAL;
+  return guarded(c, [&] {
+    A2_REQUIRE(j >= 0 && j < m->L && (side == 0 || side == 1) && in && bra && ket && out,
+               "a2_env_update: bad arguments");
+    const SiteOps& so = m->site[j];
+    cudaStream_t s = c->stream;
+    const int n = so.n;
+    if (prec == A2_FP64) {
+      if (side == 0) env_left<double>(c, so, in, bra, Dlb, Drb, ket, Dlk, Drk, out);
+      else env_right<double>(c, so, in, bra, Dlb, Drb, ket, Dlk, Drk, out);
+    } else {
+      const long long nin = side == 0 ? (long long)Dlb * so.Rl * Dlk : (long long)Drb * so.Rr * Drk;
+      const long long nout = side == 0 ? (long long)Drb * so.Rr * Drk : (long long)Dlb * so.Rl * Dlk;
+      const long long nb = (long long)Dlb * n * Drb, nk = (long long)Dlk * n * Drk;
+      c->cb.ensure(sizeof(float) * (nin + nout + nb + nk), s);
+      float* fi = c->cb.as<float>();
+      float* fo = fi + nin;
+      float* fb = fo + nout;
+      float* fk = fb + nb;
+      convert<double, float>(in, fi, nin, s);
+      convert<double, float>(bra, fb, nb, s);
+      convert<double, float>(ket, fk, nk, s);
+      if (side == 0) env_left<float>(c, so, fi, fb, Dlb, Drb, fk, Dlk, Drk, fo);
+      else env_right<float>(c, so, fi, fb, Dlb, Drb, fk, Dlk, Drk, fo);
+      convert<float, double>(fo, out, nout, s);
+    }
+  });
+}
+
+a2_status a2_svd_split(a2_ctx* c, int Dl, int n1, int n2, int Dr, const double* x, int D_max,
+                       double tol, double* P_out, double* SQ_out, int* rank_out,
+                       double* discarded_out) {
+  if (!c) return A2_EINVAL;
+  return guarded(c, [&] {
+    A2_REQUIRE(Dl >= 1 && n1 >= 1 && n2 >= 1 && Dr >= 1 && x && P_out && SQ_out && rank_out &&
+                   D_max >= 1,
+               "a2_svd_split: bad arguments");
+    double disc = 0.0;
+    const int r = svd_split_dev(c, x, Dl * n1, n2 * Dr, D_max, tol, P_out, SQ_out, &disc);
+    A2_CUDA(cudaStreamSynchronize(c->stream));
+    *rank_out = r;
+    if (discarded_out) *discarded_out = disc;
+  });
+}
+
+}  // extern "C"

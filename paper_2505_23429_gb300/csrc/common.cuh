@@ -1,0 +1,73 @@
+// Shared device/host helpers for the A2DMRG library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <stdexcept>
+
+namespace a2 {
+
+struct CudaError : std::runtime_error {
+  explicit CudaError(const std::string& s) : std::runtime_error(s) {}
+};
+struct ArgError : std::runtime_error {
+  explicit ArgError(const std::string& s) : std::runtime_error(s) {}
+};
+struct NumericError : std::runtime_error {
+  explicit NumericError(const std::string& s) : std::runtime_error(s) {}
+};
+
+#define A2_CUDA(expr)                                                              \
+  do {                                                                             \
+    cudaError_t e__ = (expr);                                                      \
+    if (e__ != cudaSuccess)                                                        \
+      throw ::a2::CudaError(std::string(#expr) + ": " + cudaGetErrorString(e__) +  \
+                            " at " + __FILE__ + ":" + std::to_string(__LINE__));   \
+  } while (0)
+
+#define A2_CHECK_LAUNCH() A2_CUDA(cudaGetLastError())
+
+#define A2_REQUIRE(cond, msg)                                                      \
+  do {                                                                             \
+    if (!(cond)) throw ::a2::ArgError(std::string(msg));                           \
+  } while (0)
+
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Stream-ordered device buffer (cudaMallocAsync pool).
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t s = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept { *this = std::move(o); }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) {
+      release();
+      p = o.p; bytes = o.bytes; s = o.s;
+      o.p = nullptr; o.bytes = 0;
+    }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+    bytes = 0;
+  }
+  void ensure(size_t nbytes, cudaStream_t stream) {
+    if (nbytes <= bytes && p) return;
+    release();
+    s = stream;
+    size_t nb = nbytes ? nbytes : 16;
+    A2_CUDA(cudaMallocAsync(&p, nb, stream));
+    bytes = nb;
+  }
+  template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+}  // namespace a2

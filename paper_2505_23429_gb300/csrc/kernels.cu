@@ -1,0 +1,708 @@
+// SIMT GEMM, sparse MPO action, vector and small dense kernels (sm_103a).
+#include "kernels.cuh"
+
+namespace a2 {
+
+// ----------------------------------------------------------------------------- SIMT GEMM
+template <typename T, typename OutT, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+simt_gemm_kernel(SimtGemm<T, OutT> g) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  constexpr int GX = BN / TN;            // threads along n
+  constexpr int GY = BM / TM;            // threads along m
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid % GX, ty = tid / GX;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int z = blockIdx.z;
+  const int b = z / g.splitk, sk = z % g.splitk;
+  const T* A = g.A + (long long)b * g.abs;
+  const T* B = g.B + (long long)b * g.bbs;
+  OutT* C = g.C + (long long)b * g.cbs;
+  const int kchunk = ((g.K + g.splitk - 1) / g.splitk + BK - 1) / BK * BK;
+  const int kbeg = sk * kchunk;
+  const int kend = min(g.K, kbeg + kchunk);
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+  const bool a_kfast = (g.sak == 1);
+  const bool b_kfast = (g.sbk == 1);
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+#pragma unroll
+    for (int e = tid; e < BM * BK; e += NT) {
+      int mm, kk;
+      if (a_kfast) { mm = e / BK; kk = e % BK; } else { kk = e / BM; mm = e % BM; }
+      const int m = m0 + mm, k = k0 + kk;
+      As[kk][mm] = (m < g.M && k < kend) ? A[(long long)m * g.sam + (long long)k * g.sak] : T(0);
+    }
+#pragma unroll
+    for (int e = tid; e < BN * BK; e += NT) {
+      int nn, kk;
+      if (b_kfast) { nn = e / BK; kk = e % BK; } else { kk = e / BN; nn = e % BN; }
+      const int n = n0 + nn, k = k0 + kk;
+      Bs[kk][nn] = (n < g.N && k < kend) ? B[(long long)n * g.sbn + (long long)k * g.sbk] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[TM], bb[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + i * GY];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) bb[j] = Bs[kk][tx + j * GX];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int m = m0 + ty + i * GY;
+    if (m >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int n = n0 + tx + j * GX;
+      if (n >= g.N) continue;
+      OutT* p = C + (long long)m * g.scm + (long long)n * g.scn;
+      const OutT v = (OutT)(g.alpha * acc[i][j]);
+      if (g.mode == GEMM_STORE) *p = v;
+      else if (g.mode == GEMM_ADD) *p += v;
+      else atomicAdd(p, v);
+    }
+  }
+}
+
+template <typename T, typename OutT>
+void simt_gemm(const SimtGemm<T, OutT>& g, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
+  A2_REQUIRE(g.splitk == 1 || g.mode == GEMM_ATOMIC, "split-K needs atomic mode");
+  if constexpr (sizeof(T) == 8) {
+    constexpr int BM = 64, BN = 64, BK = 8, TM = 4, TN = 4;
+    dim3 grid(cdiv(g.N, BN), cdiv(g.M, BM), g.batch * g.splitk);
+    A2_REQUIRE(grid.y < 65536 && grid.z < 65536, "GEMM grid too large");
+    simt_gemm_kernel<T, OutT, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, s>>>(g);
+  } else {
+    constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;
+    dim3 grid(cdiv(g.N, BN), cdiv(g.M, BM), g.batch * g.splitk);
+    A2_REQUIRE(grid.y < 65536 && grid.z < 65536, "GEMM grid too large");
+    simt_gemm_kernel<T, OutT, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, s>>>(g);
+  }
+  A2_CHECK_LAUNCH();
+}
+
+template void simt_gemm<double, double>(const SimtGemm<double, double>&, cudaStream_t);
+template void simt_gemm<float, float>(const SimtGemm<float, float>&, cudaStream_t);
+template void simt_gemm<float, double>(const SimtGemm<float, double>&, cudaStream_t);
+
+// ----------------------------------------------------------------------------- sparse MPO action
+template <typename T> __device__ __forceinline__ float to_f(T x) { return (float)x; }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x) {
+  return __bfloat162float(x);
+}
+template <typename T> struct AccT { using type = float; };
+template <> struct AccT<double> { using type = double; };
+
+template <typename TO, typename A> __device__ __forceinline__ TO from_acc(A x) { return (TO)x; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_acc<__nv_bfloat16, float>(float x) {
+  return __float2bfloat16_rn(x);
+}
+template <typename A, typename TI> __device__ __forceinline__ A load_as(const TI* p) {
+  return (A)(*p);
+}
+template <> __device__ __forceinline__ float load_as<float, __nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(*p);
+}
+
+template <typename TI, typename TO, typename V>
+__global__ void sparse_rows_kernel(SparseRows<V> sp, SparseGeom g, const TI* __restrict__ in,
+                                   TO* __restrict__ out, int rows_per_cta) {
+  using Acc = typename AccT<TO>::type;
+  const int r0 = blockIdx.x * rows_per_cta;
+  const int bz = blockIdx.y;
+  const int b1 = bz / g.B2, b2 = bz % g.B2;
+  const long long ib = b1 * g.in_b1 + b2 * g.in_b2;
+  const long long ob = b1 * g.out_b1 + b2 * g.out_b2;
+  const int nr = min(rows_per_cta, sp.nrows - r0);
+  const int items = nr * g.veclen;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int r = r0 + it / g.veclen;
+    const int v = it % g.veclen;
+    Acc acc = Acc(0);
+    const int e1 = sp.row_ptr[r + 1];
+    for (int e = sp.row_ptr[r]; e < e1; ++e) {
+      const long long ci = sp.nz_w[e] * g.in_sw + sp.nz_t[e] * g.in_st;
+      acc += (Acc)sp.nz_val[e] * load_as<Acc, TI>(in + ib + ci + v);
+    }
+    const long long ro = sp.row_w[r] * g.out_sw + sp.row_s[r] * g.out_ss;
+    out[ob + ro + v] = from_acc<TO, Acc>(acc);
+  }
+}
+
+template <typename TI, typename TO, typename V>
+void sparse_rows_apply(const SparseRows<V>& sp, const SparseGeom& g, const TI* in, TO* out,
+                       cudaStream_t s) {
+  if (sp.nrows == 0 || g.veclen == 0) return;
+  int rows = max(1, 2048 / g.veclen);
+  rows = min(rows, 64);
+  dim3 grid(cdiv(sp.nrows, rows), g.B1 * g.B2);
+  A2_REQUIRE(grid.y < 65536, "sparse grid too large");
+  sparse_rows_kernel<TI, TO, V><<<grid, 256, 0, s>>>(sp, g, in, out, rows);
+  A2_CHECK_LAUNCH();
+}
+
+template void sparse_rows_apply<double, double, double>(const SparseRows<double>&,
+                                                        const SparseGeom&, const double*,
+                                                        double*, cudaStream_t);
+template void sparse_rows_apply<float, float, float>(const SparseRows<float>&, const SparseGeom&,
+                                                     const float*, float*, cudaStream_t);
+template void sparse_rows_apply<__nv_bfloat16, __nv_bfloat16, float>(
+    const SparseRows<float>&, const SparseGeom&, const __nv_bfloat16*, __nv_bfloat16*,
+    cudaStream_t);
+template void sparse_rows_apply<__nv_bfloat16, float, float>(const SparseRows<float>&,
+                                                             const SparseGeom&,
+                                                             const __nv_bfloat16*, float*,
+                                                             cudaStream_t);
+template void sparse_rows_apply<float, __nv_bfloat16, float>(const SparseRows<float>&,
+                                                             const SparseGeom&, const float*,
+                                                             __nv_bfloat16*, cudaStream_t);
+
+// ----------------------------------------------------------------------------- permutes
+template <typename TI, typename TO>
+__global__ void permute_swap01_kernel(const TI* in, TO* out, int d0, int d1, int d2) {
+  const long long n = (long long)d0 * d1 * d2;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e % d2);
+    const long long ij = e / d2;
+    const int j = (int)(ij % d1);
+    const int i = (int)(ij / d1);
+    out[e] = (TO)in[((long long)j * d0 + i) * d2 + k];
+  }
+}
+
+template <typename TI, typename TO>
+__global__ void convert_kernel(const TI* in, TO* out, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = (TO)in[e];
+}
+template <>
+__global__ void convert_kernel<double, __nv_bfloat16>(const double* in, __nv_bfloat16* out,
+                                                      long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = __double2bfloat16(in[e]);
+}
+template <>
+__global__ void convert_kernel<float, __nv_bfloat16>(const float* in, __nv_bfloat16* out,
+                                                     long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = __float2bfloat16_rn(in[e]);
+}
+
+template <typename TI, typename TO>
+__global__ void transpose_kernel(const TI* in, TO* out, int rows, int cols) {
+  __shared__ float tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int r = by + j, c = bx + threadIdx.x;
+    if (r < rows && c < cols) tile[j][threadIdx.x] = (float)in[(long long)r * cols + c];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int c = bx + j, r = by + threadIdx.x;
+    if (r < rows && c < cols) out[(long long)c * rows + r] = (TO)tile[threadIdx.x][j];
+  }
+}
+template <>
+__global__ void transpose_kernel<double, double>(const double* in, double* out, int rows,
+                                                 int cols) {
+  __shared__ double tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int r = by + j, c = bx + threadIdx.x;
+    if (r < rows && c < cols) tile[j][threadIdx.x] = in[(long long)r * cols + c];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int c = bx + j, r = by + threadIdx.x;
+    if (r < rows && c < cols) out[(long long)c * rows + r] = tile[threadIdx.x][j];
+  }
+}
+template <>
+__global__ void transpose_kernel<double, __nv_bfloat16>(const double* in, __nv_bfloat16* out,
+                                                        int rows, int cols) {
+  __shared__ double tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int r = by + j, c = bx + threadIdx.x;
+    if (r < rows && c < cols) tile[j][threadIdx.x] = in[(long long)r * cols + c];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int c = bx + j, r = by + threadIdx.x;
+    if (r < rows && c < cols)
+      out[(long long)c * rows + r] = __double2bfloat16(tile[threadIdx.x][j]);
+  }
+}
+
+static int grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  return (int)(g < 4096 ? (g > 0 ? g : 1) : 4096);
+}
+
+template <typename TI, typename TO>
+void permute_swap01(const TI* in, TO* out, int d0, int d1, int d2, cudaStream_t s) {
+  long long n = (long long)d0 * d1 * d2;
+  if (!n) return;
+  permute_swap01_kernel<TI, TO><<<grid_for(n), 256, 0, s>>>(in, out, d0, d1, d2);
+  A2_CHECK_LAUNCH();
+}
+template <typename TI, typename TO>
+void convert(const TI* in, TO* out, long long n, cudaStream_t s) {
+  if (!n) return;
+  convert_kernel<TI, TO><<<grid_for(n), 256, 0, s>>>(in, out, n);
+  A2_CHECK_LAUNCH();
+}
+template <typename TI, typename TO>
+void transpose2d(const TI* in, TO* out, int rows, int cols, cudaStream_t s) {
+  if (!rows || !cols) return;
+  dim3 grid(cdiv(cols, 32), cdiv(rows, 32));
+  A2_REQUIRE(grid.y < 65536, "transpose grid too large");
+  transpose_kernel<TI, TO><<<grid, dim3(32, 8), 0, s>>>(in, out, rows, cols);
+  A2_CHECK_LAUNCH();
+}
+template void permute_swap01<double, double>(const double*, double*, int, int, int, cudaStream_t);
+template void permute_swap01<float, float>(const float*, float*, int, int, int, cudaStream_t);
+template void permute_swap01<double, float>(const double*, float*, int, int, int, cudaStream_t);
+template void convert<double, float>(const double*, float*, long long, cudaStream_t);
+template void convert<float, double>(const float*, double*, long long, cudaStream_t);
+template void convert<double, __nv_bfloat16>(const double*, __nv_bfloat16*, long long, cudaStream_t);
+template void convert<float, __nv_bfloat16>(const float*, __nv_bfloat16*, long long, cudaStream_t);
+template void transpose2d<double, double>(const double*, double*, int, int, cudaStream_t);
+template void transpose2d<double, float>(const double*, float*, int, int, cudaStream_t);
+template void transpose2d<double, __nv_bfloat16>(const double*, __nv_bfloat16*, int, int,
+                                                 cudaStream_t);
+
+// ----------------------------------------------------------------------------- vector kernels
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// partial[j * kReduceBlocks + block] = sum over the block's grid-stride slice of V_j . w
+__global__ void dot_multi_partial(const double* __restrict__ V, long long ldv, int k,
+                                  const double* __restrict__ w, long long n,
+                                  double* __restrict__ partial) {
+  __shared__ double red[8][64];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int j0 = 0; j0 < k; j0 += 8) {
+    const int jn = min(8, k - j0);
+    double acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+      const double wi = w[i];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q < jn) acc[q] = fma(V[(long long)(j0 + q) * ldv + i], wi, acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      double v = warp_sum(acc[q]);
+      if (lane == 0) red[q][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < jn) {
+      double t = 0.0;
+      for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t += red[threadIdx.x][ww];
+      partial[(long long)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void reduce_partials(const double* __restrict__ partial, int nb, int k,
+                                double* __restrict__ out) {
+  const int j = blockIdx.x;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += partial[(long long)j * nb + b];
+  __shared__ double red[32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    out[j] = t;
+  }
+}
+
+void dot_multi(const double* V, long long ldv, int k, const double* w, long long n,
+               double* partial, double* out, cudaStream_t s) {
+  if (k <= 0) return;
+  dot_multi_partial<<<kReduceBlocks, 256, 0, s>>>(V, ldv, k, w, n, partial);
+  A2_CHECK_LAUNCH();
+  reduce_partials<<<k, 256, 0, s>>>(partial, kReduceBlocks, k, out);
+  A2_CHECK_LAUNCH();
+}
+
+__global__ void gemv_sub_kernel(const double* __restrict__ V, long long ldv, int k,
+                                const double* __restrict__ h, double* __restrict__ w,
+                                long long n, int set_mode) {
+  __shared__ double hs[64];
+  if (threadIdx.x < k) hs[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < k; ++j) acc = fma(hs[j], V[(long long)j * ldv + i], acc);
+    if (set_mode) w[i] = acc; else w[i] -= acc;
+  }
+}
+
+void gemv_sub(const double* V, long long ldv, int k, const double* h, double* w, long long n,
+              cudaStream_t s) {
+  if (k <= 0) return;
+  A2_REQUIRE(k <= 64, "at most 64 basis vectors");
+  gemv_sub_kernel<<<grid_for(n), 256, 0, s>>>(V, ldv, k, h, w, n, 0);
+  A2_CHECK_LAUNCH();
+}
+void gemv_set(const double* V, long long ldv, int k, const double* h, double* out, long long n,
+              cudaStream_t s) {
+  A2_REQUIRE(k >= 1 && k <= 64, "1..64 basis vectors");
+  gemv_sub_kernel<<<grid_for(n), 256, 0, s>>>(V, ldv, k, h, out, n, 1);
+  A2_CHECK_LAUNCH();
+}
+
+__global__ void axpby_kernel(double a, const double* x, double b, double* y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+void axpby(double a, const double* x, double b, double* y, long long n, cudaStream_t s) {
+  if (!n) return;
+  axpby_kernel<<<grid_for(n), 256, 0, s>>>(a, x, b, y, n);
+  A2_CHECK_LAUNCH();
+}
+
+__global__ void lanczos_update_kernel(double* w, const double* v, const double* vprev,
+                                      const double* alpha, double beta, long long n) {
+  const double a = *alpha;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double t = w[i] - a * v[i];
+    if (vprev) t -= beta * vprev[i];
+    w[i] = t;
+  }
+}
+void lanczos_update(double* w, const double* v, const double* vprev, const double* alpha,
+                    double beta_prev, long long n, cudaStream_t s) {
+  lanczos_update_kernel<<<grid_for(n), 256, 0, s>>>(w, v, vprev, alpha, beta_prev, n);
+  A2_CHECK_LAUNCH();
+}
+
+__global__ void normalize_kernel(const double* w, const double* nrm2, double* out, long long n) {
+  const double inv = 1.0 / sqrt(*nrm2);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = w[i] * inv;
+}
+void normalize_into(const double* w, const double* nrm2, double* out, long long n,
+                    cudaStream_t s) {
+  normalize_kernel<<<grid_for(n), 256, 0, s>>>(w, nrm2, out, n);
+  A2_CHECK_LAUNCH();
+}
+
+__global__ void scale_dev_kernel(double* x, const double* num, const double* den_sqrt,
+                                 long long n) {
+  const double f = (num ? *num : 1.0) / (den_sqrt ? sqrt(*den_sqrt) : 1.0);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] *= f;
+}
+void scale_dev(double* x, const double* num, const double* den_sqrt, long long n,
+               cudaStream_t s) {
+  scale_dev_kernel<<<grid_for(n), 256, 0, s>>>(x, num, den_sqrt, n);
+  A2_CHECK_LAUNCH();
+}
+
+// ----------------------------------------------------------------------------- Jacobi eigensolver
+// Cyclic Jacobi with the round-robin parallel ordering (Golub & Van Loan, Sec. 8.5).
+// Works in shared memory on a (me x me) padded matrix; all threads of the CTA call it.
+// On return a is (numerically) diagonal, v holds the rotations (columns = eigvecs),
+// perm[0..m-1] sorts the first m diagonal entries ascending.
+struct JacobiShared {
+  double a[64][65];
+  double v[64][65];
+  double cs[32], sn[32];
+  int pp[32], qq[32];
+  int perm[64];
+  double off, tot;
+};
+
+__device__ int jacobi_shared(JacobiShared& J, int m) {
+  const int me = (m + 1) & ~1;
+  for (int e = threadIdx.x; e < me * me; e += blockDim.x) {
+    const int i = e / me, j = e % me;
+    J.v[i][j] = (i == j) ? 1.0 : 0.0;
+    if (i >= m || j >= m) J.a[i][j] = 0.0;
+  }
+  __syncthreads();
+  int sweep = 0;
+  const int max_sweeps = 60;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) {
+      double off = 0.0, tot = 0.0;
+      for (int i = 0; i < me; ++i)
+        for (int j = 0; j < me; ++j) {
+          tot += J.a[i][j] * J.a[i][j];
+          if (i != j) off += J.a[i][j] * J.a[i][j];
+        }
+      J.off = off;
+      J.tot = tot;
+    }
+    __syncthreads();
+    if (J.off <= 1e-30 * J.tot || J.off == 0.0) break;
+    for (int step = 0; step < me - 1; ++step) {
+      if (threadIdx.x < me / 2) {
+        const int t = threadIdx.x;
+        const int p0 = (t == 0) ? 0 : 1 + (t - 1 + step) % (me - 1);
+        const int tq = me - 1 - t;
+        const int q0 = (tq == 0) ? 0 : 1 + (tq - 1 + step) % (me - 1);
+        const int p = p0 < q0 ? p0 : q0, q = p0 < q0 ? q0 : p0;
+        J.pp[t] = p;
+        J.qq[t] = q;
+        const double apq = J.a[p][q];
+        double c = 1.0, s = 0.0;
+        if (apq != 0.0) {
+          const double tau = (J.a[q][q] - J.a[p][p]) / (2.0 * apq);
+          const double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + tt * tt);
+          s = tt * c;
+        }
+        J.cs[t] = c;
+        J.sn[t] = s;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < (me / 2) * me; e += blockDim.x) {
+        const int t = e / me, j = e % me;
+        const int p = J.pp[t], q = J.qq[t];
+        const double c = J.cs[t], s = J.sn[t];
+        const double ap = J.a[p][j], aq = J.a[q][j];
+        J.a[p][j] = c * ap - s * aq;
+        J.a[q][j] = s * ap + c * aq;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < (me / 2) * me; e += blockDim.x) {
+        const int t = e / me, i = e % me;
+        const int p = J.pp[t], q = J.qq[t];
+        const double c = J.cs[t], s = J.sn[t];
+        const double ap = J.a[i][p], aq = J.a[i][q];
+        J.a[i][p] = c * ap - s * aq;
+        J.a[i][q] = s * ap + c * aq;
+        const double vp = J.v[i][p], vq = J.v[i][q];
+        J.v[i][p] = c * vp - s * vq;
+        J.v[i][q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) {
+    // the padding index (odd m) never rotates: its column stays e_m; skip it
+    for (int i = 0; i < m; ++i) J.perm[i] = i;
+    for (int i = 0; i < m; ++i)
+      for (int j = i + 1; j < m; ++j)
+        if (J.a[J.perm[j]][J.perm[j]] < J.a[J.perm[i]][J.perm[i]]) {
+          int x = J.perm[i]; J.perm[i] = J.perm[j]; J.perm[j] = x;
+        }
+  }
+  __syncthreads();
+  return sweep < max_sweeps ? sweep : -1;
+}
+
+__global__ void jacobi_kernel(double* A, int m, double* evals, double* evecs, int* status) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  JacobiShared& J = *reinterpret_cast<JacobiShared*>(dyn_smem);
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e % m;
+    J.a[i][j] = 0.5 * (A[i * m + j] + A[j * m + i]);
+  }
+  __syncthreads();
+  const int sw = jacobi_shared(J, m);
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int j = e / m, i = e % m;
+    evecs[j * m + i] = J.v[i][J.perm[j]];
+  }
+  if (threadIdx.x < m) evals[threadIdx.x] = J.a[J.perm[threadIdx.x]][J.perm[threadIdx.x]];
+  if (threadIdx.x == 0) status[0] = sw;
+}
+
+void jacobi_eig(double* A, int m, double* evals, double* evecs, int* status, cudaStream_t s) {
+  A2_REQUIRE(m >= 1 && m <= 63, "jacobi_eig: 1 <= m <= 63");
+  static bool attr = false;
+  if (!attr) {
+    A2_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(JacobiShared)));
+    attr = true;
+  }
+  jacobi_kernel<<<1, 256, sizeof(JacobiShared), s>>>(A, m, evals, evecs, status);
+  A2_CHECK_LAUNCH();
+}
+
+// Coarse problem of Sec. 3.1 in one CTA:  S = V diag(sig) V^T, keep sig > eps*max,
+// M = Sig+^{-1/2} V+^T A V+ Sig+^{-1/2}, lowest eigpair (lam, z), c = V+ Sig+^{-1/2} z,
+// sign: c_0 >= 0 (else the largest |c_j| positive).
+struct CoarseShared {
+  JacobiShared J;
+  double Ws[64][65];   // V+ Sig+^{-1/2}  (m x p)
+  double As[64][65];
+  int keep[64];
+  int p;
+};
+
+__global__ void coarse_kernel(const double* A, const double* S, int m, double eps, double* c,
+                              double* lam, int* rank, int* status) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  CoarseShared& C = *reinterpret_cast<CoarseShared*>(dyn_smem);
+  JacobiShared& J = C.J;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e % m;
+    J.a[i][j] = 0.5 * (S[i * m + j] + S[j * m + i]);
+    C.As[i][j] = 0.5 * (A[i * m + j] + A[j * m + i]);
+  }
+  __syncthreads();
+  const int sw1 = jacobi_shared(J, m);
+  if (threadIdx.x == 0) {
+    double smax = 0.0;
+    for (int i = 0; i < m; ++i) smax = fmax(smax, J.a[i][i]);
+    int p = 0;
+    for (int j = 0; j < m; ++j) {       // ascending order of eigenvalues
+      const int col = J.perm[j];
+      if (J.a[col][col] > eps * smax) C.keep[p++] = col;
+    }
+    C.p = p;
+  }
+  __syncthreads();
+  const int p = C.p;
+  for (int e = threadIdx.x; e < m * p; e += blockDim.x) {
+    const int i = e / p, k = e % p;
+    const int col = C.keep[k];
+    C.Ws[i][k] = J.v[i][col] / sqrt(J.a[col][col]);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * p; e += blockDim.x) {   // T = A Ws (m x p) into J.v
+    const int i = e / p, k = e % p;
+    double t = 0.0;
+    for (int l = 0; l < m; ++l) t += C.As[i][l] * C.Ws[l][k];
+    J.v[i][k] = t;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {   // M = Ws^T T (p x p) into As
+    const int k = e / p, l = e % p;
+    double t = 0.0;
+    for (int i = 0; i < m; ++i) t += C.Ws[i][k] * J.v[i][l];
+    C.As[k][l] = t;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int k = e / p, l = e % p;
+    J.a[k][l] = 0.5 * (C.As[k][l] + C.As[l][k]);
+  }
+  __syncthreads();
+  const int sw2 = jacobi_shared(J, p);
+  if (threadIdx.x == 0) {
+    const int col = J.perm[0];
+    double amax = 0.0;
+    int imax = 0;
+    for (int i = 0; i < m; ++i) {
+      double t = 0.0;
+      for (int k = 0; k < p; ++k) t += C.Ws[i][k] * J.v[k][col];
+      C.As[0][i] = t;
+      if (fabs(t) > amax) { amax = fabs(t); imax = i; }
+    }
+    const double ref = (fabs(C.As[0][0]) > 1e-14 * amax) ? C.As[0][0] : C.As[0][imax];
+    const double sg = ref < 0 ? -1.0 : 1.0;
+    for (int i = 0; i < m; ++i) c[i] = sg * C.As[0][i];
+    lam[0] = J.a[col][col];
+    rank[0] = p;
+    status[0] = (sw1 < 0 || sw2 < 0) ? -1 : 0;
+  }
+}
+
+void coarse_solve_dev(const double* A, const double* S, int m, double eps, double* c,
+                      double* lam, int* rank, int* status, cudaStream_t s) {
+  A2_REQUIRE(m >= 1 && m <= 63, "coarse problem: 1 <= m <= 63");
+  static bool attr = false;
+  if (!attr) {
+    A2_CUDA(cudaFuncSetAttribute(coarse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(CoarseShared)));
+    attr = true;
+  }
+  coarse_kernel<<<1, 256, sizeof(CoarseShared), s>>>(A, S, m, eps, c, lam, rank, status);
+  A2_CHECK_LAUNCH();
+}
+
+// ----------------------------------------------------------------------------- assorted
+void fill_zero(void* p, size_t bytes, cudaStream_t s) {
+  if (bytes) A2_CUDA(cudaMemsetAsync(p, 0, bytes, s));
+}
+
+// Q: rows x k column-major (ld ldq) from orgqr; R: k x k upper (col-major, ld ldr) from geqrf.
+// Flip signs so that diag(R) >= 0: column j of Q and row j of R change sign if R_jj < 0.
+__global__ void sign_fix_kernel(double* Q, int ldq, int rows, double* R, int ldr, int k) {
+  const int j = blockIdx.x;
+  const double d = R[(long long)j * ldr + j];
+  if (d >= 0.0) return;
+  for (int i = threadIdx.x; i < rows; i += blockDim.x) Q[(long long)j * ldq + i] *= -1.0;
+  for (int c = j + threadIdx.x; c < k; c += blockDim.x) R[(long long)c * ldr + j] *= -1.0;
+}
+void sign_fix_qr(double* Q, int ldq, int rows, double* R, int ldr, int k, cudaStream_t s) {
+  if (!k) return;
+  sign_fix_kernel<<<k, 128, 0, s>>>(Q, ldq, rows, R, ldr, k);
+  A2_CHECK_LAUNCH();
+}
+
+__global__ void scale_rows_kernel(double* M, int rows, int cols, const double* sv) {
+  const long long n = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    M[e] *= sv[e / cols];
+}
+void scale_rows(double* M, int rows, int cols, const double* svals, cudaStream_t s) {
+  long long n = (long long)rows * cols;
+  if (!n) return;
+  scale_rows_kernel<<<grid_for(n), 256, 0, s>>>(M, rows, cols, svals);
+  A2_CHECK_LAUNCH();
+}
+
+// dst[(o0 + i)*dst_s0 + j*dst_s1 + (o2 + k)] = alpha * src[(i*d1 + j)*d2 + k]
+__global__ void copy_block3_kernel(const double* src, int d0, int d1, int d2, double* dst,
+                                   long long s0, long long s1, int o0, int o2, double alpha) {
+  const long long n = (long long)d0 * d1 * d2;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e % d2);
+    const long long ij = e / d2;
+    const int j = (int)(ij % d1), i = (int)(ij / d1);
+    dst[(long long)(o0 + i) * s0 + (long long)j * s1 + (o2 + k)] = alpha * src[e];
+  }
+}
+void copy_block3(const double* src, int d0, int d1, int d2, double* dst, long long dst_s0,
+                 long long dst_s1, int o0, int o2, double alpha, cudaStream_t s) {
+  long long n = (long long)d0 * d1 * d2;
+  if (!n) return;
+  copy_block3_kernel<<<grid_for(n), 256, 0, s>>>(src, d0, d1, d2, dst, dst_s0, dst_s1, o0, o2,
+                                                 alpha);
+  A2_CHECK_LAUNCH();
+}
+
+}  // namespace a2

@@ -1,0 +1,97 @@
+// Device kernels of the A2DMRG hot path (declarations).
+#pragma once
+#include "common.cuh"
+
+namespace a2 {
+
+// C(m,n) {=, +=, atomic +=} alpha * sum_k A(m,k) B(n,k), general strides:
+//   A(m,k) = A[m*sam + k*sak], B(n,k) = B[n*sbn + k*sbk], C(m,n) = C[m*scm + n*scn]
+// batched over `batch` with element strides abs/bbs/cbs, optional split-K
+// (splitk > 1 requires mode == GEMM_ATOMIC and a zeroed C).
+enum GemmMode { GEMM_STORE = 0, GEMM_ADD = 1, GEMM_ATOMIC = 2 };
+
+template <typename T, typename OutT>
+struct SimtGemm {
+  int M = 0, N = 0, K = 0;
+  const T* A = nullptr; long long sam = 0, sak = 1;
+  const T* B = nullptr; long long sbn = 0, sbk = 1;
+  OutT* C = nullptr; long long scm = 0, scn = 1;
+  int batch = 1; long long abs = 0, bbs = 0, cbs = 0;
+  int splitk = 1;
+  T alpha = T(1);
+  int mode = GEMM_STORE;
+};
+
+template <typename T, typename OutT>
+void simt_gemm(const SimtGemm<T, OutT>& g, cudaStream_t s);
+
+// Sparse action of one MPO core on rows of a dense tensor:
+//   out[ob + ro(r)][v] = sum_{nz in row r} val[nz] * in[ib + ci(nz)][v],  v < veclen
+// row r carries two indices (rw, rs): ro = rw*out_sw + rs*out_ss;
+// nonzero carries (cw, ct):           ci = cw*in_sw + ct*in_st;
+// batch (b1 < B1, b2 < B2): ib = b1*in_b1 + b2*in_b2, ob = b1*out_b1 + b2*out_b2.
+template <typename V>
+struct SparseRows {
+  int nrows = 0;
+  const int* row_ptr = nullptr;     // nrows + 1
+  const int* row_w = nullptr;       // nrows
+  const int* row_s = nullptr;       // nrows
+  const int* nz_w = nullptr;        // nnz
+  const int* nz_t = nullptr;        // nnz
+  const V* nz_val = nullptr;        // nnz
+};
+
+struct SparseGeom {
+  int veclen = 0;
+  long long out_sw = 0, out_ss = 0, in_sw = 0, in_st = 0;
+  int B1 = 1, B2 = 1;
+  long long in_b1 = 0, in_b2 = 0, out_b1 = 0, out_b2 = 0;
+};
+
+template <typename TI, typename TO, typename V>
+void sparse_rows_apply(const SparseRows<V>& sp, const SparseGeom& g, const TI* in, TO* out,
+                       cudaStream_t s);
+
+// ---- permutes and conversions
+// out[(i*d1 + j)*d2 + k] = in[(j*d0 + i)*d2 + k]   (swap the two outer dims, k contiguous)
+template <typename TI, typename TO>
+void permute_swap01(const TI* in, TO* out, int d0, int d1, int d2, cudaStream_t s);
+template <typename TI, typename TO>
+void convert(const TI* in, TO* out, long long n, cudaStream_t s);
+// 2D transpose of a (rows x cols) row-major matrix: out (cols x rows)
+template <typename TI, typename TO>
+void transpose2d(const TI* in, TO* out, int rows, int cols, cudaStream_t s);
+
+// ---- FP64 vector kernels (deterministic two-pass reductions)
+// partial buffer must hold at least kReduceBlocks * k doubles.
+constexpr int kReduceBlocks = 304;
+void dot_multi(const double* V, long long ldv, int k, const double* w, long long n,
+               double* partial, double* out, cudaStream_t s);          // out[j] = <V_j, w>
+void gemv_sub(const double* V, long long ldv, int k, const double* h, double* w, long long n,
+              cudaStream_t s);                                         // w -= sum_j h[j] V_j
+void gemv_set(const double* V, long long ldv, int k, const double* h, double* out, long long n,
+              cudaStream_t s);                                         // out = sum_j h[j] V_j
+void axpby(double a, const double* x, double b, double* y, long long n, cudaStream_t s);
+void scale_dev(double* x, const double* num, const double* den_sqrt, long long n, cudaStream_t s);
+void lanczos_update(double* w, const double* v, const double* vprev, const double* alpha,
+                    double beta_prev, long long n, cudaStream_t s);    // w -= a v + b vprev
+void normalize_into(const double* w, const double* nrm2, double* out, long long n, cudaStream_t s);
+
+// ---- small symmetric eigensolver (one CTA, cyclic Jacobi, m <= 64)
+// A (m x m, row-major, symmetric) is overwritten; evals ascending, evecs column-major
+// (evecs[j*m + i] = component i of eigenvector j).  status[0] = sweeps used (or -1).
+void jacobi_eig(double* A, int m, double* evals, double* evecs, int* status, cudaStream_t s);
+
+// Coarse problem of Sec. 3.1 (m <= 63) in one CTA; outputs on the device.
+void coarse_solve_dev(const double* A, const double* S, int m, double eps, double* c,
+                      double* lam, int* rank, int* status, cudaStream_t s);
+
+// ---- assorted
+void fill_zero(void* p, size_t bytes, cudaStream_t s);
+void sign_fix_qr(double* Q, int ldq, int rows, double* R, int ldr, int k, cudaStream_t s);
+void scale_rows(double* M, int rows, int cols, const double* svals, cudaStream_t s); // M[r,:]*=s[r]
+// TT-sum block copy: dst[(r0 + i)*ld_dst_r + ... ] = alpha * src
+void copy_block3(const double* src, int d0, int d1, int d2, double* dst, long long dst_s0,
+                 long long dst_s1, int o0, int o2, double alpha, cudaStream_t s);
+
+}  // namespace a2

@@ -1,0 +1,155 @@
+"""GPU parity of whole global iterations (Alg. 2) against the oracle, C-ABI calls."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import a2dmrg as oa2
+from oracle.dmrg import half_sweep_lr
+from oracle.tt import left_orthogonalize, right_orthogonalize, tt_full, tt_inner
+from synthetic import chemistry_integrals, chemistry_mpo, heisenberg_mpo, random_tt_cores
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2505_23429_gb300 as a2  # noqa: E402
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "golden_values.json")))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = a2.Context(0)
+    yield c
+    c.close()
+
+
+def _start(phys, r0, seed):
+    raw = random_tt_cores(phys, r0, seed)
+    U = left_orthogonalize(raw)
+    U[-1] = U[-1] / np.sqrt(tt_inner(U, U))
+    return raw, U
+
+
+def _gpu_tt(ctx, raw):
+    t = a2.TT.from_cores(ctx, raw)
+    t.left_orthogonalize()
+    return t
+
+
+KW = dict(svd_tol=1e-10, eig_tol=1e-10, coarse_eps=1e-10)
+
+
+def test_one_iteration_heisenberg_c1(ctx):
+    L = 12
+    m = heisenberg_mpo(L)
+    raw, U = _start([2] * L, 4, 23429)
+    U1, rep0 = oa2.global_iteration(U, m, [6, 5], 32, **KW)
+    mpo = a2.MPO(ctx, m)
+    t = _gpu_tt(ctx, raw)
+    rep = a2.additive_sweep(ctx, t, mpo, 2, partition=[6, 5], D_max=32, prec="fp64", **KW)
+    assert abs(rep["energy_in"] - oa2.energy(U, m)) < 1e-12 * abs(rep["energy_in"])
+    assert np.allclose(rep["S_hat"], rep0["S_hat"], atol=1e-9)
+    assert np.allclose(rep["A_hat"], rep0["A_hat"], atol=1e-9 * np.abs(rep0["A_hat"]).max())
+    assert abs(rep["lambda_coarse"] - rep0["lambda_coarse"]) < 1e-10 * abs(rep0["lambda_coarse"])
+    assert np.allclose(rep["coeffs"], rep0["coeffs"], atol=1e-7)
+    E, nrm = a2.energy(ctx, t, mpo)
+    assert abs(nrm - 1.0) < 1e-12
+    assert abs(E - rep0["energy"]) < 1e-10 * abs(E)
+    # same tensor (gauge-invariant): compare the full vectors up to sign
+    x = tt_full(t.cores())
+    x0 = tt_full(U1)
+    assert abs(abs(x @ x0) - 1.0) < 1e-9
+
+
+@pytest.mark.parametrize("D,tol", [(64, 1e-10), (32, 1e-9)])
+def test_converged_heisenberg_c1_vs_oracle_and_ed(ctx, D, tol):
+    L = 12
+    m = heisenberg_mpo(L)
+    raw, U = _start([2] * L, 4, 23429)
+    _, hist = oa2.run(U, m, [6, 5], D, 8, tol_rel=1e-14, **KW)
+    mpo = a2.MPO(ctx, m)
+    t = _gpu_tt(ctx, raw)
+    for _ in range(len(hist)):
+        a2.additive_sweep(ctx, t, mpo, 2, partition=[6, 5], D_max=D, prec="fp64", **KW)
+    E, _ = a2.energy(ctx, t, mpo)
+    E_or = hist[-1]["energy"]
+    E_ed = GOLD["heisenberg_L12_obc_J1_ed"]["value"]
+    assert abs(E - E_or) < tol * abs(E_or)
+    assert E >= E_ed - 1e-10
+    if D == 64:
+        assert abs(E - E_ed) < 1e-10 * abs(E_ed)
+
+
+def test_chemistry_L6_converges_to_ed(ctx):
+    h, eri = chemistry_integrals(6, 2505)
+    m = chemistry_mpo(h, eri)
+    raw, U = _start([4] * 6, 4, 23429)
+    U1, rep0 = oa2.global_iteration(U, m, [2, 2, 1], 64, **KW)
+    mpo = a2.MPO(ctx, m)
+    t = _gpu_tt(ctx, raw)
+    rep = a2.additive_sweep(ctx, t, mpo, 3, partition=[2, 2, 1], D_max=64, prec="fp64", **KW)
+    assert abs(rep["lambda_coarse"] - rep0["lambda_coarse"]) < 1e-10 * abs(rep0["lambda_coarse"])
+    E1, _ = a2.energy(ctx, t, mpo)
+    assert abs(E1 - rep0["energy"]) < 1e-10 * abs(E1)
+    for _ in range(3):
+        a2.additive_sweep(ctx, t, mpo, 3, partition=[2, 2, 1], D_max=64, prec="fp64", **KW)
+    E, _ = a2.energy(ctx, t, mpo)
+    E_ed = GOLD["chemistry_L6_seed2505_ed"]["value"]
+    assert abs(E - E_ed) < 1e-10 * abs(E_ed)
+
+
+def test_alg2_one_bond_per_group(ctx):
+    L = 8
+    m = heisenberg_mpo(L)
+    raw, U = _start([2] * L, 4, 7)
+    _, rep0 = oa2.global_iteration(U, m, [1] * (L - 1), 16, **KW)
+    mpo = a2.MPO(ctx, m)
+    t = _gpu_tt(ctx, raw)
+    rep = a2.additive_sweep(ctx, t, mpo, L - 1, D_max=16, prec="fp64", **KW)
+    assert rep["coarse_rank"] == rep0["coarse_rank"]
+    assert abs(rep["lambda_coarse"] - rep0["lambda_coarse"]) < 1e-10 * abs(rep0["lambda_coarse"])
+
+
+def test_classical_half_sweep(ctx):
+    L = 10
+    m = heisenberg_mpo(L)
+    raw, U = _start([2] * L, 4, 3)
+    R = right_orthogonalize(U)
+    U1, e, _ = half_sweep_lr(R, m, 16, 1e-10, 1e-10)
+    mpo = a2.MPO(ctx, m)
+    t = _gpu_tt(ctx, raw)
+    rep = a2.classical_sweep(ctx, t, mpo, D_max=16, prec="fp64", **KW)
+    E, _ = a2.energy(ctx, t, mpo)
+    E0 = oa2.energy(U1, m)
+    assert abs(E - E0) < 1e-10 * abs(E0)
+
+
+def test_fp32_path_within_1e6_of_fp64(ctx):
+    h, eri = chemistry_integrals(6, 2505)
+    m = chemistry_mpo(h, eri)
+    raw, _ = _start([4] * 6, 4, 23429)
+    mpo = a2.MPO(ctx, m)
+    res = {}
+    for prec in ("fp64", "fp32"):
+        t = _gpu_tt(ctx, raw)
+        for _ in range(4):
+            a2.additive_sweep(ctx, t, mpo, 3, partition=[2, 2, 1], D_max=64, prec=prec,
+                              svd_tol=1e-10, eig_tol=1e-8, coarse_eps=1e-10)
+        res[prec] = a2.energy(ctx, t, mpo, "fp64")[0]
+    assert abs(res["fp32"] - res["fp64"]) < 1e-6
+
+
+def test_error_leaves_tt_unchanged(ctx):
+    L = 6
+    m = heisenberg_mpo(L)
+    raw, _ = _start([2] * L, 4, 1)
+    mpo = a2.MPO(ctx, m)
+    t = _gpu_tt(ctx, raw)
+    before = tt_full(t.cores())
+    with pytest.raises(a2.A2Error):
+        a2.additive_sweep(ctx, t, mpo, 2, partition=[2, 2], D_max=8)   # sums to 4 != L-1
+    assert np.array_equal(tt_full(t.cores()), before)
