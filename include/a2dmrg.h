@@ -176,6 +176,27 @@ a2_status a2_svd_split(a2_ctx* ctx, int Dl, int n1, int n2, int Dr, const double
                        double tol, double* P_out, double* SQ_out, int* rank_out,
                        double* discarded_out);
 
+/* Stages S1 and S4 of the H_eff chain alone: the tcgen05 tensor-core GEMM
+ *   C[m][n] = sum_k A[m][k] B[n][k],  A: M x K (row stride lda), B: N x K (row
+ *   stride ldb), BF16 (device, 16-byte aligned, strides multiples of 8 elements),
+ *   C: M x N FP32 (device, row stride ldc).  splitk > 1 splits K across CTAs and
+ *   accumulates atomically (C is zeroed first).  Synchronous. */
+a2_status a2_gemm_bf16(a2_ctx* ctx, int M, int N, int K, const void* A, long long lda,
+                       const void* B, long long ldb, float* C, long long ldc, int splitk);
+
+/* Device-side error code of the bounded waits in the tensor-core kernels (0 = none);
+ * reset != 0 clears it.  Synchronizes the context stream. */
+a2_status a2_device_error(a2_ctx* ctx, int reset, int* code_out);
+
+/* Live kernel timing with CUDA events on the context stream (not paper content;
+ * used to report achieved throughput per kernel class).  op: 0 = disable,
+ * 1 = enable, 2 = reset totals, 3 = read the totals of `kind` (0 tcgen05 S1,
+ * 1 sparse S2, 2 sparse S3, 3 tcgen05 S4, 4 SIMT H_eff, 5 environment update,
+ * 6 Lanczos vector work, 7 truncated SVD, 8 LQ/QR) into the host outputs
+ * (launches, milliseconds, algorithmic flops, algorithmic bytes; any may be NULL). */
+a2_status a2_profile(a2_ctx* ctx, int op, int kind, long long* launches, double* ms,
+                     double* flops, double* bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,6 +80,11 @@ def lib():
                           ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P],
         "a2_svd_split": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
                          ctypes.c_int, ctypes.c_double, _P, _P, _I, _D],
+        "a2_gemm_bf16": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.c_longlong,
+                         _P, ctypes.c_longlong, _P, ctypes.c_longlong, ctypes.c_int],
+        "a2_device_error": [_P, ctypes.c_int, _I],
+        "a2_profile": [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _D, _D,
+                       _D],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -98,7 +103,8 @@ def exported_symbols():
             "a2_tt_create", "a2_tt_set_core", "a2_tt_get_core", "a2_tt_left_orthogonalize",
             "a2_tt_destroy", "a2_mpo_load", "a2_mpo_nnz", "a2_mpo_destroy",
             "a2_additive_sweep", "a2_classical_sweep", "a2_coarse_solve", "a2_energy",
-            "a2_heff_apply", "a2_env_update", "a2_svd_split"]
+            "a2_heff_apply", "a2_env_update", "a2_svd_split", "a2_gemm_bf16",
+            "a2_device_error", "a2_profile"]
 
 
 def _dp(a):
@@ -309,3 +315,34 @@ def svd_split(ctx, x, D_max, tol, P_out, SQ_out):
     ctx.check(lib().a2_svd_split(ctx._h, Dl, n1, n2, Dr, _ptr(x), D_max, tol, _ptr(P_out),
                                  _ptr(SQ_out), ctypes.byref(r), ctypes.byref(disc)))
     return r.value, disc.value
+
+
+def gemm_bf16(ctx, A, B, C, K=None, splitk=1):
+    """C[m][n] = sum_k A[m][k] B[n][k] on tcgen05; A (M x lda), B (N x ldb) bf16 CUDA
+    tensors whose first K columns are used; C (M x ldc) float32 CUDA tensor."""
+    M, lda = A.shape
+    N, ldb = B.shape
+    K = lda if K is None else K
+    ctx.check(lib().a2_gemm_bf16(ctx._h, M, N, K, _ptr(A), lda, _ptr(B), ldb, _ptr(C),
+                                 C.shape[1], splitk))
+
+
+def device_error(ctx, reset=True):
+    v = ctypes.c_int()
+    ctx.check(lib().a2_device_error(ctx._h, int(reset), ctypes.byref(v)))
+    return v.value
+
+
+PROFILE_KINDS = ["tc_s1", "sparse_s2", "sparse_s3", "tc_s4", "heff_simt", "env", "lanczos",
+                 "svd", "lq"]
+
+
+def profile(ctx, op, kind=0):
+    """op: 'off', 'on', 'reset' or 'read' (returns dict for `kind`)."""
+    code = {"off": 0, "on": 1, "reset": 2, "read": 3}[op]
+    n, ms, fl, by = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    ctx.check(lib().a2_profile(ctx._h, code, kind, ctypes.byref(n), ctypes.byref(ms),
+                               ctypes.byref(fl), ctypes.byref(by)))
+    if code == 3:
+        return dict(launches=n.value, ms=ms.value, flops=fl.value, bytes=by.value)
+    return None

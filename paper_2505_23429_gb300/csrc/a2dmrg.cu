@@ -63,6 +63,7 @@ struct SiteOps {
       r.row_s = rs.as<int>();
       r.nz_w = nw.as<int>();
       r.nz_t = nt.as<int>();
+      r.nnz_total = nnz;
       if constexpr (sizeof(V) == 8) r.nz_val = v64.as<double>();
       else r.nz_val = v32.as<float>();
       return r;
@@ -159,6 +160,8 @@ void check_finite(double v, const char* what) {
 }
 
 // ============================================================================= contractions
+double heff_flops(const SiteOps& A1, const SiteOps& A2, int Dl, int Dr);
+double env_flops(const SiteOps& so, int Dl, int Dr);
 // A TT core viewed in compute type T (converted copy for float).
 template <typename T>
 const T* as_compute(a2_ctx* c, const double* core, long long n, DevBuf& buf) {
@@ -178,6 +181,9 @@ void env_left(a2_ctx* c, const SiteOps& so, const T* Hin, const T* bra, int Dlb,
               const T* ket, int Dlk, int Drk, T* Hout) {
   const int n = so.n, Rl = so.Rl, Rr = so.Rr;
   cudaStream_t s = c->stream;
+  ProfScope ps(PK_ENV, s, env_flops(so, std::max(Dlb, Dlk), std::max(Drb, Drk)),
+               sizeof(T) * ((double)Dlb * Rl * Dlk + (double)Drb * Rr * Drk +
+                            2.0 * Dlb * Rl * n * Drk + 2.0 * Dlb * n * Rr * Drk));
   c->tmp1.ensure(sizeof(T) * (size_t)Dlb * Rl * n * Drk, s);
   c->tmp2.ensure(sizeof(T) * (size_t)Dlb * n * Rr * Drk, s);
   T* T1 = c->tmp1.as<T>();
@@ -214,6 +220,9 @@ void env_right(a2_ctx* c, const SiteOps& so, const T* Hin, const T* bra, int Dlb
                const T* ket, int Dlk, int Drk, T* Hout) {
   const int n = so.n, Rl = so.Rl, Rr = so.Rr;
   cudaStream_t s = c->stream;
+  ProfScope ps(PK_ENV, s, env_flops(so, std::max(Dlb, Dlk), std::max(Drb, Drk)),
+               sizeof(T) * ((double)Dlb * Rl * Dlk + (double)Drb * Rr * Drk +
+                            2.0 * Drb * Rr * n * Dlk + 2.0 * n * Drb * Rl * Dlk));
   c->tmp1.ensure(sizeof(T) * ((size_t)Drb * Rr * n * Dlk + (size_t)n * Dlk * Drk), s);
   c->tmp2.ensure(sizeof(T) * (size_t)n * Drb * Rl * Dlk, s);
   T* T1 = c->tmp1.as<T>();
@@ -263,6 +272,8 @@ void heff_T(a2_ctx* c, const SiteOps& A1, const SiteOps& A2, const T* HL, const 
   const size_t s1 = (size_t)Dl * Rl * n1 * n2 * Dr;
   const size_t s2 = (size_t)Dl * R1 * n1 * n2 * Dr;
   const size_t s3 = (size_t)Dl * n1 * n2 * Rr * Dr;
+  ProfScope ps(PK_HEFF_SIMT, s, heff_flops(A1, A2, Dl, Dr),
+               sizeof(T) * (2.0 * (s1 + s2 + s3) + (double)Dl * Rl * Dl + (double)Dr * Rr * Dr));
   c->t1.ensure(sizeof(T) * std::max(s1, s3), s);
   c->t2.ensure(sizeof(T) * s2, s);
   T* T1 = c->t1.as<T>();
@@ -320,6 +331,37 @@ double env_flops(const SiteOps& so, int Dl, int Dr) {
          2.0 * (double)Dl * Dr * (double)so.nnz;
 }
 
+// BF16 environments with padded rows for TMA: L [(a w)][a'] -> ld pad8(Dl); R [b][(w2 b')]
+struct Bf16Envs {
+  DevBuf buf;
+  const __nv_bfloat16* L = nullptr;
+  const __nv_bfloat16* R = nullptr;
+  long long ldl = 0, ldr = 0;
+  template <typename T>
+  void set(a2_ctx* c, const T* Lf, int Dl, int Rl, const T* Rf, int Dr, int Rr) {
+    ldl = pad8(Dl);
+    ldr = pad8((long long)Rr * Dr);
+    const size_t nl = (size_t)Dl * Rl * ldl, nr = (size_t)Dr * ldr;
+    const size_t off = (nl + 63) / 64 * 64;   // keep R 128-byte aligned
+    buf.ensure(sizeof(__nv_bfloat16) * (off + nr), c->stream);
+    __nv_bfloat16* lb = buf.as<__nv_bfloat16>();
+    __nv_bfloat16* rb = lb + off;
+    convert_ld<T, __nv_bfloat16>(Lf, lb, (long long)Dl * Rl, Dl, ldl, c->stream);
+    convert_ld<T, __nv_bfloat16>(Rf, rb, Dr, (long long)Rr * Dr, ldr, c->stream);
+    L = lb;
+    R = rb;
+  }
+};
+
+void heff_bf16(a2_ctx* c, const SiteOps& A1, const SiteOps& A2, const Bf16Envs& E, int Dl, int Dr,
+               const double* x, double* y) {
+  const long long N = (long long)Dl * A1.n * A2.n * Dr;
+  c->ya.ensure(sizeof(float) * N, c->stream);
+  tc_heff_bf16(c->stream, A1.n, A2.n, A1.Rl, A1.Rr, A2.Rr, Dl, Dr, E.L, E.ldl, E.R, E.ldr, x,
+               c->ya.as<float>(), A1.lr.rows<float>(), A2.lr.rows<float>(), c->t1, c->t2, c->t3);
+  convert<float, double>(c->ya.as<float>(), y, N, c->stream);
+}
+
 // ============================================================================= engine
 struct View {   // a TT as per-site device pointers and bond dims
   std::vector<const double*> core;
@@ -336,8 +378,9 @@ struct Engine {
   std::vector<DevBuf> HL, HR;            // envs in T
   std::vector<int> HLd, HRd;             // bond dims of the stored envs
   double flops = 0.0;
-  long long matvecs = 0;
+  long long matvecs = 0, matvecs_bf16 = 0;
   DevBuf cvt_bra, cvt_ket;
+  Bf16Envs bfe;
 
   Engine(a2_ctx* c_, const a2_mpo* m, a2_precision p) : c(c_), mpo(m), L(m->L), prec(p) {
     HL.resize(L + 1);
@@ -388,9 +431,18 @@ struct Engine {
     flops += heff_flops(A1, A2, Dl, Dr);
     ++matvecs;
   }
+  void matvec_bf16(int k, int Dl, int Dr, const double* x, double* y) {
+    heff_bf16(c, mpo->site[k], mpo->site[k + 1], bfe, Dl, Dr, x, y);
+    flops += heff_flops(mpo->site[k], mpo->site[k + 1], Dl, Dr);
+    ++matvecs;
+    ++matvecs_bf16;
+  }
 };
 
 // ============================================================================= Lanczos
+// residual tolerance of the BF16 tensor-core Lanczos phase (BF16 operator accuracy)
+constexpr double kBf16Tol = 3e-3;
+
 struct LanczosResult {
   double theta = 0.0;
   int matvecs = 0, cycles = 0;
@@ -442,6 +494,7 @@ LanczosResult lanczos(a2_ctx* c, MV&& mv, double* x, long long N, double tol, in
       mv(vj, w);
       ++res.matvecs;
       // alpha_j = <v_j, w>; w -= alpha v_j + beta v_{j-1}
+      ProfScope ps(PK_LANCZOS, s, 2.0 * N * (2.0 * (j + 1) * 2 + 6), 8.0 * N * (4.0 * (j + 1) + 6));
       dot_multi(vj, 0, 1, w, N, c->partial.as<double>(), scal(c, 1), s);
       lanczos_update(w, vj, j > 0 ? V + (size_t)(j - 1) * N : nullptr, scal(c, 1),
                      j > 0 ? beta.back() : 0.0, N, s);
@@ -510,6 +563,8 @@ LanczosResult lanczos(a2_ctx* c, MV&& mv, double* x, long long N, double tol, in
 int svd_split_dev(a2_ctx* c, const double* M, int rows, int cols, int D_max, double tol,
                   double* P, double* SQ, double* discarded, std::vector<double>* sv_out = nullptr) {
   cudaStream_t s = c->stream;
+  ProfScope ps(PK_SVD, s, 2.0 * rows * rows * (double)cols * 2 + 10.0 * rows * rows * (double)rows,
+               8.0 * (2.0 * rows * cols + 2.0 * rows * rows));
   c->gram.ensure(sizeof(double) * ((size_t)rows * rows + rows), s);
   double* G = c->gram.as<double>();
   double* w = G + (size_t)rows * rows;
@@ -719,10 +774,22 @@ struct Sweeper {
       auto mv = [&](const double* in, double* out) {
         eng.matvec(k, HLcur, HRk, Dl, Dr, in, out);
       };
+      int nmv = 0;
+      if constexpr (sizeof(T) == 4) {
+        if (o.prec == A2_BF16) {
+          // tensor-core Lanczos on the BF16 operator to a loose tolerance, then the
+          // accurate (FP32) operator from that start vector to eig_tol
+          eng.bfe.set(c, HLcur, Dl, mpo->R[k], HRk, Dr, mpo->R[k + 2]);
+          auto mvb = [&](const double* in, double* out) { eng.matvec_bf16(k, Dl, Dr, in, out); };
+          LanczosResult lb = lanczos(c, mvb, x.as<double>(), N, std::max(o.eig_tol, kBf16Tol),
+                                     o.max_krylov, o.max_restarts);
+          nmv += lb.matvecs;
+        }
+      }
       LanczosResult lr = lanczos(c, mv, x.as<double>(), N, o.eig_tol, o.max_krylov,
                                  o.max_restarts);
       check_finite(lr.theta, "local eigenvalue");
-      kry[k] = lr.matvecs;
+      kry[k] = nmv + lr.matvecs;
       G.theta = lr.theta;
       const int rows = Dl * n1, cols = n2 * Dr;
       const int kmax = std::min(rows, cols);
@@ -1408,9 +1475,10 @@ a2_status a2_heff_apply(a2_ctx* c, const a2_mpo* m, int k, a2_precision prec, in
       convert<float, double>(c->ya.as<float>(), y, N, s);
     } else if (prec == A2_BF16) {
       A2_REQUIRE(tc_available(), "A2_BF16 needs the tcgen05 path");
-      tc_heff_apply(c->stream, A1.n, A2.n, A1.Rl, A1.Rr, A2.Rr, Dl, Dr, L, R, x, y,
-                    A1.lr.rows<float>(), A2.lr.rows<float>(), c->t1, c->t2, c->t3, c->xa, c->ya,
-                    c->cb);
+      Bf16Envs E;
+      E.set<double>(c, L, Dl, A1.Rl, R, Dr, A2.Rr);
+      heff_bf16(c, A1, A2, E, Dl, Dr, x, y);
+      A2_CUDA(cudaStreamSynchronize(s));
     } else {
       throw ArgError("unsupported precision");
     }
@@ -1446,6 +1514,40 @@ a2_status a2_env_update(a2_ctx* c, const a2_mpo* m, int j, int side, a2_precisio
       else env_right<float>(c, so, fi, fb, Dlb, Drb, fk, Dlk, Drk, fo);
       convert<float, double>(fo, out, nout, s);
     }
+  });
+}
+
+a2_status a2_gemm_bf16(a2_ctx* c, int M, int N, int K, const void* A, long long lda,
+                       const void* B, long long ldb, float* C, long long ldc, int splitk) {
+  if (!c) return A2_EINVAL;
+  return guarded(c, [&] {
+    A2_REQUIRE(M >= 1 && N >= 1 && K >= 1 && A && B && C && splitk >= 1, "a2_gemm_bf16: bad arguments");
+    A2_REQUIRE(tc_available(), "tcgen05 path not built");
+    if (splitk > 1) fill_zero(C, sizeof(float) * (size_t)M * ldc, c->stream);
+    tc_gemm_bf16(static_cast<const __nv_bfloat16*>(A), lda, static_cast<const __nv_bfloat16*>(B),
+                 ldb, M, N, K, C, ldc, splitk > 1 ? 2 : 1, splitk, c->stream);
+    A2_CUDA(cudaStreamSynchronize(c->stream));
+  });
+}
+
+a2_status a2_device_error(a2_ctx* c, int reset, int* code_out) {
+  if (!c || !code_out) return A2_EINVAL;
+  return guarded(c, [&] {
+    A2_CUDA(cudaStreamSynchronize(c->stream));
+    *code_out = tc_error_flag(reset != 0);
+  });
+}
+
+a2_status a2_profile(a2_ctx* c, int op, int kind, long long* launches, double* ms,
+                     double* flops, double* bytes) {
+  if (!c) return A2_EINVAL;
+  return guarded(c, [&] {
+    A2_CUDA(cudaStreamSynchronize(c->stream));
+    if (op == 0) prof_enable(false);
+    else if (op == 1) prof_enable(true);
+    else if (op == 2) prof_reset();
+    else if (op == 3) prof_read(kind, launches, ms, flops, bytes);
+    else throw ArgError("a2_profile: op must be 0..3");
   });
 }
 

@@ -70,4 +70,30 @@ struct DevBuf {
   template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
 };
 
+// ---- live per-kernel-class timing with CUDA events (off unless enabled)
+enum ProfKind {
+  PK_TC_S1 = 0,      // tcgen05 GEMM, H_eff stage S1 (BF16)
+  PK_SPARSE_S2,      // sparse MPO action, H_eff stage S2 (BF16 path)
+  PK_SPARSE_S3,      // sparse MPO action, H_eff stage S3 (BF16 path)
+  PK_TC_S4,          // tcgen05 GEMM, H_eff stage S4 (BF16)
+  PK_HEFF_SIMT,      // whole H_eff application on the SIMT path (FP32/FP64)
+  PK_ENV,            // environment update (whole)
+  PK_LANCZOS,        // Lanczos vector work (dots, updates, re-orthogonalisation)
+  PK_SVD,            // truncated SVD step (Gram + eigensolve + products)
+  PK_LQ,             // LQ / QR factorisations
+  PK_COUNT
+};
+void prof_enable(bool on);
+bool prof_enabled();
+// Records an event pair around the scope on stream s with algorithmic flops / bytes.
+struct ProfScope {
+  int idx = -1;
+  cudaStream_t s = nullptr;
+  ProfScope(int kind, cudaStream_t stream, double flops, double bytes);
+  ~ProfScope();
+};
+// Accumulated totals since the last reset (synchronizes all recorded events).
+void prof_read(int kind, long long* launches, double* ms, double* flops, double* bytes);
+void prof_reset();
+
 }  // namespace a2

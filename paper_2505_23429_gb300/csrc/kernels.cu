@@ -1,7 +1,93 @@
 // SIMT GEMM, sparse MPO action, vector and small dense kernels (sm_103a).
+#include <mutex>
+#include <vector>
+
 #include "kernels.cuh"
 
 namespace a2 {
+
+// ----------------------------------------------------------------------------- profiler
+namespace {
+struct ProfRec {
+  int kind;
+  cudaEvent_t a, b;
+  double flops, bytes;
+};
+struct ProfState {
+  bool on = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  long long n[PK_COUNT] = {};
+  double ms[PK_COUNT] = {}, fl[PK_COUNT] = {}, by[PK_COUNT] = {};
+  std::mutex mu;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    A2_CUDA(cudaEventCreate(&e));
+    return e;
+  }
+  void drain() {
+    for (auto& r : recs) {
+      A2_CUDA(cudaEventSynchronize(r.b));
+      float t = 0.f;
+      A2_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+      n[r.kind] += 1;
+      ms[r.kind] += t;
+      fl[r.kind] += r.flops;
+      by[r.kind] += r.bytes;
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    recs.clear();
+  }
+};
+ProfState& P() {
+  static ProfState st;
+  return st;
+}
+}  // namespace
+
+void prof_enable(bool on) { P().on = on; }
+bool prof_enabled() { return P().on; }
+
+ProfScope::ProfScope(int kind, cudaStream_t stream, double flops, double bytes) : s(stream) {
+  ProfState& st = P();
+  if (!st.on) return;
+  std::lock_guard<std::mutex> g(st.mu);
+  ProfRec r{kind, st.get(), st.get(), flops, bytes};
+  A2_CUDA(cudaEventRecord(r.a, stream));
+  st.recs.push_back(r);
+  idx = (int)st.recs.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+  if (idx < 0) return;
+  ProfState& st = P();
+  std::lock_guard<std::mutex> g(st.mu);
+  if (idx < (int)st.recs.size()) cudaEventRecord(st.recs[idx].b, s);
+}
+
+void prof_read(int kind, long long* launches, double* ms, double* flops, double* bytes) {
+  ProfState& st = P();
+  std::lock_guard<std::mutex> g(st.mu);
+  st.drain();
+  if (kind < 0 || kind >= PK_COUNT) throw ArgError("bad profile kind");
+  if (launches) *launches = st.n[kind];
+  if (ms) *ms = st.ms[kind];
+  if (flops) *flops = st.fl[kind];
+  if (bytes) *bytes = st.by[kind];
+}
+
+void prof_reset() {
+  ProfState& st = P();
+  std::lock_guard<std::mutex> g(st.mu);
+  st.drain();
+  for (int k = 0; k < PK_COUNT; ++k) st.n[k] = 0, st.ms[k] = st.fl[k] = st.by[k] = 0.0;
+}
 
 // ----------------------------------------------------------------------------- SIMT GEMM
 template <typename T, typename OutT, int BM, int BN, int BK, int TM, int TN>
@@ -206,49 +292,34 @@ __global__ void convert_kernel<float, __nv_bfloat16>(const float* in, __nv_bfloa
     out[e] = __float2bfloat16_rn(in[e]);
 }
 
+template <typename TO> __device__ __forceinline__ TO cvt_out(double v) { return (TO)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 cvt_out<__nv_bfloat16>(double v) {
+  return __double2bfloat16(v);
+}
+
 template <typename TI, typename TO>
-__global__ void transpose_kernel(const TI* in, TO* out, int rows, int cols) {
-  __shared__ float tile[32][33];
-  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
-  for (int j = threadIdx.y; j < 32; j += 8) {
-    const int r = by + j, c = bx + threadIdx.x;
-    if (r < rows && c < cols) tile[j][threadIdx.x] = (float)in[(long long)r * cols + c];
-  }
-  __syncthreads();
-  for (int j = threadIdx.y; j < 32; j += 8) {
-    const int c = bx + j, r = by + threadIdx.x;
-    if (r < rows && c < cols) out[(long long)c * rows + r] = (TO)tile[threadIdx.x][j];
-  }
-}
-template <>
-__global__ void transpose_kernel<double, double>(const double* in, double* out, int rows,
-                                                 int cols) {
+__global__ void transpose_kernel(const TI* in, TO* out, int rows, int cols, long long ld) {
   __shared__ double tile[32][33];
   const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
   for (int j = threadIdx.y; j < 32; j += 8) {
     const int r = by + j, c = bx + threadIdx.x;
-    if (r < rows && c < cols) tile[j][threadIdx.x] = in[(long long)r * cols + c];
+    if (r < rows && c < cols) tile[j][threadIdx.x] = (double)in[(long long)r * cols + c];
   }
   __syncthreads();
   for (int j = threadIdx.y; j < 32; j += 8) {
     const int c = bx + j, r = by + threadIdx.x;
-    if (r < rows && c < cols) out[(long long)c * rows + r] = tile[threadIdx.x][j];
+    if (r < rows && c < cols) out[(long long)c * ld + r] = cvt_out<TO>(tile[threadIdx.x][j]);
   }
 }
-template <>
-__global__ void transpose_kernel<double, __nv_bfloat16>(const double* in, __nv_bfloat16* out,
-                                                        int rows, int cols) {
-  __shared__ double tile[32][33];
-  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
-  for (int j = threadIdx.y; j < 32; j += 8) {
-    const int r = by + j, c = bx + threadIdx.x;
-    if (r < rows && c < cols) tile[j][threadIdx.x] = in[(long long)r * cols + c];
-  }
-  __syncthreads();
-  for (int j = threadIdx.y; j < 32; j += 8) {
-    const int c = bx + j, r = by + threadIdx.x;
-    if (r < rows && c < cols)
-      out[(long long)c * rows + r] = __double2bfloat16(tile[threadIdx.x][j]);
+
+template <typename TI, typename TO>
+__global__ void convert_ld_kernel(const TI* in, TO* out, long long rows, long long cols,
+                                  long long ld) {
+  const long long n = rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / cols, c = e % cols;
+    out[r * ld + c] = cvt_out<TO>((double)in[e]);
   }
 }
 
@@ -271,11 +342,22 @@ void convert(const TI* in, TO* out, long long n, cudaStream_t s) {
   A2_CHECK_LAUNCH();
 }
 template <typename TI, typename TO>
-void transpose2d(const TI* in, TO* out, int rows, int cols, cudaStream_t s) {
+void transpose2d_ld(const TI* in, TO* out, int rows, int cols, long long ld, cudaStream_t s) {
   if (!rows || !cols) return;
   dim3 grid(cdiv(cols, 32), cdiv(rows, 32));
   A2_REQUIRE(grid.y < 65536, "transpose grid too large");
-  transpose_kernel<TI, TO><<<grid, dim3(32, 8), 0, s>>>(in, out, rows, cols);
+  transpose_kernel<TI, TO><<<grid, dim3(32, 8), 0, s>>>(in, out, rows, cols, ld);
+  A2_CHECK_LAUNCH();
+}
+template <typename TI, typename TO>
+void transpose2d(const TI* in, TO* out, int rows, int cols, cudaStream_t s) {
+  transpose2d_ld<TI, TO>(in, out, rows, cols, rows, s);
+}
+template <typename TI, typename TO>
+void convert_ld(const TI* in, TO* out, long long rows, long long cols, long long ld,
+                cudaStream_t s) {
+  if (!rows || !cols) return;
+  convert_ld_kernel<TI, TO><<<grid_for(rows * cols), 256, 0, s>>>(in, out, rows, cols, ld);
   A2_CHECK_LAUNCH();
 }
 template void permute_swap01<double, double>(const double*, double*, int, int, int, cudaStream_t);
@@ -289,6 +371,12 @@ template void transpose2d<double, double>(const double*, double*, int, int, cuda
 template void transpose2d<double, float>(const double*, float*, int, int, cudaStream_t);
 template void transpose2d<double, __nv_bfloat16>(const double*, __nv_bfloat16*, int, int,
                                                  cudaStream_t);
+template void transpose2d_ld<double, __nv_bfloat16>(const double*, __nv_bfloat16*, int, int,
+                                                    long long, cudaStream_t);
+template void convert_ld<double, __nv_bfloat16>(const double*, __nv_bfloat16*, long long,
+                                                long long, long long, cudaStream_t);
+template void convert_ld<float, __nv_bfloat16>(const float*, __nv_bfloat16*, long long,
+                                               long long, long long, cudaStream_t);
 
 // ----------------------------------------------------------------------------- vector kernels
 __device__ __forceinline__ double warp_sum(double v) {

@@ -39,6 +39,7 @@ struct SparseRows {
   const int* nz_w = nullptr;        // nnz
   const int* nz_t = nullptr;        // nnz
   const V* nz_val = nullptr;        // nnz
+  long long nnz_total = 0;
 };
 
 struct SparseGeom {
@@ -61,6 +62,13 @@ void convert(const TI* in, TO* out, long long n, cudaStream_t s);
 // 2D transpose of a (rows x cols) row-major matrix: out (cols x rows)
 template <typename TI, typename TO>
 void transpose2d(const TI* in, TO* out, int rows, int cols, cudaStream_t s);
+// same with an output row stride ld_out >= rows (padding untouched)
+template <typename TI, typename TO>
+void transpose2d_ld(const TI* in, TO* out, int rows, int cols, long long ld_out, cudaStream_t s);
+// out[r*ld_out + c] = in[r*cols + c]  (copy/convert into a row-padded matrix)
+template <typename TI, typename TO>
+void convert_ld(const TI* in, TO* out, long long rows, long long cols, long long ld_out,
+                cudaStream_t s);
 
 // ---- FP64 vector kernels (deterministic two-pass reductions)
 // partial buffer must hold at least kReduceBlocks * k doubles.

@@ -45,6 +45,7 @@ __global__ void lq_sign_kernel(double* L, int rows, int k, double* Q, int cols) 
 
 int Solver::lq(const double* M, int rows, int cols, double* L, double* Q, cudaStream_t s) {
   const int k = rows < cols ? rows : cols;
+  ProfScope ps(PK_LQ, s, 4.0 * (double)rows * rows * cols, 8.0 * 3.0 * rows * (double)cols);
   // M row-major (rows x cols) == M^T column-major (cols x rows), ld = cols
   tmp.ensure(sizeof(double) * ((size_t)rows * cols + (size_t)k), s);
   double* A = tmp.as<double>();

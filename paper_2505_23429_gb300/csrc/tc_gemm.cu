@@ -1,10 +1,435 @@
+// tcgen05 BF16 GEMM (TMA -> shared memory -> tcgen05.mma -> TMEM -> registers) and the
+// BF16 H_eff chain built on it (sm_103a).
+//
+//   D[m][n] = sum_k A[m][k] * B[n][k]      A: M x K, B: N x K, both K-major BF16,
+//   FP32 accumulation in tensor memory, epilogue stores BF16 or FP32 (plain or atomic).
+//
+// One CTA computes one 128 x BN output tile (optionally one K-split of it) with 128
+// threads: warp 0 lane 0 issues TMA loads into a STAGES-deep ring of 128B-swizzled
+// tiles, warp 1 lane 0 issues tcgen05.mma (M=128, N=BN, K=16 per instruction), and all
+// four warps drain the accumulator (warp w owns TMEM lanes 32w..32w+31).
+// Every mbarrier wait is bounded; a timeout raises a device error flag, the CTA skips
+// its stores, frees its TMEM and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "tc_gemm.cuh"
 
 namespace a2 {
-bool tc_available() { return false; }
-void tc_heff_apply(cudaStream_t, int, int, int, int, int, int, int, const double*, const double*,
-                   const double*, double*, const SparseRows<float>&, const SparseRows<float>&,
-                   DevBuf&, DevBuf&, DevBuf&, DevBuf&, DevBuf&, DevBuf&) {
-  throw ArgError("tcgen05 path not built");
+
+namespace tc {
+
+constexpr int BM = 128;
+constexpr int BK = 64;              // 64 bf16 = 128 bytes = one swizzle row
+constexpr uint32_t kWaitLimit = 1u << 26;
+
+__device__ int g_tc_error = 0;     // set to a nonzero code when a bounded wait gives up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred P;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, P;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: returns false (and records `code`) if the phase never completes.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int code) {
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (it > 64) __nanosleep(64);
+  }
+  atomicExch(&g_tc_error, code);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+  const uint64_t addr = smem_u32(p);
+  uint64_t d = 0;
+  d |= (addr >> 4) & 0x3FFFull;            // start address
+  d |= (uint64_t)1 << 16;                  // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                  // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                  // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both operands K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4)                     // D format F32
+         | (1u << 7)                   // A format BF16
+         | (1u << 10)                  // B format BF16
+         | ((uint32_t)(N >> 3) << 17)  // N / 8
+         | ((uint32_t)(M >> 4) << 24); // M / 16
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+enum OutKind { OUT_BF16 = 0, OUT_F32 = 1, OUT_F32_ATOMIC = 2 };
+
+struct TcArgs {
+  int M, N, K;
+  int kblocks_per_split;   // K blocks (of BK) handled by one CTA
+  void* C;
+  long long ldc;
+  int out_kind;
+};
+
+template <int BN, int STAGES>
+struct TcSmem {
+  alignas(1024) __nv_bfloat16 a[STAGES][BM * BK];
+  alignas(1024) __nv_bfloat16 b[STAGES][BN * BK];
+  alignas(8) uint64_t full[STAGES];
+  alignas(8) uint64_t empty[STAGES];
+  alignas(8) uint64_t done;
+  uint32_t tmem_base;
+  int abort_flag;
+};
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(128, 2)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+               TcArgs args) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // round the dynamic shared memory base up to 1024 bytes (swizzle atoms)
+  const uint32_t base = smem_u32(smem_raw);
+  const uint32_t pad = (1024u - (base & 1023u)) & 1023u;
+  auto& S = *reinterpret_cast<TcSmem<BN, STAGES>*>(smem_raw + pad);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM;
+  const int n0 = blockIdx.y * BN;
+  const int nk_total = (args.K + BK - 1) / BK;
+  const int kb0 = blockIdx.z * args.kblocks_per_split;
+  const int nk = max(0, min(nk_total - kb0, args.kblocks_per_split));
+  constexpr uint32_t kStageBytes = (BM + BN) * BK * 2;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&S.full[s], 1);
+      mbar_init(&S.empty[s], 1);
+    }
+    mbar_init(&S.done, 1);
+    S.abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 0) {   // TMEM accumulator: BN fp32 columns x 128 lanes
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&S.tmem_base)),
+                 "r"((uint32_t)BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = S.tmem_base;
+
+  if (nk > 0) {
+    if (warp == 0 && lane == 0) {
+      // ---------------- producer: TMA loads into the stage ring
+      int issued = 0;
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % STAGES;
+        const int round = kb / STAGES;
+        if (round > 0 && !mbar_wait(&S.empty[s], (round - 1) & 1, 1)) {
+          S.abort_flag = 1;
+          break;
+        }
+        if (*(volatile int*)&S.abort_flag) break;
+        mbar_expect_tx(&S.full[s], kStageBytes);
+        const int kx = (kb0 + kb) * BK;
+        tma_load_2d(&map_a, &S.full[s], S.a[s], kx, m0);
+        tma_load_2d(&map_b, &S.full[s], S.b[s], kx, n0);
+        issued = kb + 1;
+      }
+      // on abort: wait (bounded) for the copies already issued before leaving
+      if (*(volatile int*)&S.abort_flag) {
+        for (int kb = max(0, issued - STAGES); kb < issued; ++kb)
+          mbar_wait(&S.full[kb % STAGES], (kb / STAGES) & 1, 2);
+      }
+    } else if (warp == 1 && lane == 0) {
+      // ---------------- MMA issuer
+      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      bool ok = true;
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % STAGES;
+        if (!mbar_wait(&S.full[s], (kb / STAGES) & 1, 3)) {
+          S.abort_flag = 1;
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint64_t da = smem_desc(S.a[s]);
+        const uint64_t db = smem_desc(S.b[s]);
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          // advance 16 bf16 = 32 bytes (2 in 16-byte units) inside the swizzle atom
+          mma_bf16(tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+                   (kb > 0 || kk > 0) ? 1u : 0u);
+        }
+        mma_commit(&S.empty[s]);   // frees the stage once these MMAs have read it
+      }
+      if (ok) mma_commit(&S.done);
+      else S.abort_flag = 1;
+    }
+    __syncwarp();
+    // ---------------- epilogue: all four warps
+    bool ready = mbar_wait(&S.done, 0, 4);
+    if (!ready) S.abort_flag = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (!*(volatile int*)&S.abort_flag) {
+      const int row = m0 + warp * 32 + lane;
+      const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        if (n0 + c0 >= args.N) break;
+        float v[32];
+        tmem_ld32(tl + (uint32_t)c0, v);
+        if (row < args.M) {
+          const int ncol = min(32, args.N - (n0 + c0));
+          if (args.out_kind == OUT_BF16) {
+            __nv_bfloat16* C = reinterpret_cast<__nv_bfloat16*>(args.C) +
+                               (long long)row * args.ldc + n0 + c0;
+            if (ncol == 32 && ((reinterpret_cast<uintptr_t>(C) & 15) == 0)) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                __align__(16) __nv_bfloat162 h[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                  h[e] = __floats2bfloat162_rn(v[q * 8 + 2 * e], v[q * 8 + 2 * e + 1]);
+                *reinterpret_cast<uint4*>(C + q * 8) = *reinterpret_cast<uint4*>(h);
+              }
+            } else {
+              for (int e = 0; e < ncol; ++e) C[e] = __float2bfloat16_rn(v[e]);
+            }
+          } else {
+            float* C = reinterpret_cast<float*>(args.C) + (long long)row * args.ldc + n0 + c0;
+            if (args.out_kind == OUT_F32_ATOMIC) {
+              for (int e = 0; e < ncol; ++e) atomicAdd(C + e, v[e]);
+            } else {
+              for (int e = 0; e < ncol; ++e) C[e] = v[e];
+            }
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)BN));
+  }
+}
+
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  if (!fn) throw CudaError("cuTensorMapEncodeTiled unavailable");
+  return fn;
+}
+
+// 2D K-major BF16 operand: rows x K (row stride ld elements), box BK x box_rows, 128B swizzle.
+CUtensorMap make_map(const __nv_bfloat16* ptr, int rows, int K, long long ld, int box_rows) {
+  A2_REQUIRE((reinterpret_cast<uintptr_t>(ptr) & 15) == 0, "TMA base must be 16-byte aligned");
+  A2_REQUIRE((ld * 2) % 16 == 0, "TMA row stride must be a multiple of 16 bytes");
+  CUtensorMap m;
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)ptr, dims, strides,
+                           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw CudaError("cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return m;
+}
+
+template <int BN, int STAGES>
+void launch(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B, long long ldb, int M,
+            int N, int K, void* C, long long ldc, int out_kind, int splitk, cudaStream_t s) {
+  const CUtensorMap ma = make_map(A, M, K, lda, BM);
+  const CUtensorMap mb = make_map(B, N, K, ldb, BN);
+  const size_t smem = sizeof(TcSmem<BN, STAGES>) + 1024;
+  static bool attr = false;
+  if (!attr) {
+    A2_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  const int nk_total = (K + BK - 1) / BK;
+  splitk = std::max(1, std::min(splitk, nk_total));
+  TcArgs args;
+  args.M = M; args.N = N; args.K = K;
+  args.kblocks_per_split = (nk_total + splitk - 1) / splitk;
+  splitk = (nk_total + args.kblocks_per_split - 1) / args.kblocks_per_split;
+  args.C = C; args.ldc = ldc; args.out_kind = out_kind;
+  dim3 grid(cdiv(M, BM), cdiv(N, BN), splitk);
+  A2_REQUIRE(grid.y < 65536 && grid.z < 65536, "tcgen05 grid too large");
+  tc_gemm_kernel<BN, STAGES><<<grid, 128, smem, s>>>(ma, mb, args);
+  A2_CHECK_LAUNCH();
+}
+
+}  // namespace tc
+
+bool tc_available() { return true; }
+
+int tc_error_flag(bool reset) {
+  int v = 0;
+  A2_CUDA(cudaMemcpyFromSymbol(&v, tc::g_tc_error, sizeof(int)));
+  if (reset && v) {
+    int z = 0;
+    A2_CUDA(cudaMemcpyToSymbol(tc::g_tc_error, &z, sizeof(int)));
+  }
+  return v;
+}
+
+void tc_gemm_bf16(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B, long long ldb,
+                  int M, int N, int K, void* C, long long ldc, int out_kind, int splitk,
+                  cudaStream_t s) {
+  if (M <= 0 || N <= 0) return;
+  A2_REQUIRE(K >= 1, "K >= 1");
+  if (out_kind == tc::OUT_F32_ATOMIC || splitk > 1)
+    A2_REQUIRE(out_kind == tc::OUT_F32_ATOMIC, "split-K needs atomic FP32 output");
+  if (N <= 128) tc::launch<128, 3>(A, lda, B, ldb, M, N, K, C, ldc, out_kind, splitk, s);
+  else tc::launch<256, 2>(A, lda, B, ldb, M, N, K, C, ldc, out_kind, splitk, s);
+}
+
+// -------------------------------------------------------------- BF16 H_eff chain
+void tc_heff_bf16(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int Dl, int Dr,
+                  const __nv_bfloat16* Lb, long long ldl, const __nv_bfloat16* Rb, long long ldr,
+                  const double* x, float* y, const SparseRows<float>& W1,
+                  const SparseRows<float>& W2, DevBuf& t1, DevBuf& t2, DevBuf& xa) {
+  const long long NX = (long long)n1 * n2 * Dr;          // columns of S1
+  const long long ldx = pad8(Dl);
+  const long long s1 = (long long)Dl * Rl * NX;
+  const long long s2 = (long long)Dl * R1 * NX;
+  const long long K4 = (long long)Rr * Dr;
+  const long long ld3 = pad8(K4);
+  const long long s3 = (long long)Dl * n1 * n2 * ld3;
+  xa.ensure(sizeof(__nv_bfloat16) * (size_t)NX * ldx, s);
+  t1.ensure(sizeof(__nv_bfloat16) * (size_t)std::max(s1, s3), s);
+  t2.ensure(sizeof(__nv_bfloat16) * (size_t)s2, s);
+  __nv_bfloat16* XT = xa.as<__nv_bfloat16>();
+  __nv_bfloat16* T1 = t1.as<__nv_bfloat16>();
+  __nv_bfloat16* T2 = t2.as<__nv_bfloat16>();
+  __nv_bfloat16* T3 = t1.as<__nv_bfloat16>();
+  // x [Dl][(t1 t2 b')] -> XT [(t1 t2 b')][a'] (row stride ldx)
+  // (pad columns a' >= Dl are never read: the tensor map's K extent is Dl)
+  transpose2d_ld<double, __nv_bfloat16>(x, XT, Dl, (int)NX, ldx, s);
+  // S1: T1[(a w)][(t1 t2 b')] = sum_a' L[(a w)][a'] XT[(t1 t2 b')][a']
+  {
+    const double M = (double)Dl * Rl, N = (double)NX, K = Dl;
+    ProfScope ps(PK_TC_S1, s, 2.0 * M * N * K, 2.0 * (M * K + N * K + M * N));
+    tc_gemm_bf16(Lb, ldl, XT, ldx, Dl * Rl, (int)NX, Dl, T1, NX, tc::OUT_BF16, 1, s);
+  }
+  {  // S2
+    ProfScope ps(PK_SPARSE_S2, s, 2.0 * W1.nnz_total * (double)n2 * Dr * Dl,
+                 2.0 * (double)(s1 + s2));
+    SparseGeom gm;
+    gm.veclen = n2 * Dr;
+    gm.in_sw = NX; gm.in_st = (long long)n2 * Dr;
+    gm.out_sw = NX; gm.out_ss = (long long)n2 * Dr;
+    gm.B1 = Dl; gm.in_b1 = (long long)Rl * NX; gm.out_b1 = (long long)R1 * NX;
+    sparse_rows_apply<__nv_bfloat16, __nv_bfloat16, float>(W1, gm, T1, T2, s);
+  }
+  {  // S3 -> T3[(a s1 s2)][(w2 b')] with row stride ld3
+    ProfScope ps(PK_SPARSE_S3, s, 2.0 * W2.nnz_total * (double)Dr * Dl * n1,
+                 2.0 * (double)s2 + 2.0 * (double)Dl * n1 * n2 * Rr * Dr);
+    SparseGeom gm;
+    gm.veclen = Dr;
+    gm.in_sw = NX; gm.in_st = Dr;
+    gm.out_sw = Dr; gm.out_ss = ld3;
+    gm.B1 = Dl; gm.B2 = n1;
+    gm.in_b1 = (long long)R1 * NX; gm.in_b2 = (long long)n2 * Dr;
+    gm.out_b1 = (long long)n1 * n2 * ld3; gm.out_b2 = (long long)n2 * ld3;
+    sparse_rows_apply<__nv_bfloat16, __nv_bfloat16, float>(W2, gm, T2, T3, s);
+  }
+  // S4: y[(a s1 s2)][b] = sum_{(w2 b')} T3 HR[b][(w2 b')]   (split K, atomic FP32)
+  const int M4 = Dl * n1 * n2;
+  const long long tiles = (long long)cdiv(M4, 128) * cdiv(Dr, Dr <= 128 ? 128 : 256);
+  int splitk = (int)std::max<long long>(1, 2 * 152 / std::max<long long>(1, tiles));
+  splitk = std::min<int>(splitk, std::max<int>(1, (int)(K4 / (8 * 64))));
+  {
+    const double M = M4, N = Dr, K = (double)K4;
+    ProfScope ps(PK_TC_S4, s, 2.0 * M * N * K, 2.0 * (M * K + N * K) + 4.0 * M * N);
+    fill_zero(y, sizeof(float) * (size_t)M4 * Dr, s);
+    tc_gemm_bf16(T3, ld3, Rb, ldr, M4, Dr, (int)K4, y, Dr, tc::OUT_F32_ATOMIC, splitk, s);
+  }
+}
+
 }  // namespace a2

@@ -7,12 +7,25 @@ namespace a2 {
 
 // True when this build carries the tcgen05 kernels (sm_103a).
 bool tc_available();
+// Device error flag of the tcgen05 kernels (nonzero: a bounded wait gave up).
+int tc_error_flag(bool reset);
 
-// y = H_eff x with BF16 operands and FP32 accumulation on tcgen05 (S1, S4) and the
-// sparse MPO stages in FP32 (S2, S3).  FP64 L, R, x in; FP64 y out (device).
-void tc_heff_apply(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int Dl, int Dr,
-                   const double* L, const double* R, const double* x, double* y,
-                   const SparseRows<float>& W1, const SparseRows<float>& W2, DevBuf& t1,
-                   DevBuf& t2, DevBuf& t3, DevBuf& xa, DevBuf& ya, DevBuf& cb);
+// C[m][n] (=|+=atomic) sum_k A[m][k] B[n][k]; A: M x K (row stride lda), B: N x K
+// (row stride ldb), both BF16 with 16-byte aligned bases and row strides that are
+// multiples of 8 elements.  out_kind: 0 = BF16 store, 1 = FP32 store, 2 = FP32 atomic
+// add (required when splitk > 1; C must be zeroed by the caller).
+void tc_gemm_bf16(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B, long long ldb,
+                  int M, int N, int K, void* C, long long ldc, int out_kind, int splitk,
+                  cudaStream_t s);
+
+// y = H_eff x: BF16 environments Lb [(a w)][a'] (row stride ldl) and Rb [b][(w2 b')]
+// (row stride ldr), FP64 x in, FP32 y out; intermediates T1..T3 in BF16 with FP32
+// accumulation inside each stage.
+void tc_heff_bf16(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int Dl, int Dr,
+                  const __nv_bfloat16* Lb, long long ldl, const __nv_bfloat16* Rb, long long ldr,
+                  const double* x, float* y, const SparseRows<float>& W1,
+                  const SparseRows<float>& W2, DevBuf& t1, DevBuf& t2, DevBuf& xa);
+
+inline long long pad8(long long x) { return (x + 7) / 8 * 8; }
 
 }  // namespace a2

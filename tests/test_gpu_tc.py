@@ -1,0 +1,80 @@
+"""tcgen05 tensor-core path: the BF16 GEMM stages against their plain definition
+(FP64 products of the same BF16 inputs) and the BF16 H_eff chain / sweep against
+the oracle.  C-ABI calls."""
+import numpy as np
+import pytest
+
+from oracle.env import heff_apply as oracle_heff
+from synthetic import chemistry_integrals, chemistry_mpo, random_tt_cores
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2505_23429_gb300 as a2  # noqa: E402
+from gpu_common import dev, host, rel  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = a2.Context(0)
+    yield c
+    assert a2.device_error(c) == 0
+    c.close()
+
+
+def _bf16(rows, k, ld, seed):
+    g = torch.Generator().manual_seed(seed)
+    full = torch.zeros(rows, ld, dtype=torch.bfloat16)
+    full[:, :k] = torch.randn(rows, k, generator=g).to(torch.bfloat16)
+    return full
+
+
+@pytest.mark.parametrize("M,N,K,splitk", [
+    (128, 128, 64, 1), (256, 256, 256, 1), (200, 300, 72, 1), (1000, 130, 520, 1),
+    (129, 257, 8, 1), (64, 40, 16, 1), (4096, 256, 8192, 8), (333, 96, 1000, 3),
+    (512, 2048, 256, 1)])
+def test_gemm_bf16_matches_definition(ctx, M, N, K, splitk):
+    ld = (K + 7) // 8 * 8
+    A = _bf16(M, K, ld, 1)
+    B = _bf16(N, K, ld, 2)
+    C = torch.zeros(M, N, dtype=torch.float32, device="cuda")
+    Ad, Bd = A.cuda(), B.cuda()
+    torch.cuda.synchronize()
+    a2.gemm_bf16(ctx, Ad, Bd, C, K=K, splitk=splitk)
+    ref = A[:, :K].double().numpy() @ B[:, :K].double().numpy().T
+    got = C.cpu().double().numpy()
+    err = np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-30)
+    assert err < 2e-5, err
+
+
+@pytest.mark.parametrize("k,Dl,Dr", [(0, 1, 16), (2, 16, 64), (3, 64, 16), (1, 4, 64)])
+def test_heff_bf16_chemistry(ctx, k, Dl, Dr):
+    h, eri = chemistry_integrals(6, 2505)
+    m = chemistry_mpo(h, eri)
+    mpo = a2.MPO(ctx, m)
+    rng = np.random.default_rng(k)
+    Lh = rng.standard_normal((Dl, m[k].shape[0], Dl))
+    Rh = rng.standard_normal((Dr, m[k + 1].shape[3], Dr))
+    x = rng.standard_normal((Dl, 4, 4, Dr))
+    ref = oracle_heff(Lh, m[k], m[k + 1], Rh, x)
+    y = torch.zeros(x.shape, dtype=torch.float64, device="cuda")
+    a2.heff_apply(ctx, mpo, k, dev(Lh), dev(Rh), dev(x), y, prec="bf16")
+    assert rel(host(y, ctx), ref) < 2e-2
+
+
+def test_bf16_sweep_energy_within_1e6_of_fp64(ctx):
+    h, eri = chemistry_integrals(6, 2505)
+    m = chemistry_mpo(h, eri)
+    mpo = a2.MPO(ctx, m)
+    raw = random_tt_cores([4] * 6, 4, 23429)
+    res = {}
+    for prec in ("fp64", "bf16"):
+        t = a2.TT.from_cores(ctx, raw)
+        t.left_orthogonalize()
+        for _ in range(4):
+            a2.additive_sweep(ctx, t, mpo, 3, partition=[2, 2, 1], D_max=64, prec=prec,
+                              svd_tol=1e-10, eig_tol=1e-8, coarse_eps=1e-10)
+        res[prec] = a2.energy(ctx, t, mpo, "fp64")[0]
+    assert abs(res["bf16"] - res["fp64"]) < 1e-6
