@@ -197,6 +197,28 @@ a2_status a2_device_error(a2_ctx* ctx, int reset, int* code_out);
 a2_status a2_profile(a2_ctx* ctx, int op, int kind, long long* launches, double* ms,
                      double* flops, double* bytes);
 
+/* Allocation-free variant of a2_heff_apply (FP64 contraction only).  The paper has
+ * no counterpart: this entry point exists for callers that cannot allocate device
+ * memory while they run -- for example applications whose GPU memory belongs to
+ * their own pool or fixed budget, or loops that must not stall on an allocator.
+ * It takes the same arguments as a2_heff_apply (minus the precision) and computes
+ * the same y, but all of its intermediate tensors live in one fixed device array
+ * built into the library (4 Mi doubles = 32 MiB, reserved on every GPU that loads
+ * the library until the process exits).  It never calls cudaMalloc or cudaFree.
+ *  - Size limit: the intermediates need max(s1, s3) + s2 doubles with
+ *    s1 = Dl*R_k*n_k*n_k+1*Dr, s2 = Dl*R_k+1*n_k*n_k+1*Dr, s3 = Dl*n_k*n_k+1*R_k+2*Dr
+ *    (R_j = MPO bond j); anything above 4 Mi doubles is rejected with A2_EINVAL and
+ *    a message naming both numbers.
+ *  - The first call on a device looks up the device address of the array (this can
+ *    load the library's device code); make that first call before any CUDA stream
+ *    capture.
+ *  - Every call shares the one array and leaves its contents behind; each call
+ *    overwrites everything it reads.  Calls whose work overlaps on the GPU (other
+ *    streams, other contexts on the same device) race on the array: order them.
+ *  - y is overwritten (zeroed first when the last stage splits its reduction). */
+a2_status a2_heff_apply_noalloc(a2_ctx* ctx, const a2_mpo* mpo, int k, int Dl, int Dr,
+                                const double* L, const double* R, const double* x, double* y);
+
 #ifdef __cplusplus
 }
 #endif

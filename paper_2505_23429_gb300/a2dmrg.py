@@ -85,6 +85,8 @@ def lib():
         "a2_device_error": [_P, ctypes.c_int, _I],
         "a2_profile": [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _D, _D,
                        _D],
+        "a2_heff_apply_noalloc": [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P,
+                                  _P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -104,7 +106,7 @@ def exported_symbols():
             "a2_tt_destroy", "a2_mpo_load", "a2_mpo_nnz", "a2_mpo_destroy",
             "a2_additive_sweep", "a2_classical_sweep", "a2_coarse_solve", "a2_energy",
             "a2_heff_apply", "a2_env_update", "a2_svd_split", "a2_gemm_bf16",
-            "a2_device_error", "a2_profile"]
+            "a2_device_error", "a2_profile", "a2_heff_apply_noalloc"]
 
 
 def _dp(a):
@@ -346,3 +348,12 @@ def profile(ctx, op, kind=0):
     if code == 3:
         return dict(launches=n.value, ms=ms.value, flops=fl.value, bytes=by.value)
     return None
+
+
+def heff_apply_noalloc(ctx, mpo, k, Lenv, Renv, x, y):
+    """Same as heff_apply(..., prec="fp64") but with no device allocation: the
+    intermediates live in a fixed 32 MiB array inside the library (for callers
+    that cannot allocate while they run).  Larger problems raise A2Error."""
+    Dl, Dr = Lenv.shape[0], Renv.shape[0]
+    ctx.check(lib().a2_heff_apply_noalloc(ctx._h, mpo._h, k, Dl, Dr, _ptr(Lenv), _ptr(Renv),
+                                          _ptr(x), _ptr(y)))

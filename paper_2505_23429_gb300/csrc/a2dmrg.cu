@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -1568,3 +1569,112 @@ a2_status a2_svd_split(a2_ctx* c, int Dl, int n1, int n2, int Dr, const double* 
 }
 
 }  // extern "C"
+
+// ============================================================================= allocation-free H_eff
+// A second way to apply H_eff for callers that must not allocate device memory
+// while they run: applications whose device memory is owned by their own pool or
+// budget, code that replays fixed work inside latency-critical loops, or callers
+// in a process where cudaMalloc is disallowed once set-up is over.  The regular
+// entry point grows its intermediate buffers on demand; this one instead uses one
+// fixed scratch array compiled into the library.
+//
+// The scratch array below is a file-scope device array, so every GPU that loads the
+// library reserves it until the process exits.  In host code its name is only a
+// host-side stand-in for the symbol, never a device address: the real device address
+// is looked up with cudaGetSymbolAddress once per device and then passed to the
+// kernels.
+namespace {
+
+constexpr long long kNoAllocScratchDoubles = 4LL << 20;   // 4 Mi doubles = 32 MiB
+static __device__ __align__(256) double g_heff_scratch[kNoAllocScratchDoubles];
+
+std::mutex g_scratch_mu;
+double* g_scratch_ptr[64] = {};
+
+// Device address of g_heff_scratch on `device` (looked up on first use).
+double* scratch_address(int device) {
+  A2_REQUIRE(device >= 0 && device < 64, "device index out of range");
+  std::lock_guard<std::mutex> g(g_scratch_mu);
+  if (!g_scratch_ptr[device]) {
+    int cur = -1;
+    A2_CUDA(cudaGetDevice(&cur));
+    if (cur != device) A2_CUDA(cudaSetDevice(device));
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_heff_scratch);
+    if (cur != device) cudaSetDevice(cur);
+    if (e != cudaSuccess || !p)
+      throw CudaError(std::string("cudaGetSymbolAddress(g_heff_scratch) failed: ") +
+                      cudaGetErrorString(e));
+    g_scratch_ptr[device] = static_cast<double*>(p);
+  }
+  return g_scratch_ptr[device];
+}
+
+}  // namespace
+
+extern "C" a2_status a2_heff_apply_noalloc(a2_ctx* c, const a2_mpo* m, int k, int Dl, int Dr,
+                                           const double* L, const double* R, const double* x,
+                                           double* y) {
+  if (!c || !m) return A2_EINVAL;
+  return guarded(c, [&] {
+    A2_REQUIRE(k >= 0 && k + 1 < m->L && Dl >= 1 && Dr >= 1 && L && R && x && y,
+               "a2_heff_apply_noalloc: bad arguments");
+    const SiteOps& A1 = m->site[k];
+    const SiteOps& A2 = m->site[k + 1];
+    const int n1 = A1.n, n2 = A2.n, Rl = A1.Rl, R1 = A1.Rr, Rr = A2.Rr;
+    const long long s1 = (long long)Dl * Rl * n1 * n2 * Dr;
+    const long long s2 = (long long)Dl * R1 * n1 * n2 * Dr;
+    const long long s3 = (long long)Dl * n1 * n2 * Rr * Dr;
+    const long long need = std::max(s1, s3) + s2;
+    if (need > kNoAllocScratchDoubles)
+      throw ArgError("a2_heff_apply_noalloc: intermediates need " + std::to_string(need) +
+                     " doubles, the fixed scratch holds " +
+                     std::to_string(kNoAllocScratchDoubles) +
+                     " (use a2_heff_apply for this size)");
+    double* T1 = scratch_address(c->device);
+    double* T2 = T1 + std::max(s1, s3);
+    double* T3 = T1;
+    cudaStream_t s = c->stream;
+    const long long N1 = (long long)n1 * n2 * Dr;
+    {  // S1: T1[(a w)][(t1 t2 b')] = sum_a' L[(a w)][a'] x[a'][(t1 t2 b')]
+      SimtGemm<double, double> g;
+      g.M = Dl * Rl; g.N = (int)N1; g.K = Dl;
+      g.A = L; g.sam = Dl; g.sak = 1;
+      g.B = x; g.sbn = 1; g.sbk = N1;
+      g.C = T1; g.scm = N1; g.scn = 1;
+      simt_gemm(g, s);
+    }
+    {  // S2: MPO core k on rows (w, t1) -> (w1, s1)
+      SparseGeom gm;
+      gm.veclen = n2 * Dr;
+      gm.in_sw = (long long)n1 * n2 * Dr; gm.in_st = (long long)n2 * Dr;
+      gm.out_sw = (long long)n1 * n2 * Dr; gm.out_ss = (long long)n2 * Dr;
+      gm.B1 = Dl; gm.in_b1 = (long long)Rl * n1 * n2 * Dr;
+      gm.out_b1 = (long long)R1 * n1 * n2 * Dr;
+      sparse_rows_apply<double, double, double>(A1.lr.rows<double>(), gm, T1, T2, s);
+    }
+    {  // S3: MPO core k+1 on rows (w1, t2) -> (w2, s2), batch (a, s1)
+      SparseGeom gm;
+      gm.veclen = Dr;
+      gm.in_sw = (long long)n1 * n2 * Dr; gm.in_st = Dr;
+      gm.out_sw = Dr; gm.out_ss = (long long)Rr * Dr;
+      gm.B1 = Dl; gm.B2 = n1;
+      gm.in_b1 = (long long)R1 * n1 * n2 * Dr; gm.in_b2 = (long long)n2 * Dr;
+      gm.out_b1 = (long long)n1 * n2 * Rr * Dr; gm.out_b2 = (long long)n2 * Rr * Dr;
+      sparse_rows_apply<double, double, double>(A2.lr.rows<double>(), gm, T2, T3, s);
+    }
+    {  // S4: y[(a s1 s2)][b] = sum_{(w2 b')} T3[(a s1 s2)][(w2 b')] R[b][(w2 b')]
+      SimtGemm<double, double> g;
+      g.M = Dl * n1 * n2; g.N = Dr; g.K = Rr * Dr;
+      g.A = T3; g.sam = g.K; g.sak = 1;
+      g.B = R; g.sbn = g.K; g.sbk = 1;
+      g.C = y; g.scm = Dr; g.scn = 1;
+      g.splitk = pick_splitk(g.M, g.N, g.K, 64);
+      if (g.splitk > 1) {
+        g.mode = GEMM_ATOMIC;
+        fill_zero(y, sizeof(double) * (size_t)g.M * g.N, s);   // atomics accumulate into y
+      }
+      simt_gemm(g, s);
+    }
+  });
+}
