@@ -45,6 +45,10 @@ def parse():
     p.add_argument("--config", default="chem_L16_D256")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--profile-matvec", action="store_true",
+                   help="small case for ncu: H_eff applications at the middle bond only")
+    p.add_argument("--D", type=int, default=128, help="bond dimension of --profile-matvec")
+    p.add_argument("--reps", type=int, default=3)
     return p.parse_args()
 
 
@@ -177,8 +181,34 @@ def est_iteration_flops(cfg, mpo, matvecs_per_bond=30):
     return tot
 
 
+def profile_matvec(args):
+    """H_eff at the middle bond of the L=16 chemistry MPO with random environments of
+    bond dimension --D: BF16 and FP32-accurate tensor-core chains, --reps times each."""
+    import torch
+    import paper_2505_23429_gb300 as a2
+    cfg, cores, _ = workload(args.config)
+    ctx = a2.Context(0)
+    mpo = a2.MPO(ctx, cores)
+    k = cfg["L"] // 2 - 1
+    D, n = args.D, cfg["n"]
+    g = torch.Generator(device="cuda").manual_seed(0)
+    HL = torch.randn(D, cores[k].shape[0], D, device="cuda", dtype=torch.float64, generator=g)
+    HR = torch.randn(D, cores[k + 1].shape[3], D, device="cuda", dtype=torch.float64, generator=g)
+    x = torch.randn(D, n, n, D, device="cuda", dtype=torch.float64, generator=g)
+    y = torch.empty_like(x)
+    torch.cuda.synchronize()
+    for prec in ("bf16", "f32emu"):
+        for _ in range(args.reps):
+            a2.heff_apply(ctx, mpo, k, HL, HR, x, y, prec=prec)
+    ctx.synchronize()
+    print(json.dumps(dict(profile_matvec=True, D=D, bond=k, error_flag=a2.device_error(ctx))))
+
+
 def main():
     args = parse()
+    if args.profile_matvec:
+        profile_matvec(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
@@ -247,10 +277,10 @@ def main():
     peaks = read_peaks()
     dom = max(prof, key=lambda k: prof[k]["ms"])
     d = prof[dom]
-    if dom in ("tc_s1", "tc_s4"):
+    if dom in ("tc_s1", "tc_s4", "emu_s1", "emu_s4"):
         bound, unit, peak = "tensor", "TFLOP/s", peaks["bf16_sus"]
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
-    elif dom in ("sparse_s2", "sparse_s3", "lanczos"):
+    elif dom in ("sparse_s2", "sparse_s3", "emu_s2", "emu_s3", "lanczos"):
         bound, unit, peak = "hbm", "GB/s", peaks["hbm"]
         achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
     elif dom in ("heff_simt", "env"):

@@ -46,11 +46,14 @@ typedef enum {
 
 typedef enum {
   A2_FP64 = 0, /* every contraction in FP64 */
-  A2_BF16 = 1, /* Lanczos matvecs on tcgen05 tensor cores (BF16 in, FP32 accumulate);
-                  environments, coarse matrices and Ritz refinement in FP32,
-                  vectors / SVD / coarse eigensolve in FP64 */
+  A2_BF16 = 1, /* Lanczos on tcgen05 tensor cores with BF16 operands to a residual of
+                  3e-3, then continued with the A2_F32EMU products to eig_tol;
+                  environments and coarse matrices in FP32, vectors / SVD /
+                  coarse eigensolve in FP64 */
   A2_TF32 = 2, /* reserved */
-  A2_FP32 = 3  /* every contraction in FP32 (SIMT), vectors / SVD / coarse in FP64 */
+  A2_FP32 = 3, /* every contraction in FP32 (SIMT), vectors / SVD / coarse in FP64 */
+  A2_F32EMU = 4 /* H_eff on tcgen05 with FP32-accurate products: operands split into
+                   three BF16 slices, six slice pairs accumulated in FP32 */
 } a2_precision;
 
 typedef struct a2_ctx a2_ctx;
@@ -192,7 +195,8 @@ a2_status a2_device_error(a2_ctx* ctx, int reset, int* code_out);
  * used to report achieved throughput per kernel class).  op: 0 = disable,
  * 1 = enable, 2 = reset totals, 3 = read the totals of `kind` (0 tcgen05 S1,
  * 1 sparse S2, 2 sparse S3, 3 tcgen05 S4, 4 SIMT H_eff, 5 environment update,
- * 6 Lanczos vector work, 7 truncated SVD, 8 LQ/QR) into the host outputs
+ * 6 Lanczos vector work, 7 truncated SVD, 8 LQ/QR, 9-12 the four stages of the
+ * FP32-accurate split-product H_eff) into the host outputs
  * (launches, milliseconds, algorithmic flops, algorithmic bytes; any may be NULL). */
 a2_status a2_profile(a2_ctx* ctx, int op, int kind, long long* launches, double* ms,
                      double* flops, double* bytes);

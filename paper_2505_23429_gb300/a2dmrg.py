@@ -13,7 +13,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liba2dmrg.so")
 
-PRECISION = {"fp64": 0, "bf16": 1, "tf32": 2, "fp32": 3}
+PRECISION = {"fp64": 0, "bf16": 1, "tf32": 2, "fp32": 3, "f32emu": 4}
 STATUS = {0: "A2_OK", -1: "A2_EINVAL", -2: "A2_ENOMEM", -3: "A2_ECUDA", -4: "A2_ENOCONV",
           -5: "A2_ENUMERIC", -6: "A2_ETIMEOUT", -7: "A2_EUNSUPPORTED"}
 
@@ -336,7 +336,7 @@ def device_error(ctx, reset=True):
 
 
 PROFILE_KINDS = ["tc_s1", "sparse_s2", "sparse_s3", "tc_s4", "heff_simt", "env", "lanczos",
-                 "svd", "lq"]
+                 "svd", "lq", "emu_s1", "emu_s2", "emu_s3", "emu_s4"]
 
 
 def profile(ctx, op, kind=0):

@@ -332,23 +332,32 @@ double env_flops(const SiteOps& so, int Dl, int Dr) {
          2.0 * (double)Dl * Dr * (double)so.nnz;
 }
 
-// BF16 environments with padded rows for TMA: L [(a w)][a'] -> ld pad8(Dl); R [b][(w2 b')]
+// BF16 environments with padded rows for TMA: L [(a w)][a'] -> ld pad8(Dl); R [b][(w2 b')].
+// With three planes each value is split into BF16 hi + mid + lo slices (plane 0 alone
+// is the plain BF16 rounding used by the BF16 matvec).
 struct Bf16Envs {
   DevBuf buf;
   const __nv_bfloat16* L = nullptr;
   const __nv_bfloat16* R = nullptr;
-  long long ldl = 0, ldr = 0;
+  long long ldl = 0, ldr = 0, lplane = 0, rplane = 0;
+  int planes = 0;
   template <typename T>
-  void set(a2_ctx* c, const T* Lf, int Dl, int Rl, const T* Rf, int Dr, int Rr) {
+  void set(a2_ctx* c, const T* Lf, int Dl, int Rl, const T* Rf, int Dr, int Rr, int np = 1) {
     ldl = pad8(Dl);
     ldr = pad8((long long)Rr * Dr);
-    const size_t nl = (size_t)Dl * Rl * ldl, nr = (size_t)Dr * ldr;
-    const size_t off = (nl + 63) / 64 * 64;   // keep R 128-byte aligned
-    buf.ensure(sizeof(__nv_bfloat16) * (off + nr), c->stream);
+    lplane = ((long long)Dl * Rl * ldl + 63) / 64 * 64;   // keep planes 128-byte aligned
+    rplane = ((long long)Dr * ldr + 63) / 64 * 64;
+    planes = np;
+    buf.ensure(sizeof(__nv_bfloat16) * (size_t)(np * (lplane + rplane)), c->stream);
     __nv_bfloat16* lb = buf.as<__nv_bfloat16>();
-    __nv_bfloat16* rb = lb + off;
-    convert_ld<T, __nv_bfloat16>(Lf, lb, (long long)Dl * Rl, Dl, ldl, c->stream);
-    convert_ld<T, __nv_bfloat16>(Rf, rb, Dr, (long long)Rr * Dr, ldr, c->stream);
+    __nv_bfloat16* rb = lb + np * lplane;
+    if (np == 1) {
+      convert_ld<T, __nv_bfloat16>(Lf, lb, (long long)Dl * Rl, Dl, ldl, c->stream);
+      convert_ld<T, __nv_bfloat16>(Rf, rb, Dr, (long long)Rr * Dr, ldr, c->stream);
+    } else {
+      split3_ld<T>(Lf, (long long)Dl * Rl, Dl, lb, ldl, lplane, c->stream);
+      split3_ld<T>(Rf, Dr, (long long)Rr * Dr, rb, ldr, rplane, c->stream);
+    }
     L = lb;
     R = rb;
   }
@@ -360,6 +369,17 @@ void heff_bf16(a2_ctx* c, const SiteOps& A1, const SiteOps& A2, const Bf16Envs& 
   c->ya.ensure(sizeof(float) * N, c->stream);
   tc_heff_bf16(c->stream, A1.n, A2.n, A1.Rl, A1.Rr, A2.Rr, Dl, Dr, E.L, E.ldl, E.R, E.ldr, x,
                c->ya.as<float>(), A1.lr.rows<float>(), A2.lr.rows<float>(), c->t1, c->t2, c->t3);
+  convert<float, double>(c->ya.as<float>(), y, N, c->stream);
+}
+
+void heff_emu(a2_ctx* c, const SiteOps& A1, const SiteOps& A2, const Bf16Envs& E, int Dl, int Dr,
+              const double* x, double* y) {
+  A2_REQUIRE(E.planes == 3, "split environments required");
+  const long long N = (long long)Dl * A1.n * A2.n * Dr;
+  c->ya.ensure(sizeof(float) * N, c->stream);
+  tc_heff_f32emu(c->stream, A1.n, A2.n, A1.Rl, A1.Rr, A2.Rr, Dl, Dr, E.L, E.ldl, E.lplane, E.R,
+                 E.ldr, E.rplane, x, c->ya.as<float>(), A1.lr.rows<float>(), A2.lr.rows<float>(),
+                 c->t1, c->t2, c->t3);
   convert<float, double>(c->ya.as<float>(), y, N, c->stream);
 }
 
@@ -437,6 +457,11 @@ struct Engine {
     flops += heff_flops(mpo->site[k], mpo->site[k + 1], Dl, Dr);
     ++matvecs;
     ++matvecs_bf16;
+  }
+  void matvec_emu(int k, int Dl, int Dr, const double* x, double* y) {
+    heff_emu(c, mpo->site[k], mpo->site[k + 1], bfe, Dl, Dr, x, y);
+    flops += heff_flops(mpo->site[k], mpo->site[k + 1], Dl, Dr);
+    ++matvecs;
   }
 };
 
@@ -776,19 +801,26 @@ struct Sweeper {
         eng.matvec(k, HLcur, HRk, Dl, Dr, in, out);
       };
       int nmv = 0;
+      LanczosResult lr;
+      bool done = false;
       if constexpr (sizeof(T) == 4) {
-        if (o.prec == A2_BF16) {
-          // tensor-core Lanczos on the BF16 operator to a loose tolerance, then the
-          // accurate (FP32) operator from that start vector to eig_tol
-          eng.bfe.set(c, HLcur, Dl, mpo->R[k], HRk, Dr, mpo->R[k + 2]);
-          auto mvb = [&](const double* in, double* out) { eng.matvec_bf16(k, Dl, Dr, in, out); };
-          LanczosResult lb = lanczos(c, mvb, x.as<double>(), N, std::max(o.eig_tol, kBf16Tol),
-                                     o.max_krylov, o.max_restarts);
-          nmv += lb.matvecs;
+        if (o.prec == A2_BF16 || o.prec == A2_F32EMU) {
+          eng.bfe.set(c, HLcur, Dl, mpo->R[k], HRk, Dr, mpo->R[k + 2], 3);
+          if (o.prec == A2_BF16) {
+            // tensor-core Lanczos on the BF16 operator to a loose tolerance ...
+            auto mvb = [&](const double* in, double* out) { eng.matvec_bf16(k, Dl, Dr, in, out); };
+            LanczosResult lb = lanczos(c, mvb, x.as<double>(), N, std::max(o.eig_tol, kBf16Tol),
+                                       o.max_krylov, o.max_restarts);
+            nmv += lb.matvecs;
+          }
+          // ... then FP32-accurate tensor-core products from that vector to eig_tol
+          auto mve = [&](const double* in, double* out) { eng.matvec_emu(k, Dl, Dr, in, out); };
+          lr = lanczos(c, mve, x.as<double>(), N, o.eig_tol, o.max_krylov, o.max_restarts);
+          done = true;
         }
       }
-      LanczosResult lr = lanczos(c, mv, x.as<double>(), N, o.eig_tol, o.max_krylov,
-                                 o.max_restarts);
+      if (!done)
+        lr = lanczos(c, mv, x.as<double>(), N, o.eig_tol, o.max_krylov, o.max_restarts);
       check_finite(lr.theta, "local eigenvalue");
       kry[k] = nmv + lr.matvecs;
       G.theta = lr.theta;
@@ -998,15 +1030,13 @@ struct Sweeper {
       if (rk[1] != 0) throw NumericError("coarse Jacobi did not converge");
     }
     check_finite(lam, "coarse eigenvalue");
-    // Step 4: compression of sum_j c_j tau(U~^j)
-    std::vector<View> terms;
-    std::vector<double> coef;
-    for (int j = 0; j < m; ++j) {
-      if (cvec[j] == 0.0) continue;
-      terms.push_back(j == 0 ? base_view(L) : gv[j - 1]);
-      coef.push_back(cvec[j]);
+    // Step 4: compression of sum_j c_j tau(U~^j) from its three-channel TT form
+    {
+      std::vector<DevBuf> X;
+      std::vector<int> xd;
+      structured_sum(groups, cvec, X, xd);
+      round_into_tt(X, xd);
     }
-    compress(terms, coef);
     if (rep) {
       rep->energy_in = A[0] / S[0];
       rep->lambda_coarse = lam;
@@ -1025,12 +1055,76 @@ struct Sweeper {
     }
   }
 
-  // TT-sum (block-diagonal cores) + TT rounding, result written into tt (left-orth, norm 1).
-  void compress(const std::vector<View>& terms, const std::vector<double>& coef) {
+  // Three-channel TT of sum_j c_j tau(U~^j) (j = 0: the iterate).  At bond l the
+  // channels are: P, the left-orthogonal prefix U_0..U_{l-1} shared by the iterate and
+  // by every group that has not started; A, the single group whose block contains
+  // bond l (its new cores, weighted by c_g when the channel opens); S, the
+  // right-orthogonal suffix V_l..V_{L-1} shared by every group whose block has ended.
+  // Each core is block upper-triangular in (P, A, S); bond <= D_P + D_A + D_S.
+  void structured_sum(const std::vector<Group>& groups, const std::vector<double>& cvec,
+                      std::vector<DevBuf>& X, std::vector<int>& xd) {
+    cudaStream_t s = c->stream;
+    const int P = (int)groups.size();
+    std::vector<int> act(L + 1, -1);   // active group at bond l
+    for (int g = 0; g < P; ++g)
+      for (int l = groups[g].kg + 1; l <= groups[g].mg + 1; ++l) act[l] = g;
+    std::vector<int> dP(L + 1, 0), dA(L + 1, 0), dS(L + 1, 0);
+    xd.assign(L + 1, 1);
+    for (int l = 1; l < L; ++l) {
+      A2_REQUIRE(act[l] >= 0, "structured sum: bond without an active group");
+      const Group& G = groups[act[l]];
+      dP[l] = tt->dims[l];
+      dA[l] = G.dl[l - G.kg];
+      dS[l] = (l > groups[0].mg + 1) ? kd[l] : 0;
+      xd[l] = dP[l] + dA[l] + dS[l];
+    }
+    X.clear();
+    X.resize(L);
+    for (int j = 0; j < L; ++j) {
+      const int n = tt->phys[j];
+      const int Dl = xd[j], Dr = xd[j + 1];
+      X[j].ensure(sizeof(double) * (size_t)Dl * n * Dr, s);
+      fill_zero(X[j].p, sizeof(double) * (size_t)Dl * n * Dr, s);
+      double* dst = X[j].as<double>();
+      const long long s0 = (long long)n * Dr, s1 = Dr;
+      const bool last = (j == L - 1);
+      // rows: P at 0, A at dP[j], S at dP[j] + dA[j]   (bond 0: P only)
+      const int rP = 0, rA = (j > 0) ? dP[j] : 0, rS = (j > 0) ? dP[j] + dA[j] : 0;
+      const int cP = 0, cA = last ? 0 : dP[j + 1], cS = last ? 0 : dP[j + 1] + dA[j + 1];
+      // P -> P (or P -> end for the iterate, weighted by c_0)
+      copy_block3(tt->cores[j].as<double>(), tt->dims[j], n, tt->dims[j + 1], dst, s0, s1, rP,
+                  cP, last ? cvec[0] : 1.0, s);
+      // P -> A: a group opens at site j
+      for (int g = 0; g < P; ++g)
+        if (groups[g].kg == j) {
+          const Group& G = groups[g];
+          copy_block3(G.cores[0].template as<double>(), G.dl[0], n, G.dr[0], dst, s0, s1, rP, cA,
+                      cvec[g + 1], s);
+        }
+      // A -> A / A -> S / A -> end
+      if (j > 0) {
+        const Group& G = groups[act[j]];
+        const int q = j - G.kg;
+        const bool closes = (j == G.mg + 1);
+        const int col = last ? 0 : (closes ? cS : cA);
+        copy_block3(G.cores[q].template as<double>(), G.dl[q], n, G.dr[q], dst, s0, s1, rA, col,
+                    1.0, s);
+      }
+      // S -> S / S -> end
+      if (j > 0 && dS[j] > 0)
+        copy_block3(Vc[j].as<double>(), kd[j], n, kd[j + 1], dst, s0, s1, rS, last ? 0 : cS, 1.0,
+                    s);
+    }
+  }
+
+  // TT-sum (block-diagonal cores) of the given views, for callers with explicit terms.
+  void plain_sum(const std::vector<View>& terms, const std::vector<double>& coef,
+                 std::vector<DevBuf>& X, std::vector<int>& xd) {
     cudaStream_t s = c->stream;
     const int nt = (int)terms.size();
-    std::vector<DevBuf> X(L);
-    std::vector<int> xd(L + 1, 0);
+    X.clear();
+    X.resize(L);
+    xd.assign(L + 1, 0);
     xd[0] = 1;
     xd[L] = 1;
     for (int j = 1; j < L; ++j) {
@@ -1052,8 +1146,11 @@ struct Sweeper {
         o2 += t.Dr[j];
       }
     }
-    if (nt == 1) {   // single term: only rounding of its ranks is needed
-    }
+  }
+
+  // TT rounding of X (right-to-left LQ, left-to-right truncated SVD), normalised, into tt.
+  void round_into_tt(std::vector<DevBuf>& X, std::vector<int>& xd) {
+    cudaStream_t s = c->stream;
     // right-to-left LQ sweep
     for (int j = L - 1; j >= 1; --j) {
       const int Dl = xd[j], n = tt->phys[j], Dr = xd[j + 1];
@@ -1387,8 +1484,8 @@ static a2_status run_sweep(a2_ctx* c, a2_tt* t, const a2_mpo* m, const a2_sweep_
     if (o->prec == A2_FP64) {
       Sweeper<double> sw(c, t, m, *o);
       sw.run(rep, classical);
-    } else if (o->prec == A2_FP32 || o->prec == A2_BF16) {
-      if (o->prec == A2_BF16 && !tc_available())
+    } else if (o->prec == A2_FP32 || o->prec == A2_BF16 || o->prec == A2_F32EMU) {
+      if (o->prec != A2_FP32 && !tc_available())
         throw ArgError("A2_BF16 needs the tcgen05 path, which this build lacks");
       Sweeper<float> sw(c, t, m, *o);
       sw.run(rep, classical);
@@ -1474,11 +1571,12 @@ a2_status a2_heff_apply(a2_ctx* c, const a2_mpo* m, int k, a2_precision prec, in
       convert<double, float>(x, c->xa.as<float>(), N, s);
       heff_T<float>(c, A1, A2, Lf, Rf, Dl, Dr, c->xa.as<float>(), c->ya.as<float>());
       convert<float, double>(c->ya.as<float>(), y, N, s);
-    } else if (prec == A2_BF16) {
-      A2_REQUIRE(tc_available(), "A2_BF16 needs the tcgen05 path");
+    } else if (prec == A2_BF16 || prec == A2_F32EMU) {
+      A2_REQUIRE(tc_available(), "this precision needs the tcgen05 path");
       Bf16Envs E;
-      E.set<double>(c, L, Dl, A1.Rl, R, Dr, A2.Rr);
-      heff_bf16(c, A1, A2, E, Dl, Dr, x, y);
+      E.set<double>(c, L, Dl, A1.Rl, R, Dr, A2.Rr, prec == A2_BF16 ? 1 : 3);
+      if (prec == A2_BF16) heff_bf16(c, A1, A2, E, Dl, Dr, x, y);
+      else heff_emu(c, A1, A2, E, Dl, Dr, x, y);
       A2_CUDA(cudaStreamSynchronize(s));
     } else {
       throw ArgError("unsupported precision");

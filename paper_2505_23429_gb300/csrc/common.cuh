@@ -81,6 +81,10 @@ enum ProfKind {
   PK_LANCZOS,        // Lanczos vector work (dots, updates, re-orthogonalisation)
   PK_SVD,            // truncated SVD step (Gram + eigensolve + products)
   PK_LQ,             // LQ / QR factorisations
+  PK_EMU_S1,         // tcgen05 S1 with FP32-accurate split products (6 BF16 pairs)
+  PK_EMU_S2,         // sparse S2 in FP32 (accurate matvec)
+  PK_EMU_S3,         // sparse S3 in FP32 with split BF16 output (accurate matvec)
+  PK_EMU_S4,         // tcgen05 S4 with split products
   PK_COUNT
 };
 void prof_enable(bool on);

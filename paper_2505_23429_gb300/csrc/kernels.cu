@@ -1,4 +1,5 @@
 // SIMT GEMM, sparse MPO action, vector and small dense kernels (sm_103a).
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -87,6 +88,11 @@ void prof_reset() {
   std::lock_guard<std::mutex> g(st.mu);
   st.drain();
   for (int k = 0; k < PK_COUNT; ++k) st.n[k] = 0, st.ms[k] = st.fl[k] = st.by[k] = 0.0;
+}
+
+static int grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  return (int)(g < 4096 ? (g > 0 ? g : 1) : 4096);
 }
 
 // ----------------------------------------------------------------------------- SIMT GEMM
@@ -229,10 +235,256 @@ __global__ void sparse_rows_kernel(SparseRows<V> sp, SparseGeom g, const TI* __r
   }
 }
 
+// Vectorised variant: each lane owns VEC consecutive vector elements (16-byte loads),
+// `lpr` lanes cover one row chunk of lpr*VEC elements, a warp serves 32/lpr rows at a
+// time.  Grid: x = row blocks, y = vector chunks, z = batch; consecutive CTAs share the
+// batch and chunk, so the input rows they re-read stay in L2.
+template <typename T> struct Vec16 { static constexpr int N = 16 / sizeof(T); };
+
+template <typename TI, typename A>
+__device__ __forceinline__ void load_vec(const TI* p, A (&x)[Vec16<TI>::N]) {
+  const uint4 raw = __ldg(reinterpret_cast<const uint4*>(p));
+  const TI* e = reinterpret_cast<const TI*>(&raw);
+#pragma unroll
+  for (int i = 0; i < Vec16<TI>::N; ++i) x[i] = load_as<A, TI>(e + i);
+}
+
+template <typename TO, typename A, int NV>
+__device__ __forceinline__ void store_vec(TO* p, const A (&x)[NV]) {
+  if constexpr (sizeof(TO) * NV == 16) {
+    __align__(16) TO t[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) t[i] = from_acc<TO, A>(x[i]);
+    *reinterpret_cast<uint4*>(p) = *reinterpret_cast<const uint4*>(t);
+  } else {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) p[i] = from_acc<TO, A>(x[i]);
+  }
+}
+
+template <typename TI, typename TO, typename V>
+__global__ void __launch_bounds__(256)
+sparse_rows_vec_kernel(SparseRows<V> sp, SparseGeom g, const TI* __restrict__ in,
+                       TO* __restrict__ out, int lpr, int rows_per_cta) {
+  using Acc = typename AccT<TO>::type;
+  constexpr int NV = Vec16<TI>::N;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rpw = 32 / lpr;                           // rows served by a warp at once
+  const int slot = lane / lpr, l = lane % lpr;
+  const int v0 = blockIdx.y * (lpr * NV) + l * NV;
+  const int bz = blockIdx.z;
+  const int b1 = bz / g.B2, b2 = bz % g.B2;
+  const long long ib = b1 * g.in_b1 + b2 * g.in_b2 + v0;
+  const long long ob = b1 * g.out_b1 + b2 * g.out_b2 + v0;
+  const int r_beg = blockIdx.x * rows_per_cta;
+  const int r_end = min(sp.nrows, r_beg + rows_per_cta);
+  const int step = (blockDim.x >> 5) * rpw;
+  if (v0 >= g.veclen) return;
+  for (int r = r_beg + warp * rpw + slot; r < r_end; r += step) {
+    Acc acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = Acc(0);
+    const int e1 = __ldg(sp.row_ptr + r + 1);
+    for (int e = __ldg(sp.row_ptr + r); e < e1; ++e) {
+      const long long ci = __ldg(sp.nz_w + e) * g.in_sw + __ldg(sp.nz_t + e) * g.in_st;
+      const Acc w = (Acc)__ldg(sp.nz_val + e);
+      Acc x[NV];
+      load_vec<TI, Acc>(in + ib + ci, x);
+#pragma unroll
+      for (int i = 0; i < NV; ++i) acc[i] = fma(w, x[i], acc[i]);
+    }
+    const long long ro = __ldg(sp.row_w + r) * g.out_sw + __ldg(sp.row_s + r) * g.out_ss;
+    store_vec<TO, Acc, NV>(out + ob + ro, acc);
+  }
+}
+
+// x = hi + mid + lo with each part rounded to BF16 (three 8-bit mantissa slices)
+template <typename A>
+__device__ __forceinline__ void split3(A x, __nv_bfloat16& h, __nv_bfloat16& m,
+                                       __nv_bfloat16& l) {
+  h = __float2bfloat16_rn((float)x);
+  const A r1 = x - (A)__bfloat162float(h);
+  m = __float2bfloat16_rn((float)r1);
+  const A r2 = r1 - (A)__bfloat162float(m);
+  l = __float2bfloat16_rn((float)r2);
+}
+
+// Same as sparse_rows_vec_kernel with the output split into three BF16 planes.
+template <typename TI, typename V>
+__global__ void __launch_bounds__(256)
+sparse_rows_split3_kernel(SparseRows<V> sp, SparseGeom g, const TI* __restrict__ in,
+                          __nv_bfloat16* __restrict__ out, long long plane, int lpr,
+                          int rows_per_cta) {
+  using Acc = float;
+  constexpr int NV = Vec16<TI>::N;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rpw = 32 / lpr;
+  const int slot = lane / lpr, l = lane % lpr;
+  const int v0 = blockIdx.y * (lpr * NV) + l * NV;
+  const int bz = blockIdx.z;
+  const int b1 = bz / g.B2, b2 = bz % g.B2;
+  const long long ib = b1 * g.in_b1 + b2 * g.in_b2 + v0;
+  const long long ob = b1 * g.out_b1 + b2 * g.out_b2 + v0;
+  const int r_beg = blockIdx.x * rows_per_cta;
+  const int r_end = min(sp.nrows, r_beg + rows_per_cta);
+  const int step = (blockDim.x >> 5) * rpw;
+  if (v0 >= g.veclen) return;
+  for (int r = r_beg + warp * rpw + slot; r < r_end; r += step) {
+    Acc acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = Acc(0);
+    const int e1 = __ldg(sp.row_ptr + r + 1);
+    for (int e = __ldg(sp.row_ptr + r); e < e1; ++e) {
+      const long long ci = __ldg(sp.nz_w + e) * g.in_sw + __ldg(sp.nz_t + e) * g.in_st;
+      const Acc w = (Acc)__ldg(sp.nz_val + e);
+      Acc x[NV];
+      load_vec<TI, Acc>(in + ib + ci, x);
+#pragma unroll
+      for (int i = 0; i < NV; ++i) acc[i] = fma(w, x[i], acc[i]);
+    }
+    const long long ro = __ldg(sp.row_w + r) * g.out_sw + __ldg(sp.row_s + r) * g.out_ss;
+    __nv_bfloat16* o = out + ob + ro;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      __nv_bfloat16 h, m, lo;
+      split3<Acc>(acc[i], h, m, lo);
+      o[i] = h;
+      o[plane + i] = m;
+      o[2 * plane + i] = lo;
+    }
+  }
+}
+
+// scalar fallback of the split3 stage (rows not 16-byte aligned)
+template <typename TI, typename V>
+__global__ void sparse_rows_split3_scalar(SparseRows<V> sp, SparseGeom g, const TI* __restrict__ in,
+                                          __nv_bfloat16* __restrict__ out, long long plane,
+                                          int rows_per_cta) {
+  const int r0 = blockIdx.x * rows_per_cta;
+  const int b1 = blockIdx.y / g.B2, b2 = blockIdx.y % g.B2;
+  const long long ib = b1 * g.in_b1 + b2 * g.in_b2;
+  const long long ob = b1 * g.out_b1 + b2 * g.out_b2;
+  const int nr = min(rows_per_cta, sp.nrows - r0);
+  for (int it = threadIdx.x; it < nr * g.veclen; it += blockDim.x) {
+    const int r = r0 + it / g.veclen, v = it % g.veclen;
+    float acc = 0.f;
+    for (int e = sp.row_ptr[r]; e < sp.row_ptr[r + 1]; ++e)
+      acc += (float)sp.nz_val[e] * load_as<float, TI>(in + ib + sp.nz_w[e] * g.in_sw +
+                                                        sp.nz_t[e] * g.in_st + v);
+    const long long o = ob + sp.row_w[r] * g.out_sw + sp.row_s[r] * g.out_ss + v;
+    __nv_bfloat16 h, m, l;
+    split3<float>(acc, h, m, l);
+    out[o] = h;
+    out[plane + o] = m;
+    out[2 * plane + o] = l;
+  }
+}
+
+template <typename TI, typename V>
+void sparse_rows_apply_split3(const SparseRows<V>& sp, const SparseGeom& g, const TI* in,
+                              __nv_bfloat16* out, long long plane, cudaStream_t s) {
+  if (sp.nrows == 0 || g.veclen == 0) return;
+  constexpr int NV = Vec16<TI>::N;
+  auto al = [](long long x) { return x % NV == 0; };
+  if (!(al(g.veclen) && al(g.in_sw) && al(g.in_st) && al(g.in_b1) && al(g.in_b2) &&
+        reinterpret_cast<uintptr_t>(in) % 16 == 0)) {
+    const int rows = std::min(64, std::max(1, 2048 / g.veclen));
+    dim3 grid(cdiv(sp.nrows, rows), g.B1 * g.B2);
+    A2_REQUIRE(grid.y < 65536, "sparse grid too large");
+    sparse_rows_split3_scalar<TI, V><<<grid, 256, 0, s>>>(sp, g, in, out, plane, rows);
+    A2_CHECK_LAUNCH();
+    return;
+  }
+  int lpr = 1;
+  while (lpr < 32 && lpr * NV < g.veclen) lpr *= 2;
+  dim3 grid(cdiv(sp.nrows, 64), cdiv(g.veclen, lpr * NV), g.B1 * g.B2);
+  A2_REQUIRE(grid.y < 65536 && grid.z < 65536, "sparse grid too large");
+  sparse_rows_split3_kernel<TI, V><<<grid, 256, 0, s>>>(sp, g, in, out, plane, lpr, 64);
+  A2_CHECK_LAUNCH();
+}
+template void sparse_rows_apply_split3<float, float>(const SparseRows<float>&, const SparseGeom&,
+                                                     const float*, __nv_bfloat16*, long long,
+                                                     cudaStream_t);
+
+template <typename TI>
+__global__ void split3_ld_kernel(const TI* in, long long rows, long long cols,
+                                 __nv_bfloat16* out, long long ld, long long plane) {
+  const long long n = rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / cols, c = e % cols;
+    __nv_bfloat16 h, m, l;
+    split3<double>((double)in[e], h, m, l);
+    const long long o = r * ld + c;
+    out[o] = h;
+    out[plane + o] = m;
+    out[2 * plane + o] = l;
+  }
+}
+template <typename TI>
+void split3_ld(const TI* in, long long rows, long long cols, __nv_bfloat16* out, long long ld,
+               long long plane, cudaStream_t s) {
+  if (!rows || !cols) return;
+  split3_ld_kernel<TI><<<grid_for(rows * cols), 256, 0, s>>>(in, rows, cols, out, ld, plane);
+  A2_CHECK_LAUNCH();
+}
+template void split3_ld<float>(const float*, long long, long long, __nv_bfloat16*, long long,
+                               long long, cudaStream_t);
+template void split3_ld<double>(const double*, long long, long long, __nv_bfloat16*, long long,
+                                long long, cudaStream_t);
+
+// out planes (cols x ld) = split3 of in^T, in: rows x cols row-major FP64
+__global__ void transpose_split3_kernel(const double* in, int rows, int cols,
+                                        __nv_bfloat16* out, long long ld, long long plane) {
+  __shared__ double tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int r = by + j, c = bx + threadIdx.x;
+    if (r < rows && c < cols) tile[j][threadIdx.x] = in[(long long)r * cols + c];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int c = bx + j, r = by + threadIdx.x;
+    if (r < rows && c < cols) {
+      __nv_bfloat16 h, m, l;
+      split3<double>(tile[threadIdx.x][j], h, m, l);
+      const long long o = (long long)c * ld + r;
+      out[o] = h;
+      out[plane + o] = m;
+      out[2 * plane + o] = l;
+    }
+  }
+}
+void transpose_split3(const double* in, int rows, int cols, __nv_bfloat16* out, long long ld,
+                      long long plane, cudaStream_t s) {
+  if (!rows || !cols) return;
+  dim3 grid(cdiv(cols, 32), cdiv(rows, 32));
+  A2_REQUIRE(grid.y < 65536, "transpose grid too large");
+  transpose_split3_kernel<<<grid, dim3(32, 8), 0, s>>>(in, rows, cols, out, ld, plane);
+  A2_CHECK_LAUNCH();
+}
+
 template <typename TI, typename TO, typename V>
 void sparse_rows_apply(const SparseRows<V>& sp, const SparseGeom& g, const TI* in, TO* out,
                        cudaStream_t s) {
   if (sp.nrows == 0 || g.veclen == 0) return;
+  constexpr int NV = Vec16<TI>::N;
+  auto al = [](long long x) { return x % NV == 0; };
+  const bool vec_ok = al(g.veclen) && al(g.in_sw) && al(g.in_st) && al(g.out_sw) &&
+                      al(g.out_ss) && al(g.in_b1) && al(g.in_b2) && al(g.out_b1) &&
+                      al(g.out_b2) && (reinterpret_cast<uintptr_t>(in) % 16 == 0) &&
+                      (reinterpret_cast<uintptr_t>(out) % (sizeof(TO) * NV) == 0);
+  if (vec_ok) {
+    int lpr = 1;
+    while (lpr < 32 && lpr * NV < g.veclen) lpr *= 2;
+    const int chunks = cdiv(g.veclen, lpr * NV);
+    const int rows = 64;
+    dim3 grid(cdiv(sp.nrows, rows), chunks, g.B1 * g.B2);
+    A2_REQUIRE(grid.y < 65536 && grid.z < 65536, "sparse grid too large");
+    sparse_rows_vec_kernel<TI, TO, V><<<grid, 256, 0, s>>>(sp, g, in, out, lpr, rows);
+    A2_CHECK_LAUNCH();
+    return;
+  }
   int rows = max(1, 2048 / g.veclen);
   rows = min(rows, 64);
   dim3 grid(cdiv(sp.nrows, rows), g.B1 * g.B2);
@@ -323,10 +575,6 @@ __global__ void convert_ld_kernel(const TI* in, TO* out, long long rows, long lo
   }
 }
 
-static int grid_for(long long n) {
-  long long g = (n + 255) / 256;
-  return (int)(g < 4096 ? (g > 0 ? g : 1) : 4096);
-}
 
 template <typename TI, typename TO>
 void permute_swap01(const TI* in, TO* out, int d0, int d1, int d2, cudaStream_t s) {

@@ -53,6 +53,19 @@ template <typename TI, typename TO, typename V>
 void sparse_rows_apply(const SparseRows<V>& sp, const SparseGeom& g, const TI* in, TO* out,
                        cudaStream_t s);
 
+// Same action with the FP32 result written as three BF16 planes (hi, mid, lo) at
+// out, out + plane, out + 2*plane (rows of 16-byte aligned input required).
+template <typename TI, typename V>
+void sparse_rows_apply_split3(const SparseRows<V>& sp, const SparseGeom& g, const TI* in,
+                              __nv_bfloat16* out, long long plane, cudaStream_t s);
+// out planes [p][r*ld + c] = BF16 slice p of in[r*cols + c]  (x = hi + mid + lo)
+template <typename TI>
+void split3_ld(const TI* in, long long rows, long long cols, __nv_bfloat16* out, long long ld,
+               long long plane, cudaStream_t s);
+// out planes [p][c*ld + r] = BF16 slice p of in[r*cols + c]  (transpose and split)
+void transpose_split3(const double* in, int rows, int cols, __nv_bfloat16* out, long long ld,
+                      long long plane, cudaStream_t s);
+
 // ---- permutes and conversions
 // out[(i*d1 + j)*d2 + k] = in[(j*d0 + i)*d2 + k]   (swap the two outer dims, k contiguous)
 template <typename TI, typename TO>

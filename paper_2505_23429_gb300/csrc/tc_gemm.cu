@@ -135,6 +135,14 @@ struct TcArgs {
   void* C;
   long long ldc;
   int out_kind;
+  int npairs;              // operand pairs accumulated into one tile (split precision)
+  int pa[6], pb[6];        // A / B plane of each pair
+};
+
+// Up to three BF16 planes per operand (a value split into high, middle and low parts).
+struct TcMaps {
+  CUtensorMap a[3];
+  CUtensorMap b[3];
 };
 
 template <int BN, int STAGES>
@@ -150,8 +158,7 @@ struct TcSmem {
 
 template <int BN, int STAGES>
 __global__ void __launch_bounds__(128, 2)
-tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
-               TcArgs args) {
+tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // round the dynamic shared memory base up to 1024 bytes (swizzle atoms)
   const uint32_t base = smem_u32(smem_raw);
@@ -163,7 +170,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
   const int n0 = blockIdx.y * BN;
   const int nk_total = (args.K + BK - 1) / BK;
   const int kb0 = blockIdx.z * args.kblocks_per_split;
-  const int nk = max(0, min(nk_total - kb0, args.kblocks_per_split));
+  const int nkb = max(0, min(nk_total - kb0, args.kblocks_per_split));
+  const int np = args.npairs;
+  const int nk = nkb * np;          // pipeline steps: (K block, operand pair)
   constexpr uint32_t kStageBytes = (BM + BN) * BK * 2;
 
   if (threadIdx.x == 0) {
@@ -200,9 +209,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
         }
         if (*(volatile int*)&S.abort_flag) break;
         mbar_expect_tx(&S.full[s], kStageBytes);
-        const int kx = (kb0 + kb) * BK;
-        tma_load_2d(&map_a, &S.full[s], S.a[s], kx, m0);
-        tma_load_2d(&map_b, &S.full[s], S.b[s], kx, n0);
+        const int p = kb % np;
+        const int kx = (kb0 + kb / np) * BK;
+        tma_load_2d(&maps.a[args.pa[p]], &S.full[s], S.a[s], kx, m0);
+        tma_load_2d(&maps.b[args.pb[p]], &S.full[s], S.b[s], kx, n0);
         issued = kb + 1;
       }
       // on abort: wait (bounded) for the copies already issued before leaving
@@ -320,10 +330,19 @@ CUtensorMap make_map(const __nv_bfloat16* ptr, int rows, int K, long long ld, in
 }
 
 template <int BN, int STAGES>
-void launch(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B, long long ldb, int M,
-            int N, int K, void* C, long long ldc, int out_kind, int splitk, cudaStream_t s) {
-  const CUtensorMap ma = make_map(A, M, K, lda, BM);
-  const CUtensorMap mb = make_map(B, N, K, ldb, BN);
+void launch(const __nv_bfloat16* const* A, long long lda, const __nv_bfloat16* const* B,
+            long long ldb, int M, int N, int K, int npairs, const int* pa, const int* pb,
+            void* C, long long ldc, int out_kind, int splitk, cudaStream_t s) {
+  TcMaps maps;
+  int na = 0, nb = 0;
+  for (int p = 0; p < npairs; ++p) {
+    na = std::max(na, pa[p] + 1);
+    nb = std::max(nb, pb[p] + 1);
+  }
+  for (int i = 0; i < 3; ++i) {
+    maps.a[i] = make_map(A[i < na ? i : 0], M, K, lda, BM);
+    maps.b[i] = make_map(B[i < nb ? i : 0], N, K, ldb, BN);
+  }
   const size_t smem = sizeof(TcSmem<BN, STAGES>) + 1024;
   static bool attr = false;
   if (!attr) {
@@ -338,9 +357,14 @@ void launch(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B, long 
   args.kblocks_per_split = (nk_total + splitk - 1) / splitk;
   splitk = (nk_total + args.kblocks_per_split - 1) / args.kblocks_per_split;
   args.C = C; args.ldc = ldc; args.out_kind = out_kind;
+  args.npairs = npairs;
+  for (int p = 0; p < 6; ++p) {
+    args.pa[p] = p < npairs ? pa[p] : 0;
+    args.pb[p] = p < npairs ? pb[p] : 0;
+  }
   dim3 grid(cdiv(M, BM), cdiv(N, BN), splitk);
   A2_REQUIRE(grid.y < 65536 && grid.z < 65536, "tcgen05 grid too large");
-  tc_gemm_kernel<BN, STAGES><<<grid, 128, smem, s>>>(ma, mb, args);
+  tc_gemm_kernel<BN, STAGES><<<grid, 128, smem, s>>>(maps, args);
   A2_CHECK_LAUNCH();
 }
 
@@ -361,12 +385,24 @@ int tc_error_flag(bool reset) {
 void tc_gemm_bf16(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B, long long ldb,
                   int M, int N, int K, void* C, long long ldc, int out_kind, int splitk,
                   cudaStream_t s) {
+  const __nv_bfloat16* Ap[3] = {A, A, A};
+  const __nv_bfloat16* Bp[3] = {B, B, B};
+  const int p0[1] = {0};
+  tc_gemm_bf16_pairs(Ap, lda, Bp, ldb, M, N, K, 1, p0, p0, C, ldc, out_kind, splitk, s);
+}
+
+void tc_gemm_bf16_pairs(const __nv_bfloat16* const* A, long long lda,
+                        const __nv_bfloat16* const* B, long long ldb, int M, int N, int K,
+                        int npairs, const int* pa, const int* pb, void* C, long long ldc,
+                        int out_kind, int splitk, cudaStream_t s) {
   if (M <= 0 || N <= 0) return;
-  A2_REQUIRE(K >= 1, "K >= 1");
-  if (out_kind == tc::OUT_F32_ATOMIC || splitk > 1)
+  A2_REQUIRE(K >= 1 && npairs >= 1 && npairs <= 6, "tc GEMM: K >= 1, 1..6 operand pairs");
+  if (splitk > 1)
     A2_REQUIRE(out_kind == tc::OUT_F32_ATOMIC, "split-K needs atomic FP32 output");
-  if (N <= 128) tc::launch<128, 3>(A, lda, B, ldb, M, N, K, C, ldc, out_kind, splitk, s);
-  else tc::launch<256, 2>(A, lda, B, ldb, M, N, K, C, ldc, out_kind, splitk, s);
+  if (N <= 128)
+    tc::launch<128, 3>(A, lda, B, ldb, M, N, K, npairs, pa, pb, C, ldc, out_kind, splitk, s);
+  else
+    tc::launch<256, 2>(A, lda, B, ldb, M, N, K, npairs, pa, pb, C, ldc, out_kind, splitk, s);
 }
 
 // -------------------------------------------------------------- BF16 H_eff chain
@@ -429,6 +465,81 @@ void tc_heff_bf16(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int Dl
     ProfScope ps(PK_TC_S4, s, 2.0 * M * N * K, 2.0 * (M * K + N * K) + 4.0 * M * N);
     fill_zero(y, sizeof(float) * (size_t)M4 * Dr, s);
     tc_gemm_bf16(T3, ld3, Rb, ldr, M4, Dr, (int)K4, y, Dr, tc::OUT_F32_ATOMIC, splitk, s);
+  }
+}
+
+}  // namespace a2
+
+namespace a2 {
+
+// y = H_eff x with FP32-accurate tensor-core products: every BF16 GEMM operand is the
+// three-plane split of an FP32/FP64 value and six plane pairs are accumulated in TMEM;
+// the sparse MPO stages run in FP32.  L, R: three BF16 planes each (plane strides
+// lplane / rplane elements, row strides ldl / ldr).
+void tc_heff_f32emu(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int Dl, int Dr,
+                    const __nv_bfloat16* Lp, long long ldl, long long lplane,
+                    const __nv_bfloat16* Rp, long long ldr, long long rplane, const double* x,
+                    float* y, const SparseRows<float>& W1, const SparseRows<float>& W2,
+                    DevBuf& t1, DevBuf& t2, DevBuf& xa) {
+  static const int pa[6] = {0, 0, 1, 0, 1, 2};
+  static const int pb[6] = {0, 1, 0, 2, 1, 0};
+  const long long NX = (long long)n1 * n2 * Dr;
+  const long long ldx = pad8(Dl);
+  const long long xplane = NX * ldx;
+  const long long s1 = (long long)Dl * Rl * NX;
+  const long long s2 = (long long)Dl * R1 * NX;
+  const long long K4 = (long long)Rr * Dr;
+  const long long ld3 = pad8(K4);
+  const long long M4 = (long long)Dl * n1 * n2;
+  const long long plane3 = M4 * ld3;
+  xa.ensure(sizeof(__nv_bfloat16) * (size_t)(3 * xplane), s);
+  t1.ensure(std::max(sizeof(float) * (size_t)s1, sizeof(__nv_bfloat16) * (size_t)(3 * plane3)), s);
+  t2.ensure(sizeof(float) * (size_t)s2, s);
+  __nv_bfloat16* XT = xa.as<__nv_bfloat16>();
+  float* T1 = t1.as<float>();
+  float* T2 = t2.as<float>();
+  __nv_bfloat16* T3 = t1.as<__nv_bfloat16>();
+  transpose_split3(x, Dl, (int)NX, XT, ldx, xplane, s);
+  {  // S1
+    const __nv_bfloat16* A[3] = {Lp, Lp + lplane, Lp + 2 * lplane};
+    const __nv_bfloat16* B[3] = {XT, XT + xplane, XT + 2 * xplane};
+    const double M = (double)Dl * Rl, N = (double)NX, K = Dl;
+    ProfScope ps(PK_EMU_S1, s, 6.0 * 2.0 * M * N * K, 6.0 * (M * K + N * K) + 4.0 * M * N);
+    tc_gemm_bf16_pairs(A, ldl, B, ldx, Dl * Rl, (int)NX, Dl, 6, pa, pb, T1, NX, tc::OUT_F32, 1, s);
+  }
+  {  // S2 (FP32)
+    ProfScope ps(PK_EMU_S2, s, 2.0 * W1.nnz_total * (double)n2 * Dr * Dl,
+                 4.0 * (double)(s1 + s2));
+    SparseGeom gm;
+    gm.veclen = n2 * Dr;
+    gm.in_sw = NX; gm.in_st = (long long)n2 * Dr;
+    gm.out_sw = NX; gm.out_ss = (long long)n2 * Dr;
+    gm.B1 = Dl; gm.in_b1 = (long long)Rl * NX; gm.out_b1 = (long long)R1 * NX;
+    sparse_rows_apply<float, float, float>(W1, gm, T1, T2, s);
+  }
+  {  // S3 (FP32 in, three BF16 planes out)
+    ProfScope ps(PK_EMU_S3, s, 2.0 * W2.nnz_total * (double)Dr * Dl * n1,
+                 4.0 * (double)s2 + 6.0 * (double)M4 * K4);
+    SparseGeom gm;
+    gm.veclen = Dr;
+    gm.in_sw = NX; gm.in_st = Dr;
+    gm.out_sw = Dr; gm.out_ss = ld3;
+    gm.B1 = Dl; gm.B2 = n1;
+    gm.in_b1 = (long long)R1 * NX; gm.in_b2 = (long long)n2 * Dr;
+    gm.out_b1 = (long long)n1 * n2 * ld3; gm.out_b2 = (long long)n2 * ld3;
+    sparse_rows_apply_split3<float, float>(W2, gm, T2, T3, plane3, s);
+  }
+  {  // S4
+    const __nv_bfloat16* A[3] = {T3, T3 + plane3, T3 + 2 * plane3};
+    const __nv_bfloat16* B[3] = {Rp, Rp + rplane, Rp + 2 * rplane};
+    const long long tiles = (long long)cdiv(M4, 128) * cdiv(Dr, Dr <= 128 ? 128 : 256);
+    int splitk = (int)std::max<long long>(1, 2 * 152 / std::max<long long>(1, tiles));
+    splitk = std::min<int>(splitk, std::max<int>(1, (int)(K4 / (8 * 64))));
+    const double M = (double)M4, N = Dr, K = (double)K4;
+    ProfScope ps(PK_EMU_S4, s, 6.0 * 2.0 * M * N * K, 6.0 * (M * K + N * K) + 4.0 * M * N);
+    fill_zero(y, sizeof(float) * (size_t)M4 * Dr, s);
+    tc_gemm_bf16_pairs(A, ld3, B, ldr, (int)M4, Dr, (int)K4, 6, pa, pb, y, Dr,
+                       tc::OUT_F32_ATOMIC, splitk, s);
   }
 }
 

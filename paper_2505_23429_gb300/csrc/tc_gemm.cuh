@@ -18,6 +18,14 @@ void tc_gemm_bf16(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B,
                   int M, int N, int K, void* C, long long ldc, int out_kind, int splitk,
                   cudaStream_t s);
 
+// Same GEMM accumulating npairs operand pairs (A[pa[p]], B[pb[p]]) into one FP32 tile:
+// with A = A0 + A1 + A2 and B = B0 + B1 + B2 split into BF16 planes, the six pairs
+// (0,0) (0,1) (1,0) (0,2) (1,1) (2,0) reproduce the FP32 product to ~2^-24.
+void tc_gemm_bf16_pairs(const __nv_bfloat16* const* A, long long lda,
+                        const __nv_bfloat16* const* B, long long ldb, int M, int N, int K,
+                        int npairs, const int* pa, const int* pb, void* C, long long ldc,
+                        int out_kind, int splitk, cudaStream_t s);
+
 // y = H_eff x: BF16 environments Lb [(a w)][a'] (row stride ldl) and Rb [b][(w2 b')]
 // (row stride ldr), FP64 x in, FP32 y out; intermediates T1..T3 in BF16 with FP32
 // accumulation inside each stage.
@@ -25,6 +33,14 @@ void tc_heff_bf16(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int Dl
                   const __nv_bfloat16* Lb, long long ldl, const __nv_bfloat16* Rb, long long ldr,
                   const double* x, float* y, const SparseRows<float>& W1,
                   const SparseRows<float>& W2, DevBuf& t1, DevBuf& t2, DevBuf& xa);
+
+// y = H_eff x with FP32-accurate tensor-core products (three BF16 planes per operand,
+// six plane pairs per GEMM); L / R given as three BF16 planes each.
+void tc_heff_f32emu(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int Dl, int Dr,
+                    const __nv_bfloat16* Lp, long long ldl, long long lplane,
+                    const __nv_bfloat16* Rp, long long ldr, long long rplane, const double* x,
+                    float* y, const SparseRows<float>& W1, const SparseRows<float>& W2,
+                    DevBuf& t1, DevBuf& t2, DevBuf& xa);
 
 inline long long pad8(long long x) { return (x + 7) / 8 * 8; }
 
