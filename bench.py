@@ -41,7 +41,12 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--prec", default="bf16", choices=["bf16", "fp32", "fp64"])
+    p.add_argument("--prec", default="bf16", choices=["bf16", "f32emu", "fp32", "fp64"])
+    p.add_argument("--solver", default="lanczos", choices=["lanczos", "davidson"])
+    p.add_argument("--sequential", action="store_true",
+                   help="run the P groups one after another instead of concurrently")
+    p.add_argument("--coarse-eps", type=float, default=None,
+                   help="S_hat eigenvalue cut (default 1e-10 for fp64, 1e-5 otherwise)")
     p.add_argument("--config", default="chem_L16_D256")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -67,9 +72,14 @@ def workload(name):
     return cfg, mpo, raw
 
 
-def sweep_kwargs(cfg, prec):
+def sweep_kwargs(cfg, prec, solver="lanczos", coarse_eps=None):
+    if coarse_eps is None:
+        # the cut must sit above the relative accuracy of A_hat: FP64 entries for fp64,
+        # FP32-accurate environments otherwise
+        coarse_eps = 1e-10 if prec == "fp64" else 1e-5
     return dict(partition=cfg["partition"], D_max=cfg["D"], svd_tol=1e-6, eig_tol=1e-6,
-                coarse_eps=1e-10, max_krylov=40, max_restarts=50, prec=prec)
+                coarse_eps=coarse_eps, max_krylov=40, max_restarts=50, prec=prec,
+                solver=solver)
 
 
 def read_peaks():
@@ -226,7 +236,8 @@ def main():
     stream = torch.cuda.Stream()
     ctx = a2.Context(dev, stream.cuda_stream)
     mpo = a2.MPO(ctx, mpo_cores)
-    kw = sweep_kwargs(cfg, args.prec)
+    kw = sweep_kwargs(cfg, args.prec, args.solver, args.coarse_eps)
+    kw["sequential"] = args.sequential
     P = cfg["P"]
     t = a2.TT.from_cores(ctx, raw)
     t.left_orthogonalize()
@@ -250,6 +261,10 @@ def main():
         rep = a2.additive_sweep(ctx, t, mpo, P, **kw)
         reps.append(rep)
         history.append((rep["seconds"], rep["energy_in"]))
+        print(json.dumps(dict(iteration=len(history), seconds=rep["seconds"],
+                              energy_in=rep["energy_in"], lambda_coarse=rep["lambda_coarse"],
+                              coarse_rank=rep["coarse_rank"], krylov=rep["krylov"],
+                              max_discarded=rep["max_discarded"])), file=sys.stderr)
     ev1.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - w0
@@ -302,7 +317,10 @@ def main():
                 data="synthetic",
                 config=dict(workload=args.config, L=cfg["L"], n=cfg["n"], D=cfg["D"], P=P,
                             partition=cfg["partition"], eig_tol=1e-6, svd_tol=1e-6,
-                            precision=args.prec, parallelism="replicas" if world > 1 else "1gpu",
+                            coarse_eps=kw["coarse_eps"],
+                            precision=args.prec, solver=args.solver,
+                            groups="sequential" if args.sequential else "concurrent streams",
+                            parallelism="replicas" if world > 1 else "1gpu",
                             l2="working set >> 129 MB L2 (no flush)"),
                 energy_final=E_final, time_to_dE_1e6_s=t_conv,
                 iterations_run=len(history),

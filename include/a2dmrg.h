@@ -109,7 +109,12 @@ typedef struct {
   int max_krylov;              /* Krylov basis size before a restart (<= 64) */
   int max_restarts;            /* restart cycles per local solve */
   a2_precision prec;
-  int refine_f64;              /* mixed precision: refinement steps of each Ritz pair */
+  int refine_f64;              /* reserved (refinement is part of A2_BF16) */
+  int solver;                  /* local eigensolver: 0 = restarted Lanczos (as in the
+                                  paper's experiments), 1 = Davidson with the diagonal
+                                  preconditioner (same stopping rule, fewer matvecs) */
+  int group_streams;           /* 0 = the P groups run concurrently (one host thread and
+                                  CUDA stream each), 1 = one after another */
 } a2_sweep_opts;
 
 typedef struct {

@@ -29,7 +29,8 @@ class SweepOpts(ctypes.Structure):
                 ("D_max", ctypes.c_int), ("svd_tol", ctypes.c_double),
                 ("eig_tol", ctypes.c_double), ("coarse_eps", ctypes.c_double),
                 ("max_krylov", ctypes.c_int), ("max_restarts", ctypes.c_int),
-                ("prec", ctypes.c_int), ("refine_f64", ctypes.c_int)]
+                ("prec", ctypes.c_int), ("refine_f64", ctypes.c_int), ("solver", ctypes.c_int),
+                ("group_streams", ctypes.c_int)]
 
 
 class SweepReport(ctypes.Structure):
@@ -232,7 +233,7 @@ class MPO:
 
 
 def _opts(L, P, partition, D_max, svd_tol, eig_tol, coarse_eps, max_krylov, max_restarts, prec,
-          refine):
+          refine, solver="lanczos", sequential=False):
     o = SweepOpts()
     o.P = P
     part = None
@@ -243,14 +244,17 @@ def _opts(L, P, partition, D_max, svd_tol, eig_tol, coarse_eps, max_krylov, max_
     o.max_krylov, o.max_restarts = max_krylov, max_restarts
     o.prec = PRECISION[prec]
     o.refine_f64 = refine
+    o.solver = {"lanczos": 0, "davidson": 1}[solver]
+    o.group_streams = 1 if sequential else 0
     return o, part
 
 
 def _sweep(fn, ctx, tt, mpo, P, partition=None, D_max=64, svd_tol=1e-10, eig_tol=1e-10,
-           coarse_eps=1e-10, max_krylov=40, max_restarts=200, prec="fp64", refine=2):
+           coarse_eps=1e-10, max_krylov=40, max_restarts=200, prec="fp64", refine=2,
+           solver="lanczos", sequential=False):
     L = len(tt.phys)
     o, part = _opts(L, P, partition, D_max, svd_tol, eig_tol, coarse_eps, max_krylov,
-                    max_restarts, prec, refine)
+                    max_restarts, prec, refine, solver, sequential)
     m = P + 1
     bufs = dict(energy_local=np.zeros(P), coeffs=np.zeros(m), S_hat=np.zeros(m * m),
                 A_hat=np.zeros(m * m))

@@ -17,6 +17,7 @@
 #include <cstring>
 #include <memory>
 #include <mutex>
+#include <thread>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -38,6 +39,8 @@ struct a2_ctx {
   DevBuf scal, partial;         // device scalars, reduction partials
   double* h_scal = nullptr;     // pinned host mirror
   DevBuf t1, t2, t3, xa, ya, cb, ck, gram, wv, tmp1, tmp2;   // scratch
+  std::vector<a2_ctx*> lanes;   // per-group contexts (own stream, scratch, solver)
+  std::mutex lane_mu;
 };
 
 struct a2_tt {
@@ -142,6 +145,35 @@ void build_site(SiteOps& so, const double* W, int Rl, int n, int Rr, cudaStream_
 }
 
 double* scal(a2_ctx* c, int i) { return c->scal.as<double>() + i; }
+
+// Stream, scratch and solver of one concurrent group (created on first use, kept).
+a2_ctx* lane(a2_ctx* c, int i) {
+  std::lock_guard<std::mutex> g(c->lane_mu);
+  while ((int)c->lanes.size() <= i) {
+    auto* l = new a2_ctx();
+    l->device = c->device;
+    A2_CUDA(cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking));
+    l->own_stream = true;
+    l->solver.init(l->stream);
+    l->scal.ensure(sizeof(double) * 16384, l->stream);
+    l->partial.ensure(sizeof(double) * kReduceBlocks * 64, l->stream);
+    A2_CUDA(cudaMallocHost(&l->h_scal, sizeof(double) * 64));
+    A2_CUDA(cudaStreamSynchronize(l->stream));
+    c->lanes.push_back(l);
+  }
+  return c->lanes[i];
+}
+
+void destroy_ctx_resources(a2_ctx* c) {
+  cudaStreamSynchronize(c->stream);
+  c->solver.destroy();
+  for (DevBuf* b : {&c->scal, &c->partial, &c->t1, &c->t2, &c->t3, &c->xa, &c->ya, &c->cb, &c->ck,
+                    &c->gram, &c->wv, &c->tmp1, &c->tmp2})
+    b->release();
+  cudaStreamSynchronize(c->stream);
+  if (c->h_scal) cudaFreeHost(c->h_scal);
+  c->h_scal = nullptr;
+}
 
 // copy `count` doubles from the device scalar area to the pinned host mirror and wait
 void fetch_scalars(a2_ctx* c, int first, int count) {
@@ -502,11 +534,8 @@ LanczosResult lanczos(a2_ctx* c, MV&& mv, double* x, long long N, double tol, in
   normalize_into(tmp, scal(c, 0), V, N, s);
   LanczosResult res;
   std::vector<double> alpha, beta;
-  std::vector<double> T(64 * 64), evec(64 * 64), ev(64);
-  double* dT = scal(c, 128);
-  double* dev_ev = scal(c, 128 + 64 * 64);
-  double* dev_evec = dev_ev + 64;
-  int* dstat = reinterpret_cast<int*>(dev_evec + 64 * 64);
+  std::vector<double> ev(65);
+  double* dev_ev = scal(c, 128);
   for (int cyc = 1; cyc <= max_cycles; ++cyc) {
     res.cycles = cyc;
     alpha.clear();
@@ -536,20 +565,17 @@ LanczosResult lanczos(a2_ctx* c, MV&& mv, double* x, long long N, double tol, in
       check_finite(b2, "Lanczos beta");
       const double b = std::sqrt(std::max(b2, 0.0));
       alpha.push_back(a);
-      // lowest eigenpair of the tridiagonal T_j (device Jacobi)
+      // lowest eigenpair of the tridiagonal T_j (device bisection + inverse iteration)
       const int k = j + 1;
-      std::fill(T.begin(), T.begin() + k * k, 0.0);
-      for (int i = 0; i < k; ++i) {
-        T[i * k + i] = alpha[i];
-        if (i + 1 < k) T[i * k + i + 1] = T[(i + 1) * k + i] = beta[i];
-      }
-      A2_CUDA(cudaMemcpyAsync(dT, T.data(), sizeof(double) * k * k, cudaMemcpyHostToDevice, s));
-      jacobi_eig(dT, k, dev_ev, dev_evec, dstat, s);
-      A2_CUDA(cudaMemcpyAsync(ev.data(), dev_ev, sizeof(double), cudaMemcpyDeviceToHost, s));
-      A2_CUDA(cudaMemcpyAsync(evec.data(), dev_evec, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+      TridiagIn tin;
+      tin.k = k;
+      for (int i = 0; i < k; ++i) tin.a[i] = alpha[i];
+      for (int i = 0; i + 1 < k; ++i) tin.b[i] = beta[i];
+      tridiag_lowest(tin, dev_ev, s);
+      A2_CUDA(cudaMemcpyAsync(ev.data(), dev_ev, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, s));
       A2_CUDA(cudaStreamSynchronize(s));
       theta = ev[0];
-      svec.assign(evec.begin(), evec.begin() + k);
+      svec.assign(ev.begin() + 1, ev.begin() + 1 + k);
       const double resid = std::fabs(b * svec[k - 1]);
       const bool breakdown = b <= 1e-14 * std::max(1.0, std::fabs(theta));
       if (resid <= tol * std::max(1.0, std::fabs(theta)) || breakdown || k == N) {
@@ -582,6 +608,119 @@ LanczosResult lanczos(a2_ctx* c, MV&& mv, double* x, long long N, double tol, in
   return res;
 }
 
+// Diagonal of H_eff at bond k (FP64): diag[a,s1,s2,b] = sum_{w,w1,w2} L[a,w,a]
+// A_k[w,s1,s1,w1] A_k+1[w1,s2,s2,w2] R[b,w2,b] (preconditioner of the Davidson solver).
+template <typename T>
+void heff_diag(a2_ctx* c, const SiteOps& A1, const SiteOps& A2, const T* HL, const T* HR, int Dl,
+               int Dr, double* diag) {
+  cudaStream_t s = c->stream;
+  const int n1 = A1.n, n2 = A2.n, Rl = A1.Rl, R1 = A1.Rr, Rr = A2.Rr;
+  c->ck.ensure(sizeof(double) * ((size_t)Dl * Rl + (size_t)Dr * Rr + (size_t)Dl * n1 * R1 +
+                                 (size_t)Dr * n2 * R1), s);
+  double* Ld = c->ck.as<double>();
+  double* Rd = Ld + (size_t)Dl * Rl;
+  double* P1 = Rd + (size_t)Dr * Rr;
+  double* Q = P1 + (size_t)Dl * n1 * R1;
+  env_diag<T>(HL, Dl, Rl, Ld, s);
+  env_diag<T>(HR, Dr, Rr, Rd, s);
+  diag_action(A1.lr.rows<double>(), R1, n1, Ld, Rl, Dl, P1, s);   // P1[a][s1][w1]
+  diag_action(A2.rl.rows<double>(), R1, n2, Rd, Rr, Dr, Q, s);    // Q[b][s2][w1]
+  for (int s1 = 0; s1 < n1; ++s1)
+    for (int s2 = 0; s2 < n2; ++s2) {
+      SimtGemm<double, double> g;
+      g.M = Dl; g.N = Dr; g.K = R1;
+      g.A = P1 + (size_t)s1 * R1; g.sam = (long long)n1 * R1; g.sak = 1;
+      g.B = Q + (size_t)s2 * R1; g.sbn = (long long)n2 * R1; g.sbk = 1;
+      g.C = diag + (size_t)(s1 * n2 + s2) * Dr; g.scm = (long long)n1 * n2 * Dr; g.scn = 1;
+      simt_gemm(g, s);
+    }
+}
+
+// Davidson iteration with the diagonal preconditioner for the lowest eigenpair of `mv`
+// (same stopping rule and sign convention as `lanczos`); x: start in, unit Ritz vector out.
+template <typename MV>
+LanczosResult davidson(a2_ctx* c, MV&& mv, const double* diag, double* x, long long N, double tol,
+                       int max_sub, int max_iter) {
+  cudaStream_t s = c->stream;
+  const int m = (int)std::min<long long>(std::min(max_sub, 63), N);
+  c->wv.ensure(sizeof(double) * ((size_t)2 * m + 4) * N, s);
+  double* V = c->wv.as<double>();
+  double* AV = V + (size_t)m * N;
+  double* r = AV + (size_t)m * N;
+  double* t = r + N;
+  double* x0 = t + N;
+  double* ax = x0 + N;
+  A2_CUDA(cudaMemcpyAsync(x0, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  double nrm2 = dot_dev(c, x, x, N, 0);
+  check_finite(nrm2, "Davidson start vector");
+  if (!(nrm2 > 0.0)) {
+    std::vector<double> ones((size_t)N, 1.0);
+    A2_CUDA(cudaMemcpyAsync(x, ones.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
+    A2_CUDA(cudaMemcpyAsync(x0, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    nrm2 = dot_dev(c, x, x, N, 0);
+  }
+  normalize_into(x, scal(c, 0), V, N, s);
+  LanczosResult res;
+  mv(V, AV);
+  ++res.matvecs;
+  std::vector<double> G(64 * 64, 0.0), Gs(64 * 64), ev(64), evec(64 * 64), h(64);
+  G[0] = dot_dev(c, V, AV, N, 1);
+  int nv = 1;
+  double* dG = scal(c, 4300);
+  double* dev_ev = scal(c, 8500);
+  double* dev_evec = dev_ev + 64;
+  int* dstat = reinterpret_cast<int*>(dev_evec + 64 * 64);
+  double* dtheta = scal(c, 3);
+  for (int it = 0; it < max_iter; ++it) {
+    res.cycles = it + 1;
+    // Rayleigh-Ritz in span(V)
+    for (int i = 0; i < nv; ++i)
+      for (int j = 0; j < nv; ++j) Gs[i * nv + j] = G[i * 64 + j];
+    A2_CUDA(cudaMemcpyAsync(dG, Gs.data(), sizeof(double) * nv * nv, cudaMemcpyHostToDevice, s));
+    jacobi_eig(dG, nv, dev_ev, dev_evec, dstat, s);
+    A2_CUDA(cudaMemcpyAsync(ev.data(), dev_ev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    A2_CUDA(cudaMemcpyAsync(evec.data(), dev_evec, sizeof(double) * nv, cudaMemcpyDeviceToHost, s));
+    A2_CUDA(cudaStreamSynchronize(s));
+    const double theta = ev[0];
+    check_finite(theta, "Davidson Ritz value");
+    res.theta = theta;
+    A2_CUDA(cudaMemcpyAsync(scal(c, 8), evec.data(), sizeof(double) * nv, cudaMemcpyHostToDevice, s));
+    gemv_set(V, N, nv, scal(c, 8), x, N, s);
+    gemv_set(AV, N, nv, scal(c, 8), ax, N, s);
+    A2_CUDA(cudaMemcpyAsync(r, ax, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    axpby(-theta, x, 1.0, r, N, s);                          // r = A x - theta x
+    const double rn = std::sqrt(std::max(dot_dev(c, r, r, N, 2), 0.0));
+    check_finite(rn, "Davidson residual");
+    if (rn <= tol * std::max(1.0, std::fabs(theta))) { res.converged = true; break; }
+    if (nv == m) {                                           // restart from the Ritz pair
+      A2_CUDA(cudaMemcpyAsync(V, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+      A2_CUDA(cudaMemcpyAsync(AV, ax, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+      nv = 1;
+      G[0] = theta;
+    }
+    A2_CUDA(cudaMemcpyAsync(dtheta, &theta, sizeof(double), cudaMemcpyHostToDevice, s));
+    precondition(r, diag, dtheta, t, N, s);
+    A2_CUDA(cudaStreamSynchronize(s));                       // theta is a host stack value
+    for (int pass = 0; pass < 2; ++pass) {
+      dot_multi(V, N, nv, t, N, c->partial.as<double>(), scal(c, 8), s);
+      gemv_sub(V, N, nv, scal(c, 8), t, N, s);
+    }
+    const double tn2 = dot_dev(c, t, t, N, 4);
+    if (!(tn2 > 1e-28)) break;                               // no new direction
+    normalize_into(t, scal(c, 4), V + (size_t)nv * N, N, s);
+    mv(V + (size_t)nv * N, AV + (size_t)nv * N);
+    ++res.matvecs;
+    dot_multi(V, N, nv + 1, AV + (size_t)nv * N, N, c->partial.as<double>(), scal(c, 8), s);
+    A2_CUDA(cudaMemcpyAsync(h.data(), scal(c, 8), sizeof(double) * (nv + 1), cudaMemcpyDeviceToHost, s));
+    A2_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i <= nv; ++i) G[i * 64 + nv] = G[nv * 64 + i] = h[i];
+    ++nv;
+  }
+  const double sgn = dot_dev(c, x, x0, N, 5);
+  if (sgn < 0) axpby(0.0, x, -1.0, x, N, s);
+  return res;
+}
+
 // ============================================================================= SVD step
 // M (rows x cols, row-major) = P Sigma Q via the left Gram matrix M M^T (FP64):
 // P = leading eigenvectors (left-orthonormal), SQ = P^T M.  Returns rank r and
@@ -602,31 +741,43 @@ int svd_split_dev(a2_ctx* c, const double* M, int rows, int cols, int D_max, dou
     g.C = G; g.scm = rows; g.scn = 1;
     simt_gemm(g, s);
   }
-  c->solver.syevd(G, rows, w, s);
-  std::vector<double> lam(rows);
-  A2_CUDA(cudaMemcpyAsync(lam.data(), w, sizeof(double) * rows, cudaMemcpyDeviceToHost, s));
-  A2_CUDA(cudaStreamSynchronize(s));
-  // singular values descending
-  std::vector<double> sv(rows);
-  for (int i = 0; i < rows; ++i) sv[i] = std::sqrt(std::max(lam[rows - 1 - i], 0.0));
+  // Only the top min(D_max, rows) eigenpairs can be kept; the discarded weight of any
+  // rank is ||M||_F^2 minus the kept eigenvalues, so the rest need not be computed.
   const int kmax = std::min(rows, cols);
-  sv.resize(kmax);
-  double total = 0.0;
-  for (double x : sv) total += x * x;
-  std::vector<double> tail(kmax + 1, 0.0);
-  for (int i = kmax - 1; i >= 0; --i) tail[i] = tail[i + 1] + sv[i] * sv[i];
-  int r = kmax;
+  const int nev = std::min(kmax, D_max);
+  const double total = dot_dev(c, M, M, (long long)rows * cols, 7);
+  std::vector<double> sv(nev);           // singular values, descending
+  int col_of_first = rows - 1;           // column of the largest eigenvector in G
+  if (nev < rows && nev * 4 <= rows * 3) {
+    c->solver.syevd_top(G, rows, nev, w, s);
+    std::vector<double> lam(nev);
+    A2_CUDA(cudaMemcpyAsync(lam.data(), w, sizeof(double) * nev, cudaMemcpyDeviceToHost, s));
+    A2_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < nev; ++i) sv[i] = std::sqrt(std::max(lam[nev - 1 - i], 0.0));
+    col_of_first = nev - 1;
+  } else {
+    c->solver.syevd(G, rows, w, s);
+    std::vector<double> lam(rows);
+    A2_CUDA(cudaMemcpyAsync(lam.data(), w, sizeof(double) * rows, cudaMemcpyDeviceToHost, s));
+    A2_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < nev; ++i) sv[i] = std::sqrt(std::max(lam[rows - 1 - i], 0.0));
+  }
+  // tail[r] = sum_{k >= r} sigma_k^2 = total - sum_{k < r} sigma_k^2
+  std::vector<double> head(nev + 1, 0.0);
+  for (int i = 0; i < nev; ++i) head[i + 1] = head[i] + sv[i] * sv[i];
+  auto tail = [&](int r) { return std::max(total - head[r], 0.0); };
+  int r = nev;
   const double thr = tol * tol * total;
-  for (int cand = 1; cand <= kmax; ++cand)
-    if (tail[cand] <= thr) { r = cand; break; }
+  for (int cand = 1; cand <= nev; ++cand)
+    if (tail(cand) <= thr) { r = cand; break; }
   r = std::max(1, std::min(r, D_max));
-  if (discarded) *discarded = std::sqrt(std::max(tail[r], 0.0));
+  if (discarded) *discarded = std::sqrt(tail(r));
   if (sv_out) *sv_out = sv;
   // P[i][c] = evec column (rows-1-c): G column-major, column j at G + j*rows
   c->tmp1.ensure(sizeof(double) * (size_t)rows * r, s);
   double* Pcm = c->tmp1.as<double>();   // r columns, column-major (rows x r)
   for (int cc = 0; cc < r; ++cc)
-    A2_CUDA(cudaMemcpyAsync(Pcm + (size_t)cc * rows, G + (size_t)(rows - 1 - cc) * rows,
+    A2_CUDA(cudaMemcpyAsync(Pcm + (size_t)cc * rows, G + (size_t)(col_of_first - cc) * rows,
                             sizeof(double) * rows, cudaMemcpyDeviceToDevice, s));
   transpose2d<double, double>(Pcm, P, r, rows, s);      // -> row-major rows x r
   {  // SQ = P^T M : (r x cols)
@@ -771,10 +922,12 @@ struct Sweeper {
     std::vector<DevBuf> cores;   // new cores kg..mg+1 (mg - kg + 2 of them)
     std::vector<int> dl, dr;     // their bond dims
     double theta = 0.0;
+    double disc = 0.0;           // largest discarded weight of the group's SVD steps
   };
 
-  // Step 2 (second part): the group's left-to-right two-site micro-steps.
-  void solve_group(Group& G) {
+  // Step 2 (second part): the group's left-to-right two-site micro-steps, on the lane
+  // context `c` (own stream and scratch) with its own engine; environments are shared.
+  void solve_group(Group& G, a2_ctx* c, Engine<T>& eng) {
     cudaStream_t s = c->stream;
     DevBuf Hloc;
     int Dl = tt->dims[G.kg];
@@ -803,8 +956,27 @@ struct Sweeper {
       int nmv = 0;
       LanczosResult lr;
       bool done = false;
+      if (o.solver == 1) {
+        // Davidson with the diagonal preconditioner on the accurate operator
+        DevBuf dg;
+        dg.ensure(sizeof(double) * (size_t)N, c->stream);
+        heff_diag<T>(c, mpo->site[k], mpo->site[k + 1], HLcur, HRk, Dl, Dr, dg.as<double>());
+        if constexpr (sizeof(T) == 4) {
+          if (o.prec == A2_BF16 || o.prec == A2_F32EMU) {
+            eng.bfe.set(c, HLcur, Dl, mpo->R[k], HRk, Dr, mpo->R[k + 2], 3);
+            auto mve = [&](const double* in, double* out) { eng.matvec_emu(k, Dl, Dr, in, out); };
+            lr = davidson(c, mve, dg.as<double>(), x.as<double>(), N, o.eig_tol, o.max_krylov,
+                          o.max_krylov * o.max_restarts);
+            done = true;
+          }
+        }
+        if (!done)
+          lr = davidson(c, mv, dg.as<double>(), x.as<double>(), N, o.eig_tol, o.max_krylov,
+                        o.max_krylov * o.max_restarts);
+        done = true;
+      }
       if constexpr (sizeof(T) == 4) {
-        if (o.prec == A2_BF16 || o.prec == A2_F32EMU) {
+        if (!done && (o.prec == A2_BF16 || o.prec == A2_F32EMU)) {
           eng.bfe.set(c, HLcur, Dl, mpo->R[k], HRk, Dr, mpo->R[k + 2], 3);
           if (o.prec == A2_BF16) {
             // tensor-core Lanczos on the BF16 operator to a loose tolerance ...
@@ -832,7 +1004,7 @@ struct Sweeper {
       double disc = 0.0;
       const int r = svd_split_dev(c, x.as<double>(), rows, cols, o.D_max, o.svd_tol,
                                   P.as<double>(), SQ.as<double>(), &disc);
-      max_disc = std::max(max_disc, disc);
+      G.disc = std::max(G.disc, disc);
       // group-local left environment with the new left-orthogonal core
       DevBuf Hn;
       Hn.ensure(sizeof(T) * (size_t)r * mpo->R[k + 1] * r, s);
@@ -976,8 +1148,37 @@ struct Sweeper {
       groups[g].kg = k0;
       groups[g].mg = k0 + sizes[g] - 1;
       k0 += sizes[g];
-      solve_group(groups[g]);
     }
+    if (P > 1 && o.group_streams != 1) {
+      // the groups are independent (Alg. 2 step 2): one host thread and one stream each
+      A2_CUDA(cudaStreamSynchronize(s));                 // environments are ready
+      std::vector<std::unique_ptr<Engine<T>>> engs;
+      for (int g = 0; g < P; ++g) engs.emplace_back(new Engine<T>(lane(c, g), mpo, o.prec));
+      std::vector<std::exception_ptr> errs(P);
+      std::vector<std::thread> th;
+      for (int g = 0; g < P; ++g)
+        th.emplace_back([&, g] {
+          try {
+            A2_CUDA(cudaSetDevice(c->device));
+            a2_ctx* lc = lane(c, g);
+            solve_group(groups[g], lc, *engs[g]);
+            A2_CUDA(cudaStreamSynchronize(lc->stream));
+          } catch (...) {
+            errs[g] = std::current_exception();
+          }
+        });
+      for (auto& t : th) t.join();
+      for (auto& e : errs)
+        if (e) std::rethrow_exception(e);
+      for (auto& e : engs) {
+        eng.flops += e->flops;
+        eng.matvecs += e->matvecs;
+        eng.matvecs_bf16 += e->matvecs_bf16;
+      }
+    } else {
+      for (int g = 0; g < P; ++g) solve_group(groups[g], c, eng);
+    }
+    for (auto& G : groups) max_disc = std::max(max_disc, G.disc);
     const int m = P + 1;
     std::vector<double> S((size_t)m * m, 0.0), A((size_t)m * m, 0.0);
     // iterate: its (L-1)-orthogonal form is the stored left-orthogonal TT
@@ -1315,13 +1516,13 @@ a2_status a2_ctx_create(int device, void* cuda_stream, a2_ctx** out) {
 
 a2_status a2_ctx_destroy(a2_ctx* c) {
   if (!c) return A2_EINVAL;
-  cudaStreamSynchronize(c->stream);
-  c->solver.destroy();
-  for (DevBuf* b : {&c->scal, &c->partial, &c->t1, &c->t2, &c->t3, &c->xa, &c->ya, &c->cb, &c->ck,
-                    &c->gram, &c->wv, &c->tmp1, &c->tmp2})
-    b->release();
-  cudaStreamSynchronize(c->stream);
-  if (c->h_scal) cudaFreeHost(c->h_scal);
+  for (a2_ctx* l : c->lanes) {
+    destroy_ctx_resources(l);
+    cudaStreamDestroy(l->stream);
+    delete l;
+  }
+  c->lanes.clear();
+  destroy_ctx_resources(c);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return A2_OK;

@@ -884,12 +884,11 @@ __global__ void jacobi_kernel(double* A, int m, double* evals, double* evecs, in
 
 void jacobi_eig(double* A, int m, double* evals, double* evecs, int* status, cudaStream_t s) {
   A2_REQUIRE(m >= 1 && m <= 63, "jacobi_eig: 1 <= m <= 63");
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag once;
+  std::call_once(once, [] {
     A2_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(JacobiShared)));
-    attr = true;
-  }
+  });
   jacobi_kernel<<<1, 256, sizeof(JacobiShared), s>>>(A, m, evals, evecs, status);
   A2_CHECK_LAUNCH();
 }
@@ -977,13 +976,159 @@ __global__ void coarse_kernel(const double* A, const double* S, int m, double ep
 void coarse_solve_dev(const double* A, const double* S, int m, double eps, double* c,
                       double* lam, int* rank, int* status, cudaStream_t s) {
   A2_REQUIRE(m >= 1 && m <= 63, "coarse problem: 1 <= m <= 63");
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag once;
+  std::call_once(once, [] {
     A2_CUDA(cudaFuncSetAttribute(coarse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(CoarseShared)));
-    attr = true;
-  }
+  });
   coarse_kernel<<<1, 256, sizeof(CoarseShared), s>>>(A, S, m, eps, c, lam, rank, status);
+  A2_CHECK_LAUNCH();
+}
+
+// ----------------------------------------------------------------------------- tridiagonal
+// Lowest eigenpair of the symmetric tridiagonal T (diag a[0..k-1], off-diag b[0..k-2]):
+// bisection on the Sturm count of T - x I (Golub & Van Loan, Sec. 8.4), then inverse
+// iteration with a partially pivoted tridiagonal solve.  One thread; k <= 64.
+__device__ int sturm_below(const double* a, const double* b, int k, double x) {
+  int cnt = 0;
+  double d = a[0] - x;
+  if (d < 0) ++cnt;
+  for (int i = 1; i < k; ++i) {
+    const double dd = (d == 0.0) ? 1e-300 : d;
+    d = a[i] - x - b[i - 1] * b[i - 1] / dd;
+    if (d < 0) ++cnt;
+  }
+  return cnt;
+}
+
+__global__ void tridiag_lowest_kernel(TridiagIn in, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int k = in.k;
+  const double* a = in.a;
+  const double* b = in.b;
+  double lo = 1e300, hi = -1e300, scale = 0.0;
+  for (int i = 0; i < k; ++i) {
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < k ? fabs(b[i]) : 0.0);
+    lo = fmin(lo, a[i] - r);
+    hi = fmax(hi, a[i] + r);
+    scale = fmax(scale, fabs(a[i]) + r);
+  }
+  for (int it = 0; it < 200 && hi - lo > 4e-16 * fmax(scale, 1e-300); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_below(a, b, k, mid) >= 1) hi = mid; else lo = mid;
+  }
+  const double theta = 0.5 * (lo + hi);
+  // inverse iteration: (T - theta I) y = v
+  double y[64], v[64];
+  for (int i = 0; i < k; ++i) v[i] = 1.0 / sqrt((double)k) * (1.0 + 0.01 * i);
+  const double eps = 1e-14 * fmax(scale, 1e-300);
+  for (int rep = 0; rep < 3; ++rep) {
+    // Gaussian elimination with partial pivoting on the tridiagonal (dl, d, du, du2)
+    double dl[64], d[64], du[64], du2[64], rhs[64];
+    for (int i = 0; i < k; ++i) {
+      d[i] = a[i] - theta;
+      du[i] = (i + 1 < k) ? b[i] : 0.0;
+      dl[i] = (i + 1 < k) ? b[i] : 0.0;
+      du2[i] = 0.0;
+      rhs[i] = v[i];
+    }
+    for (int i = 0; i + 1 < k; ++i) {
+      if (fabs(d[i]) >= fabs(dl[i])) {
+        const double piv = (d[i] == 0.0) ? eps : d[i];
+        d[i] = piv;
+        const double f = dl[i] / piv;
+        d[i + 1] -= f * du[i];
+        rhs[i + 1] -= f * rhs[i];
+        dl[i] = 0.0;
+      } else {
+        const double f = d[i] / dl[i];
+        d[i] = dl[i];
+        double t = d[i + 1];
+        d[i + 1] = du[i] - f * t;
+        if (i + 2 < k) {
+          du2[i] = du[i + 1];
+          du[i + 1] = -f * du2[i];
+        }
+        du[i] = t;
+        t = rhs[i];
+        rhs[i] = rhs[i + 1];
+        rhs[i + 1] = t - f * rhs[i + 1];
+      }
+    }
+    if (d[k - 1] == 0.0) d[k - 1] = eps;
+    y[k - 1] = rhs[k - 1] / d[k - 1];
+    if (k > 1) y[k - 2] = (rhs[k - 2] - du[k - 2] * y[k - 1]) / d[k - 2];
+    for (int i = k - 3; i >= 0; --i) y[i] = (rhs[i] - du[i] * y[i + 1] - du2[i] * y[i + 2]) / d[i];
+    double nrm = 0.0;
+    for (int i = 0; i < k; ++i) nrm += y[i] * y[i];
+    nrm = sqrt(nrm);
+    for (int i = 0; i < k; ++i) v[i] = y[i] / nrm;
+  }
+  out[0] = theta;
+  for (int i = 0; i < k; ++i) out[1 + i] = v[i];
+}
+
+void tridiag_lowest(const TridiagIn& in, double* out, cudaStream_t s) {
+  A2_REQUIRE(in.k >= 1 && in.k <= 64, "tridiagonal size 1..64");
+  tridiag_lowest_kernel<<<1, 32, 0, s>>>(in, out);
+  A2_CHECK_LAUNCH();
+}
+
+// ----------------------------------------------------------------------------- H_eff diagonal
+// Ed[b][w] = E[b][w][b] for an environment E [D][R][D] (any float type) -> double
+template <typename T>
+__global__ void env_diag_kernel(const T* E, int D, int R, double* out) {
+  const long long n = (long long)D * R;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long b = e / R, w = e % R;
+    out[e] = (double)E[(b * R + w) * D + b];
+  }
+}
+template <typename T>
+void env_diag(const T* E, int D, int R, double* out, cudaStream_t s) {
+  env_diag_kernel<T><<<grid_for((long long)D * R), 256, 0, s>>>(E, D, R, out);
+  A2_CHECK_LAUNCH();
+}
+template void env_diag<double>(const double*, int, int, double*, cudaStream_t);
+template void env_diag<float>(const float*, int, int, double*, cudaStream_t);
+
+// out[b][rs][rw] = sum over entries (w, t) of row (rw, rs) with t == rs of val * Ed[b][w]
+// (the diagonal s = t part of one MPO core, acting on a diagonal environment)
+__global__ void diag_action_kernel(SparseRows<double> sp, int Rrow, int n, const double* Ed,
+                                   int Rin, int B, double* out) {
+  const int r = blockIdx.x;
+  const int rw = sp.row_w[r], rs = sp.row_s[r];
+  for (int b = threadIdx.x + blockIdx.y * blockDim.x; b < B; b += blockDim.x * gridDim.y) {
+    double acc = 0.0;
+    for (int e = sp.row_ptr[r]; e < sp.row_ptr[r + 1]; ++e)
+      if (sp.nz_t[e] == rs) acc += sp.nz_val[e] * Ed[(long long)b * Rin + sp.nz_w[e]];
+    out[((long long)b * n + rs) * Rrow + rw] = acc;
+  }
+}
+void diag_action(const SparseRows<double>& sp, int Rrow, int n, const double* Ed, int Rin, int B,
+                 double* out, cudaStream_t s) {
+  if (!sp.nrows || !B) return;
+  dim3 grid(sp.nrows, std::max(1, std::min(8, cdiv(B, 256))));
+  diag_action_kernel<<<grid, 256, 0, s>>>(sp, Rrow, n, Ed, Rin, B, out);
+  A2_CHECK_LAUNCH();
+}
+
+// Davidson correction t_i = r_i / (diag_i - theta), guarded away from zero
+__global__ void precond_kernel(const double* r, const double* diag, const double* theta,
+                               double* t, long long n) {
+  const double th = *theta;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double d = diag[i] - th;
+    if (fabs(d) < 1e-4) d = d < 0 ? -1e-4 : 1e-4;
+    t[i] = r[i] / d;
+  }
+}
+void precondition(const double* r, const double* diag, const double* theta, double* t,
+                  long long n, cudaStream_t s) {
+  precond_kernel<<<grid_for(n), 256, 0, s>>>(r, diag, theta, t, n);
   A2_CHECK_LAUNCH();
 }
 

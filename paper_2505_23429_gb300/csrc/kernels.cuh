@@ -103,9 +103,26 @@ void normalize_into(const double* w, const double* nrm2, double* out, long long 
 // (evecs[j*m + i] = component i of eigenvector j).  status[0] = sweeps used (or -1).
 void jacobi_eig(double* A, int m, double* evals, double* evecs, int* status, cudaStream_t s);
 
+// Lowest eigenpair of a symmetric tridiagonal matrix passed by value (k <= 64):
+// out[0] = eigenvalue, out[1..k] = unit eigenvector (sign arbitrary).
+struct TridiagIn {
+  int k;
+  double a[64];
+  double b[64];
+};
+void tridiag_lowest(const TridiagIn& in, double* out, cudaStream_t s);
+
 // Coarse problem of Sec. 3.1 (m <= 63) in one CTA; outputs on the device.
 void coarse_solve_dev(const double* A, const double* S, int m, double eps, double* c,
                       double* lam, int* rank, int* status, cudaStream_t s);
+
+// ---- diagonal of H_eff (Davidson preconditioner)
+template <typename T>
+void env_diag(const T* E, int D, int R, double* out, cudaStream_t s);     // out[b][w] = E[b][w][b]
+void diag_action(const SparseRows<double>& sp, int Rrow, int n, const double* Ed, int Rin, int B,
+                 double* out, cudaStream_t s);
+void precondition(const double* r, const double* diag, const double* theta, double* t,
+                  long long n, cudaStream_t s);
 
 // ---- assorted
 void fill_zero(void* p, size_t bytes, cudaStream_t s);

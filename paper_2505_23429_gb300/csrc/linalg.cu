@@ -81,3 +81,19 @@ void Solver::syevd(double* A, int m, double* w, cudaStream_t s) {
 }
 
 }  // namespace a2
+
+namespace a2 {
+void Solver::syevd_top(double* A, int m, int nev, double* w, cudaStream_t s) {
+  int lw = 0, meig = 0;
+  const int il = m - nev + 1, iu = m;
+  A2_SOLVER(cusolverDnDsyevdx_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
+                                         CUBLAS_FILL_MODE_LOWER, m, A, m, 0.0, 0.0, il, iu,
+                                         &meig, w, &lw));
+  work.ensure(sizeof(double) * (size_t)(lw > 0 ? lw : 1), s);
+  A2_SOLVER(cusolverDnDsyevdx(h, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
+                              CUBLAS_FILL_MODE_LOWER, m, A, m, 0.0, 0.0, il, iu, &meig, w,
+                              work.as<double>(), lw, info.as<int>()));
+  if (meig != nev) throw CudaError("syevdx returned " + std::to_string(meig) + " of " +
+                                   std::to_string(nev) + " eigenpairs");
+}
+}  // namespace a2

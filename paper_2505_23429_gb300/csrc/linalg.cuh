@@ -18,6 +18,9 @@ struct Solver {
   // Symmetric eigendecomposition of a (m x m) matrix in place: on exit A holds the
   // eigenvectors column-major (column j <-> eigenvalue w[j], ascending).
   void syevd(double* A, int m, double* w, cudaStream_t s);
+  // The `nev` largest eigenpairs only (ascending order in w[0..nev-1], eigenvectors in
+  // the first nev columns of A, column-major).
+  void syevd_top(double* A, int m, int nev, double* w, cudaStream_t s);
 };
 
 }  // namespace a2

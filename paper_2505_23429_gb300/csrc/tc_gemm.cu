@@ -252,39 +252,37 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
     if (!*(volatile int*)&S.abort_flag) {
-      const int row = m0 + warp * 32 + lane;
+      // The operand ring is idle once `done` has fired: each warp stages its 32 x 32
+      // accumulator chunk there (row = lane), then writes whole row segments so that
+      // consecutive lanes store consecutive columns.
+      float* stage = reinterpret_cast<float*>(&S.a[0][0]) + warp * (32 * 33);
       const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+      const int row0 = m0 + warp * 32;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         if (n0 + c0 >= args.N) break;
         float v[32];
         tmem_ld32(tl + (uint32_t)c0, v);
-        if (row < args.M) {
-          const int ncol = min(32, args.N - (n0 + c0));
-          if (args.out_kind == OUT_BF16) {
-            __nv_bfloat16* C = reinterpret_cast<__nv_bfloat16*>(args.C) +
-                               (long long)row * args.ldc + n0 + c0;
-            if (ncol == 32 && ((reinterpret_cast<uintptr_t>(C) & 15) == 0)) {
 #pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                __align__(16) __nv_bfloat162 h[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                  h[e] = __floats2bfloat162_rn(v[q * 8 + 2 * e], v[q * 8 + 2 * e + 1]);
-                *reinterpret_cast<uint4*>(C + q * 8) = *reinterpret_cast<uint4*>(h);
-              }
-            } else {
-              for (int e = 0; e < ncol; ++e) C[e] = __float2bfloat16_rn(v[e]);
-            }
-          } else {
-            float* C = reinterpret_cast<float*>(args.C) + (long long)row * args.ldc + n0 + c0;
-            if (args.out_kind == OUT_F32_ATOMIC) {
-              for (int e = 0; e < ncol; ++e) atomicAdd(C + e, v[e]);
-            } else {
-              for (int e = 0; e < ncol; ++e) C[e] = v[e];
-            }
+        for (int i = 0; i < 32; ++i) stage[lane * 33 + i] = v[i];
+        __syncwarp();
+        const int col = n0 + c0 + lane;
+        if (col < args.N) {
+#pragma unroll 4
+          for (int r = 0; r < 32; ++r) {
+            const int row = row0 + r;
+            if (row >= args.M) break;
+            const float x = stage[r * 33 + lane];
+            const long long off = (long long)row * args.ldc + col;
+            if (args.out_kind == OUT_BF16)
+              reinterpret_cast<__nv_bfloat16*>(args.C)[off] = __float2bfloat16_rn(x);
+            else if (args.out_kind == OUT_F32_ATOMIC)
+              atomicAdd(reinterpret_cast<float*>(args.C) + off, x);
+            else
+              reinterpret_cast<float*>(args.C)[off] = x;
           }
         }
+        __syncwarp();
       }
     }
   }
@@ -344,12 +342,11 @@ void launch(const __nv_bfloat16* const* A, long long lda, const __nv_bfloat16* c
     maps.b[i] = make_map(B[i < nb ? i : 0], N, K, ldb, BN);
   }
   const size_t smem = sizeof(TcSmem<BN, STAGES>) + 1024;
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag once;
+  std::call_once(once, [smem] {
     A2_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  });
   const int nk_total = (K + BK - 1) / BK;
   splitk = std::max(1, std::min(splitk, nk_total));
   TcArgs args;

@@ -153,3 +153,44 @@ def test_error_leaves_tt_unchanged(ctx):
     with pytest.raises(a2.A2Error):
         a2.additive_sweep(ctx, t, mpo, 2, partition=[2, 2], D_max=8)   # sums to 4 != L-1
     assert np.array_equal(tt_full(t.cores()), before)
+
+
+@pytest.mark.parametrize("prec", ["fp64"])
+def test_davidson_solver_matches_oracle(ctx, prec):
+    """The Davidson local solver reaches the same eigenpairs as the oracle's Lanczos."""
+    h, eri = chemistry_integrals(6, 2505)
+    m = chemistry_mpo(h, eri)
+    raw, U = _start([4] * 6, 4, 23429)
+    U1, rep0 = oa2.global_iteration(U, m, [2, 2, 1], 64, **KW)
+    mpo = a2.MPO(ctx, m)
+    t = _gpu_tt(ctx, raw)
+    tol = 1e-10 if prec == "fp64" else 1e-6
+    rep = a2.additive_sweep(ctx, t, mpo, 3, partition=[2, 2, 1], D_max=64, prec=prec,
+                            solver="davidson", svd_tol=1e-10,
+                            eig_tol=1e-10 if prec == "fp64" else 1e-8, coarse_eps=1e-10)
+    assert abs(rep["lambda_coarse"] - rep0["lambda_coarse"]) < tol * abs(rep0["lambda_coarse"])
+    for _ in range(3):
+        a2.additive_sweep(ctx, t, mpo, 3, partition=[2, 2, 1], D_max=64, prec=prec,
+                          solver="davidson", svd_tol=1e-10,
+                          eig_tol=1e-10 if prec == "fp64" else 1e-8, coarse_eps=1e-10)
+    E, _ = a2.energy(ctx, t, mpo)
+    E_ed = GOLD["chemistry_L6_seed2505_ed"]["value"]
+    assert abs(E - E_ed) < (1e-10 * abs(E_ed) if prec == "fp64" else 1e-6)
+
+
+def test_concurrent_groups_match_sequential(ctx):
+    """Groups on separate streams/threads give the same iteration as one after another."""
+    h, eri = chemistry_integrals(6, 2505)
+    m = chemistry_mpo(h, eri)
+    raw, _ = _start([4] * 6, 4, 23429)
+    mpo = a2.MPO(ctx, m)
+    out = {}
+    for seq in (True, False):
+        t = _gpu_tt(ctx, raw)
+        for _ in range(2):
+            rep = a2.additive_sweep(ctx, t, mpo, 3, partition=[2, 2, 1], D_max=64, prec="fp64",
+                                    sequential=seq, **KW)
+        out[seq] = (rep, tt_full(t.cores()))
+    assert abs(out[True][0]["lambda_coarse"] - out[False][0]["lambda_coarse"]) < 1e-12 * 10
+    x, y = out[True][1], out[False][1]
+    assert abs(abs(x @ y) - 1.0) < 1e-10

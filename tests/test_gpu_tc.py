@@ -64,6 +64,38 @@ def test_heff_bf16_chemistry(ctx, k, Dl, Dr):
     assert rel(host(y, ctx), ref) < 2e-2
 
 
+@pytest.mark.parametrize("k,Dl,Dr", [(0, 1, 16), (2, 16, 64), (3, 64, 16), (1, 4, 64), (2, 33, 9)])
+def test_heff_f32emu_chemistry(ctx, k, Dl, Dr):
+    """Three-slice BF16 products (six pairs) reach FP32 accuracy on tcgen05."""
+    h, eri = chemistry_integrals(6, 2505)
+    m = chemistry_mpo(h, eri)
+    mpo = a2.MPO(ctx, m)
+    rng = np.random.default_rng(10 + k)
+    Lh = rng.standard_normal((Dl, m[k].shape[0], Dl))
+    Rh = rng.standard_normal((Dr, m[k + 1].shape[3], Dr))
+    x = rng.standard_normal((Dl, 4, 4, Dr))
+    ref = oracle_heff(Lh, m[k], m[k + 1], Rh, x)
+    y = torch.zeros(x.shape, dtype=torch.float64, device="cuda")
+    a2.heff_apply(ctx, mpo, k, dev(Lh), dev(Rh), dev(x), y, prec="f32emu")
+    assert rel(host(y, ctx), ref) < 5e-6
+
+
+def test_f32emu_sweep_energy_within_1e6_of_fp64(ctx):
+    h, eri = chemistry_integrals(6, 2505)
+    m = chemistry_mpo(h, eri)
+    mpo = a2.MPO(ctx, m)
+    raw = random_tt_cores([4] * 6, 4, 23429)
+    res = {}
+    for prec in ("fp64", "f32emu"):
+        t = a2.TT.from_cores(ctx, raw)
+        t.left_orthogonalize()
+        for _ in range(4):
+            a2.additive_sweep(ctx, t, mpo, 3, partition=[2, 2, 1], D_max=64, prec=prec,
+                              svd_tol=1e-10, eig_tol=1e-8, coarse_eps=1e-10)
+        res[prec] = a2.energy(ctx, t, mpo, "fp64")[0]
+    assert abs(res["f32emu"] - res["fp64"]) < 1e-6
+
+
 def test_bf16_sweep_energy_within_1e6_of_fp64(ctx):
     h, eri = chemistry_integrals(6, 2505)
     m = chemistry_mpo(h, eri)
