@@ -43,6 +43,9 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--prec", default="bf16", choices=["bf16", "f32emu", "fp32", "fp64"])
     p.add_argument("--solver", default="lanczos", choices=["lanczos", "davidson"])
+    p.add_argument("--converge", type=int, default=0,
+                   help="after the timed steps, keep iterating (up to this many iterations in "
+                        "total) until |dE|/|E| < 1e-6, to report the time from the seeded TT")
     p.add_argument("--sequential", action="store_true",
                    help="run the P groups one after another instead of concurrently")
     p.add_argument("--coarse-eps", type=float, default=None,
@@ -214,6 +217,23 @@ def profile_matvec(args):
     print(json.dumps(dict(profile_matvec=True, D=D, bond=k, error_flag=a2.device_error(ctx))))
 
 
+def max_over_ranks(ms, world, device):
+    """Slowest rank's timed-region length (the job ends when the last replica ends)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(steps, ms, world):
+    """Whole-job global iterations per second: every rank runs `steps` independent
+    replica iterations in `ms` (max over ranks)."""
+    return steps * world / (ms * 1e-3)
+
+
 def main():
     args = parse()
     if args.profile_matvec:
@@ -252,6 +272,7 @@ def main():
     torch.cuda.synchronize()
     a2.profile(ctx, "reset")
     a2.profile(ctx, "on")
+    launches0 = a2.profile(ctx, "launches")
     clocks = Clocks()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -270,22 +291,30 @@ def main():
     wall = time.perf_counter() - w0
     clk = clocks.stop()
     a2.profile(ctx, "off")
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        tt_ = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt_, op=dist.ReduceOp.MAX)
-        ms = float(tt_.item())
+    launches = a2.profile(ctx, "launches") - launches0
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, "cuda")
     prof = {k: a2.profile(ctx, "read", i) for i, k in enumerate(a2.a2dmrg.PROFILE_KINDS)}
+
+    def converged(hist):
+        e = [x[1] for x in hist]
+        return any(abs(e[i] - e[i - 1]) < 1e-6 * abs(e[i]) for i in range(2, len(e)))
+    while args.converge and len(history) < args.converge and not converged(history):
+        rep = a2.additive_sweep(ctx, t, mpo, P, **kw)
+        history.append((rep["seconds"], rep["energy_in"]))
+        print(json.dumps(dict(iteration=len(history), seconds=rep["seconds"],
+                              energy_in=rep["energy_in"], lambda_coarse=rep["lambda_coarse"],
+                              krylov=sum(rep["krylov"]))), file=sys.stderr)
     E_final, _ = a2.energy(ctx, t, mpo, "fp64")
 
     # time to |dE| < 1e-6 (relative, between successive global iterations, as in the
     # stopping rule of the experiments), from the seeded TT, if reached in W+K iterations
+    # energies[i] = energy after i+1 iterations; the stopping rule compares successive ones
     energies = [e for _, e in history[1:]] + [E_final]
-    t_conv, cum = None, 0.0
+    t_conv, it_conv, cum = None, None, history[0][0]
     for i in range(1, len(energies)):
         cum += history[i][0]
         if abs(energies[i] - energies[i - 1]) < 1e-6 * abs(energies[i]):
-            t_conv = cum
+            t_conv, it_conv = cum, i + 1
             break
 
     # dominant kernel class and its roofline
@@ -309,7 +338,7 @@ def main():
     # H_eff matvec TFLOP/s: tensor-core chain vs a plain torch.einsum chain (dense MPO, BF16)
     mv = matvec_compare(a2, ctx, mpo, mpo_cores, cfg, torch, stream)
 
-    value = args.steps / (ms * 1e-3) * world
+    value = job_throughput(args.steps, ms, world)
     line = dict(metric=METRIC, value=value, unit="additive sweeps/s", n_gpus=world,
                 steps=args.steps, warmup=args.warmup, ms_per_step=ms / args.steps,
                 higher_is_better=True, scaling="weak", vs_baseline=None,
@@ -322,7 +351,7 @@ def main():
                             groups="sequential" if args.sequential else "concurrent streams",
                             parallelism="replicas" if world > 1 else "1gpu",
                             l2="working set >> 129 MB L2 (no flush)"),
-                energy_final=E_final, time_to_dE_1e6_s=t_conv,
+                energy_final=E_final, time_to_dE_1e6_s=t_conv, iterations_to_dE_1e6=it_conv,
                 iterations_run=len(history),
                 roofline=dict(kernel=dom, bound=bound, achieved=achieved, peak=peak, unit=unit,
                               frac=achieved / peak, traffic=None,
@@ -331,7 +360,7 @@ def main():
                 kernel_classes={k: dict(ms=round(v["ms"], 3), launches=v["launches"])
                                 for k, v in prof.items()},
                 heff_matvec=mv, clocks=clk, wall_s=wall,
-                gpu_launches=int(sum(v["launches"] for v in prof.values())))
+                gpu_launches=int(launches))
     if not args.no_e2e:
         line["e2e"] = e2e_run(a2, ctx, mpo, cfg, kw, t, args.steps, torch, stream, world)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -351,48 +380,61 @@ def main():
 
 
 def matvec_compare(a2, ctx, mpo, cores, cfg, torch, stream):
-    """Tensor-core H_eff vs a plain torch.einsum/cuBLAS chain of the same contraction."""
+    """H_eff applications at full bond dimension: the tensor-core chains (BF16 and
+    FP32-accurate split products), the FP64 SIMT chain, and a plain torch.tensordot
+    chain of the same contraction in BF16 with the dense MPO cores (cuBLAS), at the
+    hand-over bond of the operator automaton and at a typical middle bond."""
     L, D, n = cfg["L"], cfg["D"], cfg["n"]
-    k = L // 2 - 1
-    W1, W2 = cores[k], cores[k + 1]
-    g = torch.Generator(device="cuda").manual_seed(0)
-    with torch.cuda.stream(stream):
-        HL = torch.randn(D, W1.shape[0], D, device="cuda", dtype=torch.float64, generator=g)
-        HR = torch.randn(D, W2.shape[3], D, device="cuda", dtype=torch.float64, generator=g)
-        x = torch.randn(D, n, n, D, device="cuda", dtype=torch.float64, generator=g)
-        y = torch.empty_like(x)
-    torch.cuda.synchronize()
-    nnz = np.count_nonzero(W1) + np.count_nonzero(W2)
-    flops = 2.0 * n * n * D * D * (W1.shape[0] * D + W2.shape[3] * D) + 2.0 * n * D * D * nnz
-
-    def timeit(fn, reps=10):
-        fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
-
-    ours = timeit(lambda: a2.heff_apply(ctx, mpo, k, HL, HR, x, y, prec="bf16"))
-    with torch.cuda.stream(stream):
-        Lb, Rb, xb = HL.bfloat16(), HR.bfloat16(), x.bfloat16()
-        W1b = torch.from_numpy(W1).cuda().bfloat16()
-        W2b = torch.from_numpy(W2).cuda().bfloat16()
-
-    def plain():
+    out = []
+    for k in (L // 2 - 1, L // 2 - 3):
+        W1, W2 = cores[k], cores[k + 1]
+        g = torch.Generator(device="cuda").manual_seed(0)
         with torch.cuda.stream(stream):
-            T = torch.tensordot(Lb, xb, dims=([2], [0]))                  # a w t1 t2 b'
-            T = torch.tensordot(T, W1b, dims=([1, 2], [0, 2]))            # a t2 b' s1 w1
-            T = torch.tensordot(T, W2b, dims=([1, 4], [2, 0]))            # a b' s1 s2 w2
-            return torch.tensordot(T, Rb, dims=([1, 4], [2, 1]))          # a s1 s2 b
-    pl = timeit(plain)
-    return dict(bond=k, D=D, R=[int(W1.shape[0]), int(W1.shape[3]), int(W2.shape[3])],
-                alg_flops=flops, ours_ms=ours, ours_tflops=flops / (ours * 1e-3) / 1e12,
-                plain_ms=pl, plain_tflops=flops / (pl * 1e-3) / 1e12,
-                plain="torch.tensordot chain in BF16 with the dense MPO cores (cuBLAS)")
+            HL = torch.randn(D, W1.shape[0], D, device="cuda", dtype=torch.float64, generator=g)
+            HR = torch.randn(D, W2.shape[3], D, device="cuda", dtype=torch.float64, generator=g)
+            x = torch.randn(D, n, n, D, device="cuda", dtype=torch.float64, generator=g)
+            y = torch.empty_like(x)
+        torch.cuda.synchronize()
+        nnz = np.count_nonzero(W1) + np.count_nonzero(W2)
+        flops = (2.0 * n * n * D * D * (W1.shape[0] * D + W2.shape[3] * D)
+                 + 2.0 * n * D * D * nnz)
+
+        def timeit(fn, reps=10):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        res = dict(bond=k, D=D, R=[int(W1.shape[0]), int(W1.shape[3]), int(W2.shape[3])],
+                   nnz=[int(np.count_nonzero(W1)), int(np.count_nonzero(W2))], alg_flops=flops)
+        for prec, reps in (("bf16", 10), ("f32emu", 10), ("fp64", 1)):
+            ms = timeit(lambda: a2.heff_apply(ctx, mpo, k, HL, HR, x, y, prec=prec), reps)
+            res[f"{prec}_ms"] = ms
+            res[f"{prec}_tflops"] = flops / (ms * 1e-3) / 1e12
+        with torch.cuda.stream(stream):
+            Lb, Rb, xb = HL.bfloat16(), HR.bfloat16(), x.bfloat16()
+            W1b = torch.from_numpy(W1).cuda().bfloat16()
+            W2b = torch.from_numpy(W2).cuda().bfloat16()
+
+        def plain():
+            with torch.cuda.stream(stream):
+                T = torch.tensordot(Lb, xb, dims=([2], [0]))                  # a w t1 t2 b'
+                T = torch.tensordot(T, W1b, dims=([1, 2], [0, 2]))            # a t2 b' s1 w1
+                T = torch.tensordot(T, W2b, dims=([1, 4], [2, 0]))            # a b' s1 s2 w2
+                return torch.tensordot(T, Rb, dims=([1, 4], [2, 1]))          # a s1 s2 b
+        pl = timeit(plain)
+        res["plain_bf16_ms"] = pl
+        res["plain_bf16_tflops"] = flops / (pl * 1e-3) / 1e12
+        out.append(res)
+    return dict(bonds=out, note="timed through a2_heff_apply (includes the per-call conversion "
+                "of FP64 environments to BF16 slices); plain = torch.tensordot chain in BF16 "
+                "with the dense MPO cores (cuBLAS); TFLOP/s use the algorithmic count with MPO "
+                "nonzeros")
 
 
 def e2e_run(a2, ctx, mpo, cfg, kw, t, steps, torch, stream, world):

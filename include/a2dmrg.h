@@ -202,7 +202,9 @@ a2_status a2_device_error(a2_ctx* ctx, int reset, int* code_out);
  * 1 sparse S2, 2 sparse S3, 3 tcgen05 S4, 4 SIMT H_eff, 5 environment update,
  * 6 Lanczos vector work, 7 truncated SVD, 8 LQ/QR, 9-12 the four stages of the
  * FP32-accurate split-product H_eff) into the host outputs
- * (launches, milliseconds, algorithmic flops, algorithmic bytes; any may be NULL). */
+ * (launches, milliseconds, algorithmic flops, algorithmic bytes; any may be NULL).
+ * op 4 returns in *launches the number of kernel launches this library has made
+ * since the process started (all of its own kernels, library calls excluded). */
 a2_status a2_profile(a2_ctx* ctx, int op, int kind, long long* launches, double* ms,
                      double* flops, double* bytes);
 

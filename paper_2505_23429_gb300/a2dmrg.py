@@ -345,12 +345,14 @@ PROFILE_KINDS = ["tc_s1", "sparse_s2", "sparse_s3", "tc_s4", "heff_simt", "env",
 
 def profile(ctx, op, kind=0):
     """op: 'off', 'on', 'reset' or 'read' (returns dict for `kind`)."""
-    code = {"off": 0, "on": 1, "reset": 2, "read": 3}[op]
+    code = {"off": 0, "on": 1, "reset": 2, "read": 3, "launches": 4}[op]
     n, ms, fl, by = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     ctx.check(lib().a2_profile(ctx._h, code, kind, ctypes.byref(n), ctypes.byref(ms),
                                ctypes.byref(fl), ctypes.byref(by)))
     if code == 3:
         return dict(launches=n.value, ms=ms.value, flops=fl.value, bytes=by.value)
+    if code == 4:
+        return n.value
     return None
 
 

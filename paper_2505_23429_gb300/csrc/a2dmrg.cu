@@ -288,6 +288,112 @@ void env_right(a2_ctx* c, const SiteOps& so, const T* Hin, const T* bra, int Dlb
   }
 }
 
+// ---- environment updates with FP32-accurate split products on tcgen05 (FP32 envs)
+inline long long round64(long long x) { return (x + 63) / 64 * 64; }
+static const int kPairA[6] = {0, 0, 1, 0, 1, 2};
+static const int kPairB[6] = {0, 1, 0, 2, 1, 0};
+
+struct Planes {   // three BF16 slices of a (rows x K) operand, row stride ld
+  const __nv_bfloat16* p[3];
+  long long ld;
+};
+Planes planes_at(__nv_bfloat16* base, long long ld, long long plane) {
+  return Planes{{base, base + plane, base + 2 * plane}, ld};
+}
+
+void env_left_emu(a2_ctx* c, const SiteOps& so, const float* Hin, const double* bra, int Dlb,
+                  int Drb, const double* ket, int Dlk, int Drk, float* Hout) {
+  const int n = so.n, Rl = so.Rl, Rr = so.Rr;
+  cudaStream_t s = c->stream;
+  ProfScope ps(PK_ENV, s, env_flops(so, std::max(Dlb, Dlk), std::max(Drb, Drk)),
+               4.0 * ((double)Dlb * Rl * Dlk + (double)Drb * Rr * Drk +
+                      2.0 * Dlb * Rl * n * Drk + 2.0 * Dlb * n * Rr * Drk));
+  const long long ldH = pad8(Dlk), pH = round64((long long)Dlb * Rl * ldH);
+  const long long ldK = pad8(Dlk), pK = round64((long long)n * Drk * ldK);
+  const long long ldB = pad8((long long)Dlb * n), pB = round64((long long)Drb * ldB);
+  const long long pT = round64((long long)Rr * Drk * ldB);
+  c->cb.ensure(sizeof(__nv_bfloat16) * (size_t)(3 * (pH + pK + pB)), s);
+  __nv_bfloat16* Hp = c->cb.as<__nv_bfloat16>();
+  __nv_bfloat16* Kp = Hp + 3 * pH;
+  __nv_bfloat16* Bp = Kp + 3 * pK;
+  c->tmp1.ensure(sizeof(float) * (size_t)Dlb * Rl * n * Drk, s);
+  c->tmp2.ensure(sizeof(float) * (size_t)Dlb * n * Rr * Drk, s);
+  c->t3.ensure(sizeof(__nv_bfloat16) * (size_t)(3 * pT), s);
+  float* T1 = c->tmp1.as<float>();
+  float* T2 = c->tmp2.as<float>();
+  __nv_bfloat16* T2p = c->t3.as<__nv_bfloat16>();
+  split3_ld<float>(Hin, (long long)Dlb * Rl, Dlk, Hp, ldH, pH, s);
+  transpose_split3<double>(ket, Dlk, n * Drk, Kp, ldK, pK, s);
+  {  // E1: T1[(a w)][(t b')] = sum_a' Hin[(a w)][a'] ket[a'][(t b')]
+    Planes A = planes_at(Hp, ldH, pH), B = planes_at(Kp, ldK, pK);
+    tc_gemm_bf16_pairs(A.p, A.ld, B.p, B.ld, Dlb * Rl, n * Drk, Dlk, 6, kPairA, kPairB, T1,
+                       (long long)n * Drk, 1, 1, s);
+  }
+  {  // E2 (FP32)
+    SparseGeom gm;
+    gm.veclen = Drk;
+    gm.in_sw = (long long)n * Drk; gm.in_st = Drk;
+    gm.out_sw = Drk; gm.out_ss = (long long)Rr * Drk;
+    gm.B1 = Dlb; gm.in_b1 = (long long)Rl * n * Drk; gm.out_b1 = (long long)n * Rr * Drk;
+    sparse_rows_apply<float, float, float>(so.lr.rows<float>(), gm, T1, T2, s);
+  }
+  transpose_split3<double>(bra, Dlb * n, Drb, Bp, ldB, pB, s);
+  transpose_split3<float>(T2, Dlb * n, Rr * Drk, T2p, ldB, pT, s);
+  {  // E3: Hout[b][(w' b')] = sum_{(a s)} bra[(a s)][b] T2[(a s)][(w' b')]
+    Planes A = planes_at(Bp, ldB, pB), B = planes_at(T2p, ldB, pT);
+    tc_gemm_bf16_pairs(A.p, A.ld, B.p, B.ld, Drb, Rr * Drk, Dlb * n, 6, kPairA, kPairB, Hout,
+                       (long long)Rr * Drk, 1, 1, s);
+  }
+}
+
+void env_right_emu(a2_ctx* c, const SiteOps& so, const float* Hin, const double* bra, int Dlb,
+                   int Drb, const double* ket, int Dlk, int Drk, float* Hout) {
+  const int n = so.n, Rl = so.Rl, Rr = so.Rr;
+  cudaStream_t s = c->stream;
+  ProfScope ps(PK_ENV, s, env_flops(so, std::max(Dlb, Dlk), std::max(Drb, Drk)),
+               4.0 * ((double)Dlb * Rl * Dlk + (double)Drb * Rr * Drk +
+                      2.0 * Drb * Rr * n * Dlk + 2.0 * n * Drb * Rl * Dlk));
+  const long long ldH = pad8(Drk), pH = round64((long long)Drb * Rr * ldH);
+  const long long ldV = pad8(Drk), pV = round64((long long)n * Dlk * ldV);
+  const long long ldB = pad8((long long)n * Drb), pB = round64((long long)Dlb * ldB);
+  const long long pT = round64((long long)Rl * Dlk * ldB);
+  c->cb.ensure(sizeof(__nv_bfloat16) * (size_t)(3 * (pH + pV + pB)) +
+                   sizeof(double) * (size_t)n * Dlk * Drk, s);
+  __nv_bfloat16* Hp = c->cb.as<__nv_bfloat16>();
+  __nv_bfloat16* Vp = Hp + 3 * pH;
+  __nv_bfloat16* Bp = Vp + 3 * pV;
+  double* Vt = reinterpret_cast<double*>(Bp + 3 * pB);
+  c->tmp1.ensure(sizeof(float) * (size_t)Drb * Rr * n * Dlk, s);
+  c->tmp2.ensure(sizeof(float) * (size_t)n * Drb * Rl * Dlk, s);
+  c->t3.ensure(sizeof(__nv_bfloat16) * (size_t)(3 * pT), s);
+  float* T1 = c->tmp1.as<float>();
+  float* T2 = c->tmp2.as<float>();
+  __nv_bfloat16* T2p = c->t3.as<__nv_bfloat16>();
+  split3_ld<float>(Hin, (long long)Drb * Rr, Drk, Hp, ldH, pH, s);
+  permute_swap01<double, double>(ket, Vt, n, Dlk, Drk, s);          // Vt[t][a'][b']
+  split3_ld<double>(Vt, (long long)n * Dlk, Drk, Vp, ldV, pV, s);
+  {  // F1: T1[(b w')][(t a')] = sum_b' Hin[(b w')][b'] Vt[(t a')][b']
+    Planes A = planes_at(Hp, ldH, pH), B = planes_at(Vp, ldV, pV);
+    tc_gemm_bf16_pairs(A.p, A.ld, B.p, B.ld, Drb * Rr, n * Dlk, Drk, 6, kPairA, kPairB, T1,
+                       (long long)n * Dlk, 1, 1, s);
+  }
+  {  // F2 (FP32)
+    SparseGeom gm;
+    gm.veclen = Dlk;
+    gm.in_sw = (long long)n * Dlk; gm.in_st = Dlk;
+    gm.out_sw = Dlk; gm.out_ss = (long long)Drb * Rl * Dlk;
+    gm.B1 = Drb; gm.in_b1 = (long long)Rr * n * Dlk; gm.out_b1 = (long long)Rl * Dlk;
+    sparse_rows_apply<float, float, float>(so.rl.rows<float>(), gm, T1, T2, s);
+  }
+  split3_ld<double>(bra, Dlb, (long long)n * Drb, Bp, ldB, pB, s);
+  transpose_split3<float>(T2, n * Drb, Rl * Dlk, T2p, ldB, pT, s);
+  {  // F3: Hout[a][(w a')] = sum_{(s b)} bra[a][(s b)] T2[(s b)][(w a')]
+    Planes A = planes_at(Bp, ldB, pB), B = planes_at(T2p, ldB, pT);
+    tc_gemm_bf16_pairs(A.p, A.ld, B.p, B.ld, Dlb, Rl * Dlk, n * Drb, 6, kPairA, kPairB, Hout,
+                       (long long)Rl * Dlk, 1, 1, s);
+  }
+}
+
 // Split-K factor so that the skinny S4 GEMM fills the GPU.
 int pick_splitk(int M, int N, int K, int tile) {
   const long long tiles = (long long)cdiv(M, tile) * cdiv(N, tile);
@@ -453,6 +559,13 @@ struct Engine {
   void left_update(const T* Hin, int j, const double* bra, int Dlb, int Drb, const double* ket,
                    int Dlk, int Drk, T* Hout) {
     const int n = mpo->phys[j];
+    if constexpr (sizeof(T) == 4) {
+      if (prec == A2_BF16 || prec == A2_F32EMU) {
+        env_left_emu(c, mpo->site[j], Hin, bra, Dlb, Drb, ket, Dlk, Drk, Hout);
+        flops += env_flops(mpo->site[j], std::max(Dlb, Dlk), std::max(Drb, Drk));
+        return;
+      }
+    }
     const T* b = as_compute<T>(c, bra, (long long)Dlb * n * Drb, cvt_bra);
     const T* k = (ket == bra) ? b : as_compute<T>(c, ket, (long long)Dlk * n * Drk, cvt_ket);
     env_left<T>(c, mpo->site[j], Hin, b, Dlb, Drb, k, Dlk, Drk, Hout);
@@ -461,6 +574,13 @@ struct Engine {
   void right_update(const T* Hin, int j, const double* bra, int Dlb, int Drb,
                     const double* ket, int Dlk, int Drk, T* Hout) {
     const int n = mpo->phys[j];
+    if constexpr (sizeof(T) == 4) {
+      if (prec == A2_BF16 || prec == A2_F32EMU) {
+        env_right_emu(c, mpo->site[j], Hin, bra, Dlb, Drb, ket, Dlk, Drk, Hout);
+        flops += env_flops(mpo->site[j], std::max(Dlb, Dlk), std::max(Drb, Drk));
+        return;
+      }
+    }
     const T* b = as_compute<T>(c, bra, (long long)Dlb * n * Drb, cvt_bra);
     const T* k = (ket == bra) ? b : as_compute<T>(c, ket, (long long)Dlk * n * Drk, cvt_ket);
     env_right<T>(c, mpo->site[j], Hin, b, Dlb, Drb, k, Dlk, Drk, Hout);
@@ -744,16 +864,23 @@ int svd_split_dev(a2_ctx* c, const double* M, int rows, int cols, int D_max, dou
   // Only the top min(D_max, rows) eigenpairs can be kept; the discarded weight of any
   // rank is ||M||_F^2 minus the kept eigenvalues, so the rest need not be computed.
   const int kmax = std::min(rows, cols);
-  const int nev = std::min(kmax, D_max);
-  const double total = dot_dev(c, M, M, (long long)rows * cols, 7);
-  std::vector<double> sv(nev);           // singular values, descending
-  int col_of_first = rows - 1;           // column of the largest eigenvector in G
-  if (nev < rows && nev * 4 <= rows * 3) {
+  const bool partial = (D_max < kmax) && (D_max * 4 <= rows * 3);
+  const int nev = partial ? D_max : kmax;   // eigenpairs computed (largest first)
+  std::vector<double> sv(nev);              // singular values, descending
+  int col_of_first = rows - 1;              // column of the largest eigenvector in G
+  double rest = 0.0;                        // weight beyond the computed eigenpairs
+  if (partial) {
+    const double total = dot_dev(c, M, M, (long long)rows * cols, 7);
     c->solver.syevd_top(G, rows, nev, w, s);
     std::vector<double> lam(nev);
     A2_CUDA(cudaMemcpyAsync(lam.data(), w, sizeof(double) * nev, cudaMemcpyDeviceToHost, s));
     A2_CUDA(cudaStreamSynchronize(s));
-    for (int i = 0; i < nev; ++i) sv[i] = std::sqrt(std::max(lam[nev - 1 - i], 0.0));
+    double kept = 0.0;
+    for (int i = 0; i < nev; ++i) {
+      sv[i] = std::sqrt(std::max(lam[nev - 1 - i], 0.0));
+      kept += sv[i] * sv[i];
+    }
+    rest = std::max(total - kept, 0.0);
     col_of_first = nev - 1;
   } else {
     c->solver.syevd(G, rows, w, s);
@@ -762,16 +889,17 @@ int svd_split_dev(a2_ctx* c, const double* M, int rows, int cols, int D_max, dou
     A2_CUDA(cudaStreamSynchronize(s));
     for (int i = 0; i < nev; ++i) sv[i] = std::sqrt(std::max(lam[rows - 1 - i], 0.0));
   }
-  // tail[r] = sum_{k >= r} sigma_k^2 = total - sum_{k < r} sigma_k^2
-  std::vector<double> head(nev + 1, 0.0);
-  for (int i = 0; i < nev; ++i) head[i + 1] = head[i] + sv[i] * sv[i];
-  auto tail = [&](int r) { return std::max(total - head[r], 0.0); };
+  // tail[r] = sum_{k >= r} sigma_k^2 (computed eigenvalues summed from the small end)
+  std::vector<double> tail(nev + 1, 0.0);
+  tail[nev] = rest;
+  for (int i = nev - 1; i >= 0; --i) tail[i] = tail[i + 1] + sv[i] * sv[i];
+  const double total = tail[0];
   int r = nev;
   const double thr = tol * tol * total;
   for (int cand = 1; cand <= nev; ++cand)
-    if (tail(cand) <= thr) { r = cand; break; }
+    if (tail[cand] <= thr) { r = cand; break; }
   r = std::max(1, std::min(r, D_max));
-  if (discarded) *discarded = std::sqrt(tail(r));
+  if (discarded) *discarded = std::sqrt(std::max(tail[r], 0.0));
   if (sv_out) *sv_out = sv;
   // P[i][c] = evec column (rows-1-c): G column-major, column j at G + j*rows
   c->tmp1.ensure(sizeof(double) * (size_t)rows * r, s);
@@ -1810,8 +1938,15 @@ a2_status a2_env_update(a2_ctx* c, const a2_mpo* m, int j, int side, a2_precisio
       convert<double, float>(in, fi, nin, s);
       convert<double, float>(bra, fb, nb, s);
       convert<double, float>(ket, fk, nk, s);
-      if (side == 0) env_left<float>(c, so, fi, fb, Dlb, Drb, fk, Dlk, Drk, fo);
-      else env_right<float>(c, so, fi, fb, Dlb, Drb, fk, Dlk, Drk, fo);
+      if (prec == A2_F32EMU || prec == A2_BF16) {
+        A2_REQUIRE(tc_available(), "this precision needs the tcgen05 path");
+        if (side == 0) env_left_emu(c, so, fi, bra, Dlb, Drb, ket, Dlk, Drk, fo);
+        else env_right_emu(c, so, fi, bra, Dlb, Drb, ket, Dlk, Drk, fo);
+      } else if (side == 0) {
+        env_left<float>(c, so, fi, fb, Dlb, Drb, fk, Dlk, Drk, fo);
+      } else {
+        env_right<float>(c, so, fi, fb, Dlb, Drb, fk, Dlk, Drk, fo);
+      }
       convert<float, double>(fo, out, nout, s);
     }
   });
@@ -1847,7 +1982,8 @@ a2_status a2_profile(a2_ctx* c, int op, int kind, long long* launches, double* m
     else if (op == 1) prof_enable(true);
     else if (op == 2) prof_reset();
     else if (op == 3) prof_read(kind, launches, ms, flops, bytes);
-    else throw ArgError("a2_profile: op must be 0..3");
+    else if (op == 4) { if (launches) *launches = launch_count(); }
+    else throw ArgError("a2_profile: op must be 0..4");
   });
 }
 

@@ -27,7 +27,14 @@ struct NumericError : std::runtime_error {
                             " at " + __FILE__ + ":" + std::to_string(__LINE__));   \
   } while (0)
 
-#define A2_CHECK_LAUNCH() A2_CUDA(cudaGetLastError())
+// Every kernel launch of this library goes through A2_CHECK_LAUNCH, which also counts it.
+void count_launch();
+long long launch_count();
+#define A2_CHECK_LAUNCH()            \
+  do {                               \
+    ::a2::count_launch();            \
+    A2_CUDA(cudaGetLastError());     \
+  } while (0)
 
 #define A2_REQUIRE(cond, msg)                                                      \
   do {                                                                             \

@@ -1,11 +1,19 @@
 // SIMT GEMM, sparse MPO action, vector and small dense kernels (sm_103a).
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
 #include "kernels.cuh"
 
 namespace a2 {
+
+// ----------------------------------------------------------------------------- launch count
+namespace {
+std::atomic<long long> g_launches{0};
+}
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 // ----------------------------------------------------------------------------- profiler
 namespace {
@@ -433,14 +441,15 @@ template void split3_ld<float>(const float*, long long, long long, __nv_bfloat16
 template void split3_ld<double>(const double*, long long, long long, __nv_bfloat16*, long long,
                                 long long, cudaStream_t);
 
-// out planes (cols x ld) = split3 of in^T, in: rows x cols row-major FP64
-__global__ void transpose_split3_kernel(const double* in, int rows, int cols,
-                                        __nv_bfloat16* out, long long ld, long long plane) {
+// out planes (cols x ld) = split3 of in^T, in: rows x cols row-major (FP64 or FP32)
+template <typename TI>
+__global__ void transpose_split3_kernel(const TI* in, int rows, int cols, __nv_bfloat16* out,
+                                        long long ld, long long plane) {
   __shared__ double tile[32][33];
   const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
   for (int j = threadIdx.y; j < 32; j += 8) {
     const int r = by + j, c = bx + threadIdx.x;
-    if (r < rows && c < cols) tile[j][threadIdx.x] = in[(long long)r * cols + c];
+    if (r < rows && c < cols) tile[j][threadIdx.x] = (double)in[(long long)r * cols + c];
   }
   __syncthreads();
   for (int j = threadIdx.y; j < 32; j += 8) {
@@ -455,14 +464,19 @@ __global__ void transpose_split3_kernel(const double* in, int rows, int cols,
     }
   }
 }
-void transpose_split3(const double* in, int rows, int cols, __nv_bfloat16* out, long long ld,
+template <typename TI>
+void transpose_split3(const TI* in, int rows, int cols, __nv_bfloat16* out, long long ld,
                       long long plane, cudaStream_t s) {
   if (!rows || !cols) return;
   dim3 grid(cdiv(cols, 32), cdiv(rows, 32));
   A2_REQUIRE(grid.y < 65536, "transpose grid too large");
-  transpose_split3_kernel<<<grid, dim3(32, 8), 0, s>>>(in, rows, cols, out, ld, plane);
+  transpose_split3_kernel<TI><<<grid, dim3(32, 8), 0, s>>>(in, rows, cols, out, ld, plane);
   A2_CHECK_LAUNCH();
 }
+template void transpose_split3<double>(const double*, int, int, __nv_bfloat16*, long long,
+                                       long long, cudaStream_t);
+template void transpose_split3<float>(const float*, int, int, __nv_bfloat16*, long long,
+                                      long long, cudaStream_t);
 
 template <typename TI, typename TO, typename V>
 void sparse_rows_apply(const SparseRows<V>& sp, const SparseGeom& g, const TI* in, TO* out,

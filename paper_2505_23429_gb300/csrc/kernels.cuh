@@ -63,7 +63,8 @@ template <typename TI>
 void split3_ld(const TI* in, long long rows, long long cols, __nv_bfloat16* out, long long ld,
                long long plane, cudaStream_t s);
 // out planes [p][c*ld + r] = BF16 slice p of in[r*cols + c]  (transpose and split)
-void transpose_split3(const double* in, int rows, int cols, __nv_bfloat16* out, long long ld,
+template <typename TI>
+void transpose_split3(const TI* in, int rows, int cols, __nv_bfloat16* out, long long ld,
                       long long plane, cudaStream_t s);
 
 // ---- permutes and conversions
