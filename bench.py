@@ -50,6 +50,8 @@ def parse():
                    help="run the P groups one after another instead of concurrently")
     p.add_argument("--coarse-eps", type=float, default=None,
                    help="S_hat eigenvalue cut (default 1e-10 for fp64, 1e-5 otherwise)")
+    p.add_argument("--no-fold", action="store_true",
+                   help="keep every MPO core fully sparse (no identity-block fold)")
     p.add_argument("--config", default="chem_L16_D256")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -256,6 +258,8 @@ def main():
     stream = torch.cuda.Stream()
     ctx = a2.Context(dev, stream.cuda_stream)
     mpo = a2.MPO(ctx, mpo_cores)
+    if args.no_fold:
+        mpo.set_fold(False)
     kw = sweep_kwargs(cfg, args.prec, args.solver, args.coarse_eps)
     kw["sequential"] = args.sequential
     P = cfg["P"]
@@ -349,6 +353,7 @@ def main():
                             coarse_eps=kw["coarse_eps"],
                             precision=args.prec, solver=args.solver,
                             groups="sequential" if args.sequential else "concurrent streams",
+                            identity_fold=not args.no_fold,
                             parallelism="replicas" if world > 1 else "1gpu",
                             l2="working set >> 129 MB L2 (no flush)"),
                 energy_final=E_final, time_to_dE_1e6_s=t_conv, iterations_to_dE_1e6=it_conv,
@@ -357,7 +362,11 @@ def main():
                               frac=achieved / peak, traffic=None,
                               per_launch_ms=per_launch, launches=d["launches"],
                               peak_source=peaks["src"]),
-                kernel_classes={k: dict(ms=round(v["ms"], 3), launches=v["launches"])
+                kernel_classes={k: dict(ms=round(v["ms"], 3), launches=v["launches"],
+                                        tflops=round(v["flops"] / (v["ms"] * 1e9), 2)
+                                        if v["ms"] > 0 else None,
+                                        gbs=round(v["bytes"] / (v["ms"] * 1e6), 1)
+                                        if v["ms"] > 0 else None)
                                 for k, v in prof.items()},
                 heff_matvec=mv, clocks=clk, wall_s=wall,
                 gpu_launches=int(launches))
@@ -413,7 +422,9 @@ def matvec_compare(a2, ctx, mpo, cores, cfg, torch, stream):
         res = dict(bond=k, D=D, R=[int(W1.shape[0]), int(W1.shape[3]), int(W2.shape[3])],
                    nnz=[int(np.count_nonzero(W1)), int(np.count_nonzero(W2))], alg_flops=flops)
         for prec, reps in (("bf16", 10), ("f32emu", 10), ("fp64", 1)):
-            ms = timeit(lambda: a2.heff_apply(ctx, mpo, k, HL, HR, x, y, prec=prec), reps)
+            op = a2.HeffOp(ctx, mpo, k, HL, HR, prec=prec)
+            ms = timeit(lambda: op.apply(x, y), reps)
+            op.close()
             res[f"{prec}_ms"] = ms
             res[f"{prec}_tflops"] = flops / (ms * 1e-3) / 1e12
         with torch.cuda.stream(stream):
@@ -431,10 +442,10 @@ def matvec_compare(a2, ctx, mpo, cores, cfg, torch, stream):
         res["plain_bf16_ms"] = pl
         res["plain_bf16_tflops"] = flops / (pl * 1e-3) / 1e12
         out.append(res)
-    return dict(bonds=out, note="timed through a2_heff_apply (includes the per-call conversion "
-                "of FP64 environments to BF16 slices); plain = torch.tensordot chain in BF16 "
-                "with the dense MPO cores (cuBLAS); TFLOP/s use the algorithmic count with MPO "
-                "nonzeros")
+    return dict(bonds=out, note="timed through a2_heff_apply_op (environments converted once, "
+                "as inside a local solve; FP64 x in, FP64 y out); plain = torch.tensordot chain "
+                "in BF16 with the dense MPO cores (cuBLAS) on BF16 environments converted "
+                "beforehand; TFLOP/s use the algorithmic count with MPO nonzeros")
 
 
 def e2e_run(a2, ctx, mpo, cfg, kw, t, steps, torch, stream, world):

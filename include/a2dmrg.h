@@ -97,6 +97,23 @@ a2_status a2_mpo_load(a2_ctx* ctx, int L, const int* phys, const int* mpo_bonds,
 a2_status a2_mpo_nnz(const a2_mpo* mpo, int site, long long* nnz_out);
 a2_status a2_mpo_destroy(a2_mpo* mpo);
 
+/* Identity-on-physical split of a core (a regrouping of the App. A contraction, not a
+ * step of the paper): W[wl][s][t][wr] = delta_st G[wl][wr] + W_rest[wl][s][t][wr] with
+ * G[wl][wr] = W[wl][s][s][wr] where all n diagonal entries are equal and nonzero, else
+ * 0.  Host only (no device, no context): W is a host array [Rl][n][n][Rr], G_out
+ * (host, Rl*Rr, may be NULL) receives G row-major, *nnz_g its nonzero count,
+ * *foldable whether a2_mpo_load marks such a core for folding (the H_eff
+ * applications of the BF16 / split-precision paths then contract G into the
+ * environments once per local problem and keep only W_rest sparse).  A2_EINVAL on
+ * NULL W / outputs or non-positive sizes. */
+a2_status a2_mpo_fold_split(const double* W, int Rl, int n, int Rr, double* G_out,
+                            long long* nnz_g, int* foldable);
+/* Whether core `site` of a loaded MPO is folded (*foldable) and nnz(G) (*nnz_g). */
+a2_status a2_mpo_fold_info(const a2_mpo* mpo, int site, int* foldable, long long* nnz_g);
+/* Enable (1, default) or disable (0) folding for every foldable core of the MPO; the
+ * results agree up to rounding either way.  Not thread-safe against running sweeps. */
+a2_status a2_mpo_set_fold(a2_mpo* mpo, int enable);
+
 /* ---- one global iteration -------------------------------------------------- */
 
 typedef struct {
@@ -164,6 +181,22 @@ a2_status a2_energy(a2_ctx* ctx, const a2_tt* tt, const a2_mpo* mpo, a2_precisio
  * L: [Dl][R_k][Dl], R: [Dr][R_{k+2}][Dr], x, y: [Dl][n_k][n_k+1][Dr] (device). */
 a2_status a2_heff_apply(a2_ctx* ctx, const a2_mpo* mpo, int k, a2_precision prec, int Dl, int Dr,
                         const double* L, const double* R, const double* x, double* y);
+
+/* The same operator as a handle whose environments are copied / converted once (as
+ * inside a local solve of Alg. 2 step 2, where H^L and H^R stay fixed while Lanczos
+ * applies H_eff many times): a2_heff_create copies L, R (device, FP64, layouts as
+ * above; the caller may free them afterwards) into the precision's working form
+ * (FP64, FP32, BF16 or split BF16 planes, with the identity-block fold of
+ * a2_mpo_fold_split); a2_heff_apply_op(x, y) then enqueues y = H_eff x on the
+ * context's stream (device x, y as above; asynchronous: a2_synchronize before y is
+ * read elsewhere).  The handle references the context and the MPO (both must
+ * outlive it) and uses the context's scratch: one application at a time per context.
+ * Errors: A2_EINVAL on bad sizes / NULLs, A2_ECUDA on CUDA failure. */
+typedef struct a2_heff a2_heff;
+a2_status a2_heff_create(a2_ctx* ctx, const a2_mpo* mpo, int k, a2_precision prec, int Dl,
+                         int Dr, const double* L, const double* R, a2_heff** out);
+a2_status a2_heff_apply_op(a2_heff* op, const double* x, double* y);
+a2_status a2_heff_destroy(a2_heff* op);
 
 /* Environment update at site j (eqs. env_L / env_R and the update of App. A):
  * side 0 (left):  out[b,w',b'] = sum bra[a,s,b] in[a,w,a'] A_j[w,s,t,w'] ket[a',t,b'],

@@ -7,6 +7,7 @@ and for the current CUDA stream.
 """
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -71,6 +72,14 @@ def lib():
         "a2_mpo_load": [_P, ctypes.c_int, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_P)],
         "a2_mpo_nnz": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)],
         "a2_mpo_destroy": [_P],
+        "a2_mpo_fold_split": [_D, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D,
+                              ctypes.POINTER(ctypes.c_longlong), _I],
+        "a2_mpo_fold_info": [_P, ctypes.c_int, _I, ctypes.POINTER(ctypes.c_longlong)],
+        "a2_mpo_set_fold": [_P, ctypes.c_int],
+        "a2_heff_create": [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
+                           _P, ctypes.POINTER(_P)],
+        "a2_heff_apply_op": [_P, _P, _P],
+        "a2_heff_destroy": [_P],
         "a2_additive_sweep": [_P, _P, _P, ctypes.POINTER(SweepOpts), ctypes.POINTER(SweepReport)],
         "a2_classical_sweep": [_P, _P, _P, ctypes.POINTER(SweepOpts), ctypes.POINTER(SweepReport)],
         "a2_coarse_solve": [_P, ctypes.c_int, _D, _D, ctypes.c_double, _D, _D, _I],
@@ -107,7 +116,9 @@ def exported_symbols():
             "a2_tt_destroy", "a2_mpo_load", "a2_mpo_nnz", "a2_mpo_destroy",
             "a2_additive_sweep", "a2_classical_sweep", "a2_coarse_solve", "a2_energy",
             "a2_heff_apply", "a2_env_update", "a2_svd_split", "a2_gemm_bf16",
-            "a2_device_error", "a2_profile", "a2_heff_apply_noalloc"]
+            "a2_device_error", "a2_profile", "a2_heff_apply_noalloc", "a2_mpo_fold_split",
+            "a2_mpo_fold_info", "a2_mpo_set_fold", "a2_heff_create", "a2_heff_apply_op",
+            "a2_heff_destroy"]
 
 
 def _dp(a):
@@ -125,9 +136,13 @@ def _ptr(t):
 class Context:
     def __init__(self, device=0, stream=None):
         self._h = _P()
+        self._children = []     # weak references to TT / MPO / HeffOp handles, in creation order
         st = lib().a2_ctx_create(device, _P(stream) if stream else None, ctypes.byref(self._h))
         if st != 0:
             raise A2Error(st, "a2_ctx_create failed")
+
+    def _adopt(self, child):
+        self._children.append(weakref.ref(child))
 
     def check(self, st):
         if st != 0:
@@ -137,7 +152,13 @@ class Context:
         self.check(lib().a2_ctx_synchronize(self._h))
 
     def close(self):
+        """Destroy every handle made on this context (newest first), then the context."""
         if self._h:
+            for ref in reversed(self._children):
+                ch = ref()
+                if ch is not None:
+                    ch.close()
+            self._children = []
             lib().a2_ctx_destroy(self._h)
             self._h = _P()
 
@@ -151,6 +172,7 @@ class Context:
 class TT:
     def __init__(self, ctx, handle, phys):
         self.ctx, self._h, self.phys = ctx, handle, list(phys)
+        ctx._adopt(self)
 
     @classmethod
     def random(cls, ctx, phys, bonds, seed):
@@ -213,12 +235,22 @@ class MPO:
         self._h = _P()
         ctx.check(lib().a2_mpo_load(ctx._h, L, phys.ctypes.data_as(_I), R.ctypes.data_as(_I),
                                     ptrs, ctypes.byref(self._h)))
+        ctx._adopt(self)
         self.L, self.phys, self.R = L, phys, R
 
     def nnz(self, j):
         v = ctypes.c_longlong()
         self.ctx.check(lib().a2_mpo_nnz(self._h, j, ctypes.byref(v)))
         return v.value
+
+    def fold_info(self, j):
+        """(folded, nnz(G)) of core j (identity-on-physical block, see fold_split)."""
+        f, v = ctypes.c_int(), ctypes.c_longlong()
+        self.ctx.check(lib().a2_mpo_fold_info(self._h, j, ctypes.byref(f), ctypes.byref(v)))
+        return bool(f.value), v.value
+
+    def set_fold(self, enable):
+        self.ctx.check(lib().a2_mpo_set_fold(self._h, 1 if enable else 0))
 
     def close(self):
         if self._h:
@@ -308,6 +340,32 @@ def heff_apply(ctx, mpo, k, Lenv, Renv, x, y, prec="fp64"):
                                   _ptr(Renv), _ptr(x), _ptr(y)))
 
 
+class HeffOp:
+    """H_eff at bond k with its environments converted once (a2_heff_create); apply(x, y)
+    enqueues y = H_eff x on the context's stream."""
+    def __init__(self, ctx, mpo, k, Lenv, Renv, prec="fp64"):
+        Dl, Dr = Lenv.shape[0], Renv.shape[0]
+        self.ctx, self.mpo = ctx, mpo
+        self._h = _P()
+        ctx.check(lib().a2_heff_create(ctx._h, mpo._h, k, PRECISION[prec], Dl, Dr,
+                                       _ptr(Lenv), _ptr(Renv), ctypes.byref(self._h)))
+        ctx._adopt(self)
+
+    def apply(self, x, y):
+        self.ctx.check(lib().a2_heff_apply_op(self._h, _ptr(x), _ptr(y)))
+
+    def close(self):
+        if self._h:
+            lib().a2_heff_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def env_update(ctx, mpo, j, side, Hin, bra, ket, out, prec="fp64"):
     Dlb, _, Drb = bra.shape
     Dlk, _, Drk = ket.shape
@@ -363,3 +421,16 @@ def heff_apply_noalloc(ctx, mpo, k, Lenv, Renv, x, y):
     Dl, Dr = Lenv.shape[0], Renv.shape[0]
     ctx.check(lib().a2_heff_apply_noalloc(ctx._h, mpo._h, k, Dl, Dr, _ptr(Lenv), _ptr(Renv),
                                           _ptr(x), _ptr(y)))
+
+
+def fold_split(W):
+    """Identity-on-physical split of a core W[wl][s][t][wr] (host only): returns
+    (G, nnz(G), foldable) with W = delta_st G + W_rest."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    Rl, n, _, Rr = W.shape
+    G = np.zeros((Rl, Rr))
+    nz, f = ctypes.c_longlong(), ctypes.c_int()
+    st = lib().a2_mpo_fold_split(_dp(W), Rl, n, Rr, _dp(G), ctypes.byref(nz), ctypes.byref(f))
+    if st != 0:
+        raise A2Error(st, "a2_mpo_fold_split failed")
+    return G, nz.value, bool(f.value)

@@ -38,7 +38,7 @@ struct a2_ctx {
   std::string err;
   DevBuf scal, partial;         // device scalars, reduction partials
   double* h_scal = nullptr;     // pinned host mirror
-  DevBuf t1, t2, t3, xa, ya, cb, ck, gram, wv, tmp1, tmp2;   // scratch
+  DevBuf t1, t2, t3, xa, ya, cb, ck, gram, wv, tmp1, tmp2, tf;   // scratch
   std::vector<a2_ctx*> lanes;   // per-group contexts (own stream, scratch, solver)
   std::mutex lane_mu;
 };
@@ -56,6 +56,11 @@ namespace {
 struct SiteOps {
   int Rl = 0, n = 0, Rr = 0;
   long long nnz = 0;
+  // W = I (x) G + W_rest (G[wl][wr] = the common value of the n diagonal entries
+  // W[wl][s][s][wr]); when G is large (the hand-over core of the operator automaton)
+  // the H_eff chains fold G into the environments and keep only W_rest sparse.
+  int foldable = 0, fold_on = 1;
+  long long nnz_g = 0;
   struct Part {
     int nrows = 0, nnz = 0;
     DevBuf ptr, rw, rs, nw, nt, v64, v32;
@@ -73,6 +78,10 @@ struct SiteOps {
       return r;
     }
   } lr, rl;
+  Part lr_rest;            // left-to-right action of W_rest (foldable cores only)
+  Part g_lr;               // G by columns: rows wr, entries (wl, 0, G[wl][wr])
+  Part g_rl;               // G by rows:    rows wl, entries (wr, 0, G[wl][wr])
+  bool fold() const { return foldable && fold_on; }
 };
 
 }  // namespace
@@ -86,6 +95,29 @@ struct a2_mpo {
 
 // ============================================================================= helpers
 namespace {
+
+// I (x) G split of an MPO core W[wl][s][t][wr]: G[wl][wr] = W[wl][s][s][wr] where all n
+// diagonal entries are equal and nonzero, else 0 (G: Rl x Rr, written in full).  Returns
+// the number of nonzeros of G.
+long long identity_block_split(const double* W, int Rl, int n, int Rr, double* G) {
+  long long nnz = 0;
+  for (int wl = 0; wl < Rl; ++wl)
+    for (int wr = 0; wr < Rr; ++wr) {
+      const double v = W[(((size_t)wl * n + 0) * n + 0) * Rr + wr];
+      bool same = v != 0.0;
+      for (int sx = 1; sx < n && same; ++sx)
+        same = W[(((size_t)wl * n + sx) * n + sx) * Rr + wr] == v;
+      G[(size_t)wl * Rr + wr] = same ? v : 0.0;
+      nnz += same ? 1 : 0;
+    }
+  return nnz;
+}
+
+// Folding G into an environment costs a dense contraction over the whole (Rl x Rr)
+// block; it pays when G holds at least ~1/64 of that block and is not tiny.
+bool fold_worthwhile(long long nnz_g, int Rl, int Rr) {
+  return nnz_g >= 1024 && nnz_g * 64 >= (long long)Rl * Rr;
+}
 
 void upload(DevBuf& b, const void* h, size_t bytes, cudaStream_t s) {
   b.ensure(bytes, s);
@@ -119,9 +151,10 @@ void build_part(SiteOps::Part& part, const std::vector<std::vector<std::array<do
   upload(part.v32, v32.data(), v32.size() * sizeof(float), s);
 }
 
-// Scan one dense core W[wl][s][t][wr] into the two sparse actions.
-void build_site(SiteOps& so, const double* W, int Rl, int n, int Rr, cudaStream_t s) {
-  so.Rl = Rl; so.n = n; so.Rr = Rr;
+// Scan a dense core W[wl][s][t][wr] (minus `sub` = I (x) G when given) into the two
+// sparse actions; returns the number of nonzeros.
+long long scan_actions(const double* W, const double* G, int Rl, int n, int Rr,
+                       SiteOps::Part& plr, SiteOps::Part* prl, cudaStream_t s) {
   std::vector<std::vector<std::array<double, 3>>> lr((size_t)Rr * n), rl((size_t)Rl * n);
   std::vector<std::pair<int, int>> lrid((size_t)Rr * n), rlid((size_t)Rl * n);
   for (int wr = 0; wr < Rr; ++wr)
@@ -133,15 +166,39 @@ void build_site(SiteOps& so, const double* W, int Rl, int n, int Rr, cudaStream_
     for (int sx = 0; sx < n; ++sx)
       for (int t = 0; t < n; ++t)
         for (int wr = 0; wr < Rr; ++wr) {
-          const double v = W[(((size_t)wl * n + sx) * n + t) * Rr + wr];
+          double v = W[(((size_t)wl * n + sx) * n + t) * Rr + wr];
+          if (G && sx == t) v -= G[(size_t)wl * Rr + wr];
           if (v == 0.0) continue;
           ++nnz;
           lr[(size_t)wr * n + sx].push_back({(double)wl, (double)t, v});
           rl[(size_t)wl * n + sx].push_back({(double)wr, (double)t, v});
         }
-  so.nnz = nnz;
-  build_part(so.lr, lr, lrid, s);
-  build_part(so.rl, rl, rlid, s);
+  build_part(plr, lr, lrid, s);
+  if (prl) build_part(*prl, rl, rlid, s);
+  return nnz;
+}
+
+void build_site(SiteOps& so, const double* W, int Rl, int n, int Rr, cudaStream_t s) {
+  so.Rl = Rl; so.n = n; so.Rr = Rr;
+  so.nnz = scan_actions(W, nullptr, Rl, n, Rr, so.lr, &so.rl, s);
+  std::vector<double> G((size_t)Rl * Rr, 0.0);
+  so.nnz_g = identity_block_split(W, Rl, n, Rr, G.data());
+  so.foldable = fold_worthwhile(so.nnz_g, Rl, Rr) ? 1 : 0;
+  if (!so.foldable) return;
+  scan_actions(W, G.data(), Rl, n, Rr, so.lr_rest, nullptr, s);
+  std::vector<std::vector<std::array<double, 3>>> gc((size_t)Rr), gr((size_t)Rl);
+  std::vector<std::pair<int, int>> gcid((size_t)Rr), grid((size_t)Rl);
+  for (int wr = 0; wr < Rr; ++wr) gcid[wr] = {wr, 0};
+  for (int wl = 0; wl < Rl; ++wl) grid[wl] = {wl, 0};
+  for (int wl = 0; wl < Rl; ++wl)
+    for (int wr = 0; wr < Rr; ++wr) {
+      const double v = G[(size_t)wl * Rr + wr];
+      if (v == 0.0) continue;
+      gc[wr].push_back({(double)wl, 0.0, v});
+      gr[wl].push_back({(double)wr, 0.0, v});
+    }
+  build_part(so.g_lr, gc, gcid, s);
+  build_part(so.g_rl, gr, grid, s);
 }
 
 double* scal(a2_ctx* c, int i) { return c->scal.as<double>() + i; }
@@ -168,7 +225,7 @@ void destroy_ctx_resources(a2_ctx* c) {
   cudaStreamSynchronize(c->stream);
   c->solver.destroy();
   for (DevBuf* b : {&c->scal, &c->partial, &c->t1, &c->t2, &c->t3, &c->xa, &c->ya, &c->cb, &c->ck,
-                    &c->gram, &c->wv, &c->tmp1, &c->tmp2})
+                    &c->gram, &c->wv, &c->tmp1, &c->tmp2, &c->tf})
     b->release();
   cudaStreamSynchronize(c->stream);
   if (c->h_scal) cudaFreeHost(c->h_scal);
@@ -473,31 +530,82 @@ double env_flops(const SiteOps& so, int Dl, int Dr) {
 // BF16 environments with padded rows for TMA: L [(a w)][a'] -> ld pad8(Dl); R [b][(w2 b')].
 // With three planes each value is split into BF16 hi + mid + lo slices (plane 0 alone
 // is the plain BF16 rounding used by the BF16 matvec).
+// Fold of an identity-on-physical block W = I (x) G + W_rest (App. A contraction regrouped):
+//   A_k = I (x) G:     sum_w L[a,w,a'] G[w,w1] = Lt[a,w1,a'], so stage S2's G part is the
+//                      GEMM Lt x (written straight into T2);
+//   A_{k+1} = I (x) G: sum_w2 G[w1,w2] R[b,w2,b'] = Rt[b,w1,b'], so stage S3's G part
+//                      becomes a second K segment of S4 over T2: sum_{w1,b'} T2 Rt.
+// Lt / Rt are built once per local problem (the environments are fixed during it).
 struct Bf16Envs {
-  DevBuf buf;
+  DevBuf buf, fbuf, ftmp;
   const __nv_bfloat16* L = nullptr;
   const __nv_bfloat16* R = nullptr;
-  long long ldl = 0, ldr = 0, lplane = 0, rplane = 0;
+  const __nv_bfloat16* Lt = nullptr;    // [(a w1)][a'], row stride ldl, plane ltplane
+  const __nv_bfloat16* Rt = nullptr;    // [b][w1][b'] dense, plane rtplane
+  long long ldl = 0, ldr = 0, lplane = 0, rplane = 0, ltplane = 0, rtplane = 0;
   int planes = 0;
   template <typename T>
-  void set(a2_ctx* c, const T* Lf, int Dl, int Rl, const T* Rf, int Dr, int Rr, int np = 1) {
+  void set(a2_ctx* c, const T* Lf, int Dl, int Rl, const T* Rf, int Dr, int Rr, int np,
+           const SiteOps* A1 = nullptr, const SiteOps* A2 = nullptr) {
+    cudaStream_t s = c->stream;
     ldl = pad8(Dl);
     ldr = pad8((long long)Rr * Dr);
     lplane = ((long long)Dl * Rl * ldl + 63) / 64 * 64;   // keep planes 128-byte aligned
     rplane = ((long long)Dr * ldr + 63) / 64 * 64;
     planes = np;
-    buf.ensure(sizeof(__nv_bfloat16) * (size_t)(np * (lplane + rplane)), c->stream);
+    buf.ensure(sizeof(__nv_bfloat16) * (size_t)(np * (lplane + rplane)), s);
     __nv_bfloat16* lb = buf.as<__nv_bfloat16>();
     __nv_bfloat16* rb = lb + np * lplane;
     if (np == 1) {
-      convert_ld<T, __nv_bfloat16>(Lf, lb, (long long)Dl * Rl, Dl, ldl, c->stream);
-      convert_ld<T, __nv_bfloat16>(Rf, rb, Dr, (long long)Rr * Dr, ldr, c->stream);
+      convert_ld<T, __nv_bfloat16>(Lf, lb, (long long)Dl * Rl, Dl, ldl, s);
+      convert_ld<T, __nv_bfloat16>(Rf, rb, Dr, (long long)Rr * Dr, ldr, s);
     } else {
-      split3_ld<T>(Lf, (long long)Dl * Rl, Dl, lb, ldl, lplane, c->stream);
-      split3_ld<T>(Rf, Dr, (long long)Rr * Dr, rb, ldr, rplane, c->stream);
+      split3_ld<T>(Lf, (long long)Dl * Rl, Dl, lb, ldl, lplane, s);
+      split3_ld<T>(Rf, Dr, (long long)Rr * Dr, rb, ldr, rplane, s);
     }
     L = lb;
     R = rb;
+    Lt = Rt = nullptr;
+    if (!A1 || !A2) return;
+    const bool fl = A1->fold();
+    const bool fr = A2->fold() && Dr % 8 == 0 && 128 % (A1->n * A2->n) == 0;
+    if (!fl && !fr) return;
+    const int R1 = A1->Rr;
+    ltplane = fl ? ((long long)Dl * R1 * ldl + 63) / 64 * 64 : 0;
+    rtplane = fr ? ((long long)Dr * R1 * Dr + 63) / 64 * 64 : 0;
+    fbuf.ensure(sizeof(__nv_bfloat16) * (size_t)(np * (ltplane + rtplane)), s);
+    ftmp.ensure(sizeof(T) * (size_t)std::max(fl ? (long long)Dl * R1 * Dl : 0,
+                                             fr ? (long long)Dr * R1 * Dr : 0), s);
+    T* tmp = ftmp.as<T>();
+    __nv_bfloat16* ltb = fbuf.as<__nv_bfloat16>();
+    __nv_bfloat16* rtb = ltb + np * ltplane;
+    if (fl) {   // Lt[a][w1][a'] = sum_w G[w][w1] L[a][w][a']
+      SparseGeom gm;
+      gm.veclen = Dl;
+      gm.in_sw = Dl; gm.out_sw = Dl;
+      gm.B1 = Dl; gm.in_b1 = (long long)Rl * Dl; gm.out_b1 = (long long)R1 * Dl;
+      sparse_rows_apply<T, T, T>(A1->g_lr.rows<T>(), gm, Lf, tmp, s);
+      if (np == 1) convert_ld<T, __nv_bfloat16>(tmp, ltb, (long long)Dl * R1, Dl, ldl, s);
+      else split3_ld<T>(tmp, (long long)Dl * R1, Dl, ltb, ldl, ltplane, s);
+      Lt = ltb;
+    }
+    if (fr) {   // Rt[b][w1][b'] = sum_w2 G[w1][w2] R[b][w2][b']
+      SparseGeom gm;
+      gm.veclen = Dr;
+      gm.in_sw = Dr; gm.out_sw = Dr;
+      gm.B1 = Dr; gm.in_b1 = (long long)Rr * Dr; gm.out_b1 = (long long)R1 * Dr;
+      sparse_rows_apply<T, T, T>(A2->g_rl.rows<T>(), gm, Rf, tmp, s);
+      const long long cols = (long long)R1 * Dr;
+      if (np == 1) convert_ld<T, __nv_bfloat16>(tmp, rtb, Dr, cols, cols, s);
+      else split3_ld<T>(tmp, Dr, cols, rtb, cols, rtplane, s);
+      Rt = rtb;
+    }
+  }
+  HeffFold fold() const {
+    HeffFold f;
+    f.Lt = Lt; f.ltplane = ltplane;
+    f.Rt = Rt; f.rtplane = rtplane;
+    return f;
   }
 };
 
@@ -505,8 +613,11 @@ void heff_bf16(a2_ctx* c, const SiteOps& A1, const SiteOps& A2, const Bf16Envs& 
                const double* x, double* y) {
   const long long N = (long long)Dl * A1.n * A2.n * Dr;
   c->ya.ensure(sizeof(float) * N, c->stream);
+  const auto& W1 = E.Lt ? A1.lr_rest : A1.lr;
+  const auto& W2 = E.Rt ? A2.lr_rest : A2.lr;
   tc_heff_bf16(c->stream, A1.n, A2.n, A1.Rl, A1.Rr, A2.Rr, Dl, Dr, E.L, E.ldl, E.R, E.ldr, x,
-               c->ya.as<float>(), A1.lr.rows<float>(), A2.lr.rows<float>(), c->t1, c->t2, c->t3);
+               c->ya.as<float>(), W1.rows<float>(), W2.rows<float>(), E.fold(), c->t1, c->t2,
+               c->t3, c->tf);
   convert<float, double>(c->ya.as<float>(), y, N, c->stream);
 }
 
@@ -515,9 +626,11 @@ void heff_emu(a2_ctx* c, const SiteOps& A1, const SiteOps& A2, const Bf16Envs& E
   A2_REQUIRE(E.planes == 3, "split environments required");
   const long long N = (long long)Dl * A1.n * A2.n * Dr;
   c->ya.ensure(sizeof(float) * N, c->stream);
+  const auto& W1 = E.Lt ? A1.lr_rest : A1.lr;
+  const auto& W2 = E.Rt ? A2.lr_rest : A2.lr;
   tc_heff_f32emu(c->stream, A1.n, A2.n, A1.Rl, A1.Rr, A2.Rr, Dl, Dr, E.L, E.ldl, E.lplane, E.R,
-                 E.ldr, E.rplane, x, c->ya.as<float>(), A1.lr.rows<float>(), A2.lr.rows<float>(),
-                 c->t1, c->t2, c->t3);
+                 E.ldr, E.rplane, x, c->ya.as<float>(), W1.rows<float>(), W2.rows<float>(),
+                 E.fold(), c->t1, c->t2, c->t3, c->tf);
   convert<float, double>(c->ya.as<float>(), y, N, c->stream);
 }
 
@@ -1091,7 +1204,8 @@ struct Sweeper {
         heff_diag<T>(c, mpo->site[k], mpo->site[k + 1], HLcur, HRk, Dl, Dr, dg.as<double>());
         if constexpr (sizeof(T) == 4) {
           if (o.prec == A2_BF16 || o.prec == A2_F32EMU) {
-            eng.bfe.set(c, HLcur, Dl, mpo->R[k], HRk, Dr, mpo->R[k + 2], 3);
+            eng.bfe.set(c, HLcur, Dl, mpo->R[k], HRk, Dr, mpo->R[k + 2], 3, &mpo->site[k],
+                         &mpo->site[k + 1]);
             auto mve = [&](const double* in, double* out) { eng.matvec_emu(k, Dl, Dr, in, out); };
             lr = davidson(c, mve, dg.as<double>(), x.as<double>(), N, o.eig_tol, o.max_krylov,
                           o.max_krylov * o.max_restarts);
@@ -1105,7 +1219,8 @@ struct Sweeper {
       }
       if constexpr (sizeof(T) == 4) {
         if (!done && (o.prec == A2_BF16 || o.prec == A2_F32EMU)) {
-          eng.bfe.set(c, HLcur, Dl, mpo->R[k], HRk, Dr, mpo->R[k + 2], 3);
+          eng.bfe.set(c, HLcur, Dl, mpo->R[k], HRk, Dr, mpo->R[k + 2], 3, &mpo->site[k],
+                         &mpo->site[k + 1]);
           if (o.prec == A2_BF16) {
             // tensor-core Lanczos on the BF16 operator to a loose tolerance ...
             auto mvb = [&](const double* in, double* out) { eng.matvec_bf16(k, Dl, Dr, in, out); };
@@ -1789,6 +1904,33 @@ a2_status a2_mpo_nnz(const a2_mpo* m, int site, long long* nnz) {
   return A2_OK;
 }
 
+a2_status a2_mpo_fold_split(const double* W, int Rl, int n, int Rr, double* G_out,
+                            long long* nnz_g, int* foldable) {
+  if (!W || !nnz_g || !foldable || Rl < 1 || n < 1 || Rr < 1) return A2_EINVAL;
+  try {
+    std::vector<double> G((size_t)Rl * Rr, 0.0);
+    *nnz_g = identity_block_split(W, Rl, n, Rr, G.data());
+    *foldable = fold_worthwhile(*nnz_g, Rl, Rr) ? 1 : 0;
+    if (G_out) std::copy(G.begin(), G.end(), G_out);
+  } catch (...) {
+    return A2_ENOMEM;
+  }
+  return A2_OK;
+}
+
+a2_status a2_mpo_fold_info(const a2_mpo* m, int site, int* foldable, long long* nnz_g) {
+  if (!m || !foldable || !nnz_g || site < 0 || site >= m->L) return A2_EINVAL;
+  *foldable = m->site[site].fold() ? 1 : 0;
+  *nnz_g = m->site[site].nnz_g;
+  return A2_OK;
+}
+
+a2_status a2_mpo_set_fold(a2_mpo* m, int enable) {
+  if (!m) return A2_EINVAL;
+  for (auto& so : m->site) so.fold_on = enable ? 1 : 0;
+  return A2_OK;
+}
+
 a2_status a2_mpo_destroy(a2_mpo* m) {
   if (!m) return A2_EINVAL;
   cudaStreamSynchronize(m->ctx->stream);
@@ -1876,6 +2018,86 @@ a2_status a2_energy(a2_ctx* c, const a2_tt* t, const a2_mpo* m, a2_precision pre
   });
 }
 
+struct a2_heff {
+  a2_ctx* ctx = nullptr;
+  const a2_mpo* mpo = nullptr;
+  int k = 0, Dl = 0, Dr = 0;
+  a2_precision prec = A2_FP64;
+  DevBuf env;          // FP64 / FP32 copies of L and R
+  Bf16Envs bfe;        // BF16 / split planes (with folded blocks)
+};
+
+a2_status a2_heff_create(a2_ctx* c, const a2_mpo* m, int k, a2_precision prec, int Dl, int Dr,
+                         const double* L, const double* R, a2_heff** out) {
+  if (!c || !m || !out) return c ? fail(c, A2_EINVAL, "null argument") : A2_EINVAL;
+  *out = nullptr;
+  auto* h = new (std::nothrow) a2_heff();
+  if (!h) return A2_ENOMEM;
+  a2_status st = guarded(c, [&] {
+    A2_REQUIRE(k >= 0 && k + 1 < m->L && Dl >= 1 && Dr >= 1 && L && R,
+               "a2_heff_create: bad arguments");
+    const SiteOps& A1 = m->site[k];
+    const SiteOps& A2 = m->site[k + 1];
+    cudaStream_t s = c->stream;
+    h->ctx = c; h->mpo = m; h->k = k; h->Dl = Dl; h->Dr = Dr; h->prec = prec;
+    const long long nl = (long long)Dl * A1.Rl * Dl, nr = (long long)Dr * A2.Rr * Dr;
+    if (prec == A2_FP64) {
+      h->env.ensure(sizeof(double) * (size_t)(nl + nr), s);
+      A2_CUDA(cudaMemcpyAsync(h->env.p, L, sizeof(double) * nl, cudaMemcpyDeviceToDevice, s));
+      A2_CUDA(cudaMemcpyAsync(h->env.as<double>() + nl, R, sizeof(double) * nr,
+                              cudaMemcpyDeviceToDevice, s));
+    } else if (prec == A2_FP32) {
+      h->env.ensure(sizeof(float) * (size_t)(nl + nr), s);
+      convert<double, float>(L, h->env.as<float>(), nl, s);
+      convert<double, float>(R, h->env.as<float>() + nl, nr, s);
+    } else if (prec == A2_BF16 || prec == A2_F32EMU) {
+      A2_REQUIRE(tc_available(), "this precision needs the tcgen05 path");
+      h->bfe.set<double>(c, L, Dl, A1.Rl, R, Dr, A2.Rr, prec == A2_BF16 ? 1 : 3, &A1, &A2);
+    } else {
+      throw ArgError("unsupported precision");
+    }
+    A2_CUDA(cudaStreamSynchronize(s));
+  });
+  if (st != A2_OK) { delete h; return st; }
+  *out = h;
+  return A2_OK;
+}
+
+a2_status a2_heff_apply_op(a2_heff* h, const double* x, double* y) {
+  if (!h) return A2_EINVAL;
+  a2_ctx* c = h->ctx;
+  return guarded(c, [&] {
+    A2_REQUIRE(x && y, "a2_heff_apply_op: null vector");
+    const SiteOps& A1 = h->mpo->site[h->k];
+    const SiteOps& A2 = h->mpo->site[h->k + 1];
+    const int Dl = h->Dl, Dr = h->Dr;
+    const long long nl = (long long)Dl * A1.Rl * Dl;
+    cudaStream_t s = c->stream;
+    if (h->prec == A2_FP64) {
+      heff_T<double>(c, A1, A2, h->env.as<double>(), h->env.as<double>() + nl, Dl, Dr, x, y);
+    } else if (h->prec == A2_FP32) {
+      const long long N = (long long)Dl * A1.n * A2.n * Dr;
+      c->xa.ensure(sizeof(float) * N, s);
+      c->ya.ensure(sizeof(float) * N, s);
+      convert<double, float>(x, c->xa.as<float>(), N, s);
+      heff_T<float>(c, A1, A2, h->env.as<float>(), h->env.as<float>() + nl, Dl, Dr,
+                    c->xa.as<float>(), c->ya.as<float>());
+      convert<float, double>(c->ya.as<float>(), y, N, s);
+    } else if (h->prec == A2_BF16) {
+      heff_bf16(c, A1, A2, h->bfe, Dl, Dr, x, y);
+    } else {
+      heff_emu(c, A1, A2, h->bfe, Dl, Dr, x, y);
+    }
+  });
+}
+
+a2_status a2_heff_destroy(a2_heff* h) {
+  if (!h) return A2_EINVAL;
+  cudaStreamSynchronize(h->ctx->stream);
+  delete h;
+  return A2_OK;
+}
+
 a2_status a2_heff_apply(a2_ctx* c, const a2_mpo* m, int k, a2_precision prec, int Dl, int Dr,
                         const double* L, const double* R, const double* x, double* y) {
   if (!c || !m) return A2_EINVAL;
@@ -1903,7 +2125,7 @@ a2_status a2_heff_apply(a2_ctx* c, const a2_mpo* m, int k, a2_precision prec, in
     } else if (prec == A2_BF16 || prec == A2_F32EMU) {
       A2_REQUIRE(tc_available(), "this precision needs the tcgen05 path");
       Bf16Envs E;
-      E.set<double>(c, L, Dl, A1.Rl, R, Dr, A2.Rr, prec == A2_BF16 ? 1 : 3);
+      E.set<double>(c, L, Dl, A1.Rl, R, Dr, A2.Rr, prec == A2_BF16 ? 1 : 3, &A1, &A2);
       if (prec == A2_BF16) heff_bf16(c, A1, A2, E, Dl, Dr, x, y);
       else heff_emu(c, A1, A2, E, Dl, Dr, x, y);
       A2_CUDA(cudaStreamSynchronize(s));
@@ -1930,8 +2152,10 @@ a2_status a2_env_update(a2_ctx* c, const a2_mpo* m, int j, int side, a2_precisio
       const long long nin = side == 0 ? (long long)Dlb * so.Rl * Dlk : (long long)Drb * so.Rr * Drk;
       const long long nout = side == 0 ? (long long)Drb * so.Rr * Drk : (long long)Dlb * so.Rl * Dlk;
       const long long nb = (long long)Dlb * n * Drb, nk = (long long)Dlk * n * Drk;
-      c->cb.ensure(sizeof(float) * (nin + nout + nb + nk), s);
-      float* fi = c->cb.as<float>();
+      // own buffer: the update kernels use the context scratch (cb, tmp1, tmp2, t3)
+      DevBuf fbuf;
+      fbuf.ensure(sizeof(float) * (nin + nout + nb + nk), s);
+      float* fi = fbuf.as<float>();
       float* fo = fi + nin;
       float* fb = fo + nout;
       float* fk = fb + nb;

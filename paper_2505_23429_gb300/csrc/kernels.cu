@@ -239,6 +239,7 @@ __global__ void sparse_rows_kernel(SparseRows<V> sp, SparseGeom g, const TI* __r
       acc += (Acc)sp.nz_val[e] * load_as<Acc, TI>(in + ib + ci + v);
     }
     const long long ro = sp.row_w[r] * g.out_sw + sp.row_s[r] * g.out_ss;
+    if (g.accumulate) acc += load_as<Acc, TO>(out + ob + ro + v);
     out[ob + ro + v] = from_acc<TO, Acc>(acc);
   }
 }
@@ -270,7 +271,7 @@ __device__ __forceinline__ void store_vec(TO* p, const A (&x)[NV]) {
   }
 }
 
-template <typename TI, typename TO, typename V>
+template <typename TI, typename TO, typename V, bool ACC>
 __global__ void __launch_bounds__(256)
 sparse_rows_vec_kernel(SparseRows<V> sp, SparseGeom g, const TI* __restrict__ in,
                        TO* __restrict__ out, int lpr, int rows_per_cta) {
@@ -302,6 +303,10 @@ sparse_rows_vec_kernel(SparseRows<V> sp, SparseGeom g, const TI* __restrict__ in
       for (int i = 0; i < NV; ++i) acc[i] = fma(w, x[i], acc[i]);
     }
     const long long ro = __ldg(sp.row_w + r) * g.out_sw + __ldg(sp.row_s + r) * g.out_ss;
+    if constexpr (ACC) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) acc[i] += load_as<Acc, TO>(out + ob + ro + i);
+    }
     store_vec<TO, Acc, NV>(out + ob + ro, acc);
   }
 }
@@ -318,9 +323,10 @@ __device__ __forceinline__ void split3(A x, __nv_bfloat16& h, __nv_bfloat16& m,
 }
 
 // Same as sparse_rows_vec_kernel with the output split into three BF16 planes.
-template <typename TI, typename V>
+template <typename TI, typename V, bool PLANES, bool ADD>
 __global__ void __launch_bounds__(256)
 sparse_rows_split3_kernel(SparseRows<V> sp, SparseGeom g, const TI* __restrict__ in,
+                          long long in_plane, const float* __restrict__ add,
                           __nv_bfloat16* __restrict__ out, long long plane, int lpr,
                           int rows_per_cta) {
   using Acc = float;
@@ -347,10 +353,21 @@ sparse_rows_split3_kernel(SparseRows<V> sp, SparseGeom g, const TI* __restrict__
       const Acc w = (Acc)__ldg(sp.nz_val + e);
       Acc x[NV];
       load_vec<TI, Acc>(in + ib + ci, x);
+      if constexpr (PLANES) {
+        Acc x1[NV], x2[NV];
+        load_vec<TI, Acc>(in + ib + ci + in_plane, x1);
+        load_vec<TI, Acc>(in + ib + ci + 2 * in_plane, x2);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) x[i] += x1[i] + x2[i];
+      }
 #pragma unroll
       for (int i = 0; i < NV; ++i) acc[i] = fma(w, x[i], acc[i]);
     }
     const long long ro = __ldg(sp.row_w + r) * g.out_sw + __ldg(sp.row_s + r) * g.out_ss;
+    if constexpr (ADD) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) acc[i] += add[ob + ro + i];
+    }
     __nv_bfloat16* o = out + ob + ro;
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
@@ -366,6 +383,7 @@ sparse_rows_split3_kernel(SparseRows<V> sp, SparseGeom g, const TI* __restrict__
 // scalar fallback of the split3 stage (rows not 16-byte aligned)
 template <typename TI, typename V>
 __global__ void sparse_rows_split3_scalar(SparseRows<V> sp, SparseGeom g, const TI* __restrict__ in,
+                                          long long in_plane, const float* __restrict__ add,
                                           __nv_bfloat16* __restrict__ out, long long plane,
                                           int rows_per_cta) {
   const int r0 = blockIdx.x * rows_per_cta;
@@ -376,10 +394,14 @@ __global__ void sparse_rows_split3_scalar(SparseRows<V> sp, SparseGeom g, const 
   for (int it = threadIdx.x; it < nr * g.veclen; it += blockDim.x) {
     const int r = r0 + it / g.veclen, v = it % g.veclen;
     float acc = 0.f;
-    for (int e = sp.row_ptr[r]; e < sp.row_ptr[r + 1]; ++e)
-      acc += (float)sp.nz_val[e] * load_as<float, TI>(in + ib + sp.nz_w[e] * g.in_sw +
-                                                        sp.nz_t[e] * g.in_st + v);
+    for (int e = sp.row_ptr[r]; e < sp.row_ptr[r + 1]; ++e) {
+      const TI* p = in + ib + sp.nz_w[e] * g.in_sw + sp.nz_t[e] * g.in_st + v;
+      float x = load_as<float, TI>(p);
+      if (in_plane) x += load_as<float, TI>(p + in_plane) + load_as<float, TI>(p + 2 * in_plane);
+      acc += (float)sp.nz_val[e] * x;
+    }
     const long long o = ob + sp.row_w[r] * g.out_sw + sp.row_s[r] * g.out_ss + v;
+    if (add) acc += add[o];
     __nv_bfloat16 h, m, l;
     split3<float>(acc, h, m, l);
     out[o] = h;
@@ -390,16 +412,19 @@ __global__ void sparse_rows_split3_scalar(SparseRows<V> sp, SparseGeom g, const 
 
 template <typename TI, typename V>
 void sparse_rows_apply_split3(const SparseRows<V>& sp, const SparseGeom& g, const TI* in,
-                              __nv_bfloat16* out, long long plane, cudaStream_t s) {
+                              long long in_plane, const float* add, __nv_bfloat16* out,
+                              long long plane, cudaStream_t s) {
   if (sp.nrows == 0 || g.veclen == 0) return;
   constexpr int NV = Vec16<TI>::N;
+  if constexpr (sizeof(TI) != 2) A2_REQUIRE(in_plane == 0, "input planes need BF16 input");
   auto al = [](long long x) { return x % NV == 0; };
   if (!(al(g.veclen) && al(g.in_sw) && al(g.in_st) && al(g.in_b1) && al(g.in_b2) &&
-        reinterpret_cast<uintptr_t>(in) % 16 == 0)) {
+        al(in_plane) && reinterpret_cast<uintptr_t>(in) % 16 == 0)) {
     const int rows = std::min(64, std::max(1, 2048 / g.veclen));
     dim3 grid(cdiv(sp.nrows, rows), g.B1 * g.B2);
     A2_REQUIRE(grid.y < 65536, "sparse grid too large");
-    sparse_rows_split3_scalar<TI, V><<<grid, 256, 0, s>>>(sp, g, in, out, plane, rows);
+    sparse_rows_split3_scalar<TI, V><<<grid, 256, 0, s>>>(sp, g, in, in_plane, add, out, plane,
+                                                         rows);
     A2_CHECK_LAUNCH();
     return;
   }
@@ -407,12 +432,21 @@ void sparse_rows_apply_split3(const SparseRows<V>& sp, const SparseGeom& g, cons
   while (lpr < 32 && lpr * NV < g.veclen) lpr *= 2;
   dim3 grid(cdiv(sp.nrows, 64), cdiv(g.veclen, lpr * NV), g.B1 * g.B2);
   A2_REQUIRE(grid.y < 65536 && grid.z < 65536, "sparse grid too large");
-  sparse_rows_split3_kernel<TI, V><<<grid, 256, 0, s>>>(sp, g, in, out, plane, lpr, 64);
+  auto kern = in_plane ? (add ? sparse_rows_split3_kernel<TI, V, true, true>
+                               : sparse_rows_split3_kernel<TI, V, true, false>)
+                      : (add ? sparse_rows_split3_kernel<TI, V, false, true>
+                             : sparse_rows_split3_kernel<TI, V, false, false>);
+  kern<<<grid, 256, 0, s>>>(sp, g, in, in_plane, add, out, plane, lpr, 64);
   A2_CHECK_LAUNCH();
 }
 template void sparse_rows_apply_split3<float, float>(const SparseRows<float>&, const SparseGeom&,
-                                                     const float*, __nv_bfloat16*, long long,
-                                                     cudaStream_t);
+                                                     const float*, long long, const float*,
+                                                     __nv_bfloat16*, long long, cudaStream_t);
+template void sparse_rows_apply_split3<__nv_bfloat16, float>(const SparseRows<float>&,
+                                                             const SparseGeom&,
+                                                             const __nv_bfloat16*, long long,
+                                                             const float*, __nv_bfloat16*,
+                                                             long long, cudaStream_t);
 
 template <typename TI>
 __global__ void split3_ld_kernel(const TI* in, long long rows, long long cols,
@@ -495,7 +529,10 @@ void sparse_rows_apply(const SparseRows<V>& sp, const SparseGeom& g, const TI* i
     const int rows = 64;
     dim3 grid(cdiv(sp.nrows, rows), chunks, g.B1 * g.B2);
     A2_REQUIRE(grid.y < 65536 && grid.z < 65536, "sparse grid too large");
-    sparse_rows_vec_kernel<TI, TO, V><<<grid, 256, 0, s>>>(sp, g, in, out, lpr, rows);
+    if (g.accumulate)
+      sparse_rows_vec_kernel<TI, TO, V, true><<<grid, 256, 0, s>>>(sp, g, in, out, lpr, rows);
+    else
+      sparse_rows_vec_kernel<TI, TO, V, false><<<grid, 256, 0, s>>>(sp, g, in, out, lpr, rows);
     A2_CHECK_LAUNCH();
     return;
   }

@@ -44,6 +44,7 @@ struct SparseRows {
 
 struct SparseGeom {
   int veclen = 0;
+  int accumulate = 0;               // 1: out += result (read in the output's type)
   long long out_sw = 0, out_ss = 0, in_sw = 0, in_st = 0;
   int B1 = 1, B2 = 1;
   long long in_b1 = 0, in_b2 = 0, out_b1 = 0, out_b2 = 0;
@@ -54,10 +55,14 @@ void sparse_rows_apply(const SparseRows<V>& sp, const SparseGeom& g, const TI* i
                        cudaStream_t s);
 
 // Same action with the FP32 result written as three BF16 planes (hi, mid, lo) at
-// out, out + plane, out + 2*plane (rows of 16-byte aligned input required).
+// out, out + plane, out + 2*plane.  in_plane > 0 (BF16 input only): the input is itself
+// three planes in, in + in_plane, in + 2*in_plane and each value is their sum.  add
+// (optional, FP32, laid out like one output plane) is added to the result before the
+// split.  g.accumulate is ignored.
 template <typename TI, typename V>
 void sparse_rows_apply_split3(const SparseRows<V>& sp, const SparseGeom& g, const TI* in,
-                              __nv_bfloat16* out, long long plane, cudaStream_t s);
+                              long long in_plane, const float* add, __nv_bfloat16* out,
+                              long long plane, cudaStream_t s);
 // out planes [p][r*ld + c] = BF16 slice p of in[r*cols + c]  (x = hi + mid + lo)
 template <typename TI>
 void split3_ld(const TI* in, long long rows, long long cols, __nv_bfloat16* out, long long ld,

@@ -4,12 +4,12 @@
 //   D[m][n] = sum_k A[m][k] * B[n][k]      A: M x K, B: N x K, both K-major BF16,
 //   FP32 accumulation in tensor memory, epilogue stores BF16 or FP32 (plain or atomic).
 //
-// One CTA computes one 128 x BN output tile (optionally one K-split of it) with 128
-// threads: warp 0 lane 0 issues TMA loads into a STAGES-deep ring of 128B-swizzled
-// tiles, warp 1 lane 0 issues tcgen05.mma (M=128, N=BN, K=16 per instruction), and all
-// four warps drain the accumulator (warp w owns TMEM lanes 32w..32w+31).
-// Every mbarrier wait is bounded; a timeout raises a device error flag, the CTA skips
-// its stores, frees its TMEM and exits.
+// A persistent kernel (one CTA of 192 threads per SM) walks the 128 x BN output tiles
+// (and their K splits): warp 0 lane 0 issues TMA loads into a STAGES-deep ring of
+// 128B-swizzled tiles, warp 1 lane 0 issues tcgen05.mma (M=128, N=BN, K=16 per
+// instruction) into one of two TMEM accumulators, and warps 2..5 drain the other one.
+// Every mbarrier wait is bounded; a timeout raises a device error flag, every role
+// leaves its loop, the in-flight copies and MMAs are waited for, TMEM is freed.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -72,6 +72,24 @@ __device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* ba
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(const CUtensorMap* map, uint64_t* bar, void* dst,
+                                            int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(const CUtensorMap* map, uint64_t* bar, void* dst,
+                                            int x, int y, int z, int w) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
 __device__ __forceinline__ uint64_t smem_desc(const void* p) {
   const uint64_t addr = smem_u32(p);
@@ -131,7 +149,10 @@ enum OutKind { OUT_BF16 = 0, OUT_F32 = 1, OUT_F32_ATOMIC = 2 };
 
 struct TcArgs {
   int M, N, K;
-  int kblocks_per_split;   // K blocks (of BK) handled by one CTA
+  int nk1, nk2;            // K blocks of the plain product and of the optional second segment
+  int nbc2, n12;           // second segment: b' chunks per w1, (s1 s2) rows per a
+  int kblocks_per_split;   // K blocks (of BK) in one work unit
+  int splits;              // K splits (work units per output tile)
   void* C;
   long long ldc;
   int out_kind;
@@ -140,39 +161,73 @@ struct TcArgs {
 };
 
 // Up to three BF16 planes per operand (a value split into high, middle and low parts).
+// a2 / b2: the optional second K segment, A as a 4D view [a][w1][s12][b'] (box
+// 64 x n12 x 1 x 128/n12, i.e. 128 rows (a, s12) x 64 b') and B as a 3D view
+// [b][w1][b'] (box 64 x 1 x BN); both land in shared memory exactly like the 2D boxes.
 struct TcMaps {
   CUtensorMap a[3];
   CUtensorMap b[3];
+  CUtensorMap a2[3];
+  CUtensorMap b2[3];
 };
+
+constexpr int kEpiWarps = 4;                       // one per TMEM lane quarter
+constexpr int kThreads = 64 + 32 * kEpiWarps;      // producer warp, MMA warp, epilogue warps
 
 template <int BN, int STAGES>
 struct TcSmem {
   alignas(1024) __nv_bfloat16 a[STAGES][BM * BK];
   alignas(1024) __nv_bfloat16 b[STAGES][BN * BK];
-  alignas(8) uint64_t full[STAGES];
-  alignas(8) uint64_t empty[STAGES];
-  alignas(8) uint64_t done;
+  float stage[kEpiWarps][32 * 33];                 // epilogue transpose buffers
+  alignas(8) uint64_t full[STAGES];                // TMA -> MMA
+  alignas(8) uint64_t empty[STAGES];               // MMA -> TMA
+  alignas(8) uint64_t acc_full[2];                 // MMA -> epilogue (per TMEM buffer)
+  alignas(8) uint64_t acc_empty[2];                // epilogue -> MMA
+  alignas(8) uint64_t drain;                       // MMA completion on abort
   uint32_t tmem_base;
   int abort_flag;
 };
 
+static_assert(sizeof(TcSmem<256, 4>) + 1024 <= 227 * 1024, "BN=256 ring exceeds shared memory");
+static_assert(sizeof(TcSmem<128, 6>) + 1024 <= 227 * 1024, "BN=128 ring exceeds shared memory");
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait that also gives up early once another role has raised the abort flag.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, int code,
+                                                   const int* abort_flag) {
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255) == 255 && *(volatile const int*)abort_flag) return false;
+    if (it > 64) __nanosleep(64);
+  }
+  atomicExch(&g_tc_error, code);
+  return false;
+}
+
+// Persistent warp-specialised GEMM.  Work unit = (128 x BN output tile, K split); CTA c
+// takes units c, c + gridDim.x, ...  Warp 0 lane 0 streams (A, B) K blocks through a
+// STAGES-deep ring with TMA, warp 1 lane 0 issues tcgen05.mma into one of two TMEM
+// accumulators (2 x BN columns), warps 2..5 drain the other accumulator (warp w reads
+// TMEM lanes 32*(w%4)..+31) and store it, so the epilogue of one unit overlaps the MMAs
+// of the next.  Every wait is bounded; a timeout raises the device error flag and all
+// roles leave their loops, wait (bounded) for their copies / MMAs in flight and exit.
 template <int BN, int STAGES>
-__global__ void __launch_bounds__(128, 2)
+__global__ void __launch_bounds__(kThreads, 1)
 tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // round the dynamic shared memory base up to 1024 bytes (swizzle atoms)
   const uint32_t base = smem_u32(smem_raw);
   const uint32_t pad = (1024u - (base & 1023u)) & 1023u;
   auto& S = *reinterpret_cast<TcSmem<BN, STAGES>*>(smem_raw + pad);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * BM;
-  const int n0 = blockIdx.y * BN;
-  const int nk_total = (args.K + BK - 1) / BK;
-  const int kb0 = blockIdx.z * args.kblocks_per_split;
-  const int nkb = max(0, min(nk_total - kb0, args.kblocks_per_split));
+  const int tiles_m = (args.M + BM - 1) / BM;
+  const int tiles_n = (args.N + BN - 1) / BN;
+  const int nk_total = args.nk1 + args.nk2;
+  const int nunits = tiles_m * tiles_n * args.splits;
   const int np = args.npairs;
-  const int nk = nkb * np;          // pipeline steps: (K block, operand pair)
   constexpr uint32_t kStageBytes = (BM + BN) * BK * 2;
 
   if (threadIdx.x == 0) {
@@ -180,15 +235,18 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
       mbar_init(&S.full[s], 1);
       mbar_init(&S.empty[s], 1);
     }
-    mbar_init(&S.done, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&S.acc_full[i], 1);
+      mbar_init(&S.acc_empty[i], kEpiWarps);
+    }
+    mbar_init(&S.drain, 1);
     S.abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  __syncwarp();
-  if (warp == 0) {   // TMEM accumulator: BN fp32 columns x 128 lanes
+  if (warp == 0) {   // two accumulators of BN fp32 columns x 128 lanes
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&S.tmem_base)),
-                 "r"((uint32_t)BN));
+                 "r"((uint32_t)(2 * BN)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -196,68 +254,116 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = S.tmem_base;
 
-  if (nk > 0) {
-    if (warp == 0 && lane == 0) {
-      // ---------------- producer: TMA loads into the stage ring
-      int issued = 0;
-      for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % STAGES;
-        const int round = kb / STAGES;
-        if (round > 0 && !mbar_wait(&S.empty[s], (round - 1) & 1, 1)) {
-          S.abort_flag = 1;
-          break;
+  auto unit_k = [&](int u, int& kb0, int& nkb) {
+    const int sp = u / (tiles_m * tiles_n);
+    kb0 = sp * args.kblocks_per_split;
+    nkb = max(0, min(nk_total - kb0, args.kblocks_per_split));
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- producer
+      uint32_t g = 0, issued = 0;
+      for (int u = blockIdx.x; u < nunits && !*(volatile int*)&S.abort_flag; u += gridDim.x) {
+        const int m0 = (u % tiles_m) * BM;
+        const int n0 = ((u / tiles_m) % tiles_n) * BN;
+        int kb0, nkb;
+        unit_k(u, kb0, nkb);
+        const int steps = nkb * np;
+        for (int kb = 0; kb < steps; ++kb, ++g) {
+          const int s = g % STAGES;
+          const uint32_t round = g / STAGES;
+          if (round > 0 &&
+              !mbar_wait_or_abort(&S.empty[s], (round - 1) & 1, 1, &S.abort_flag)) {
+            S.abort_flag = 1;
+            break;
+          }
+          if (*(volatile int*)&S.abort_flag) break;
+          mbar_expect_tx(&S.full[s], kStageBytes);
+          const int p = kb % np;
+          const int kbg = kb0 + kb / np;
+          if (kbg < args.nk1) {
+            const int kx = kbg * BK;
+            tma_load_2d(&maps.a[args.pa[p]], &S.full[s], S.a[s], kx, m0);
+            tma_load_2d(&maps.b[args.pb[p]], &S.full[s], S.b[s], kx, n0);
+          } else {   // second segment: K block = (w1, chunk of b')
+            const int j = kbg - args.nk1;
+            const int w1 = j / args.nbc2, bx = (j % args.nbc2) * BK;
+            tma_load_4d(&maps.a2[args.pa[p]], &S.full[s], S.a[s], bx, 0, w1, m0 / args.n12);
+            tma_load_3d(&maps.b2[args.pb[p]], &S.full[s], S.b[s], bx, w1, n0);
+          }
+          issued = g + 1;
         }
-        if (*(volatile int*)&S.abort_flag) break;
-        mbar_expect_tx(&S.full[s], kStageBytes);
-        const int p = kb % np;
-        const int kx = (kb0 + kb / np) * BK;
-        tma_load_2d(&maps.a[args.pa[p]], &S.full[s], S.a[s], kx, m0);
-        tma_load_2d(&maps.b[args.pb[p]], &S.full[s], S.b[s], kx, n0);
-        issued = kb + 1;
       }
-      // on abort: wait (bounded) for the copies already issued before leaving
+      // on abort: wait (bounded) for the copies still in flight before leaving
       if (*(volatile int*)&S.abort_flag) {
-        for (int kb = max(0, issued - STAGES); kb < issued; ++kb)
-          mbar_wait(&S.full[kb % STAGES], (kb / STAGES) & 1, 2);
+        for (uint32_t j = issued > (uint32_t)STAGES ? issued - STAGES : 0; j < issued; ++j)
+          mbar_wait(&S.full[j % STAGES], (j / STAGES) & 1, 2);
       }
-    } else if (warp == 1 && lane == 0) {
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
       // ---------------- MMA issuer
       constexpr uint32_t idesc = idesc_bf16(BM, BN);
-      bool ok = true;
-      for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % STAGES;
-        if (!mbar_wait(&S.full[s], (kb / STAGES) & 1, 3)) {
+      uint32_t g = 0, lu = 0;
+      bool issued_any = false;
+      for (int u = blockIdx.x; u < nunits && !*(volatile int*)&S.abort_flag;
+           u += gridDim.x, ++lu) {
+        const uint32_t buf = lu & 1, use = lu >> 1;
+        if (use > 0 &&
+            !mbar_wait_or_abort(&S.acc_empty[buf], (use - 1) & 1, 5, &S.abort_flag)) {
           S.abort_flag = 1;
-          ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint64_t da = smem_desc(S.a[s]);
-        const uint64_t db = smem_desc(S.b[s]);
+        const uint32_t d = tmem + buf * BN;
+        int kb0, nkb;
+        unit_k(u, kb0, nkb);
+        const int steps = nkb * np;
+        bool ok = true;
+        for (int kb = 0; kb < steps; ++kb, ++g) {
+          const int s = g % STAGES;
+          if (!mbar_wait_or_abort(&S.full[s], (g / STAGES) & 1, 3, &S.abort_flag)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t da = smem_desc(S.a[s]);
+          const uint64_t db = smem_desc(S.b[s]);
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          // advance 16 bf16 = 32 bytes (2 in 16-byte units) inside the swizzle atom
-          mma_bf16(tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
-                   (kb > 0 || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < BK / 16; ++kk)
+            mma_bf16(d, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+                     (kb > 0 || kk > 0) ? 1u : 0u);
+          issued_any = true;
+          mma_commit(&S.empty[s]);   // frees the stage once these MMAs have read it
         }
-        mma_commit(&S.empty[s]);   // frees the stage once these MMAs have read it
+        if (!ok) {
+          S.abort_flag = 1;
+          break;
+        }
+        mma_commit(&S.acc_full[buf]);
       }
-      if (ok) mma_commit(&S.done);
-      else S.abort_flag = 1;
+      if (*(volatile int*)&S.abort_flag && issued_any) {
+        mma_commit(&S.drain);      // wait (bounded) for the MMAs still in flight
+        mbar_wait(&S.drain, 0, 6);
+      }
     }
-    __syncwarp();
-    // ---------------- epilogue: all four warps
-    bool ready = mbar_wait(&S.done, 0, 4);
-    if (!ready) S.abort_flag = 1;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (!*(volatile int*)&S.abort_flag) {
-      // The operand ring is idle once `done` has fired: each warp stages its 32 x 32
-      // accumulator chunk there (row = lane), then writes whole row segments so that
-      // consecutive lanes store consecutive columns.
-      float* stage = reinterpret_cast<float*>(&S.a[0][0]) + warp * (32 * 33);
-      const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-      const int row0 = m0 + warp * 32;
+  } else {
+    // ---------------- epilogue warps
+    const int q = warp & 3;                          // TMEM lane quarter of this warp
+    float* stage = S.stage[warp - 2];
+    uint32_t lu = 0;
+    for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++lu) {
+      const uint32_t buf = lu & 1, use = lu >> 1;
+      if (!mbar_wait_or_abort(&S.acc_full[buf], use & 1, 4, &S.abort_flag)) {
+        S.abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int m0 = (u % tiles_m) * BM;
+      const int n0 = ((u / tiles_m) % tiles_n) * BN;
+      const uint32_t tl = tmem + buf * BN + ((uint32_t)(q * 32) << 16);
+      const int row0 = m0 + q * 32;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         if (n0 + c0 >= args.N) break;
@@ -284,13 +390,16 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
         }
         __syncwarp();
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.acc_empty[buf]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"((uint32_t)BN));
+                 "r"((uint32_t)(2 * BN)));
   }
 }
 
@@ -327,10 +436,28 @@ CUtensorMap make_map(const __nv_bfloat16* ptr, int rows, int K, long long ld, in
   return m;
 }
 
+// Tiled BF16 map of rank 3 or 4 (dims innermost first, strides in bytes for dims 1..),
+// 128B swizzle, zero fill outside the extents.
+CUtensorMap make_map_nd(const __nv_bfloat16* ptr, int rank, const cuuint64_t* dims,
+                        const cuuint64_t* strides, const cuuint32_t* box) {
+  A2_REQUIRE((reinterpret_cast<uintptr_t>(ptr) & 15) == 0, "TMA base must be 16-byte aligned");
+  for (int i = 0; i < rank - 1; ++i)
+    A2_REQUIRE(strides[i] % 16 == 0, "TMA strides must be multiples of 16 bytes");
+  CUtensorMap m;
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, (void*)ptr, dims, strides,
+                           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw CudaError("cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return m;
+}
+
 template <int BN, int STAGES>
 void launch(const __nv_bfloat16* const* A, long long lda, const __nv_bfloat16* const* B,
             long long ldb, int M, int N, int K, int npairs, const int* pa, const int* pb,
-            void* C, long long ldc, int out_kind, int splitk, cudaStream_t s) {
+            const TcSeg2* seg, void* C, long long ldc, int out_kind, int splitk,
+            cudaStream_t s) {
   TcMaps maps;
   int na = 0, nb = 0;
   for (int p = 0; p < npairs; ++p) {
@@ -341,16 +468,52 @@ void launch(const __nv_bfloat16* const* A, long long lda, const __nv_bfloat16* c
     maps.a[i] = make_map(A[i < na ? i : 0], M, K, lda, BM);
     maps.b[i] = make_map(B[i < nb ? i : 0], N, K, ldb, BN);
   }
+  int nk2 = 0, nbc2 = 1, n12 = 1;
+  if (seg) {
+    const long long Dr = seg->Dr, R1 = seg->R1;
+    n12 = seg->n12;
+    A2_REQUIRE(n12 >= 1 && BM % n12 == 0 && (long long)M == (long long)seg->Dl * n12,
+               "tc GEMM segment: rows must be (a, s12) with s12 dividing 128");
+    A2_REQUIRE(Dr % 8 == 0 && seg->Nb == N, "tc GEMM segment: Dr % 8 == 0, N == Dr");
+    nbc2 = (int)((Dr + BK - 1) / BK);
+    nk2 = (int)(R1 * nbc2);
+    for (int i = 0; i < 3; ++i) {
+      const cuuint64_t ad[4] = {(cuuint64_t)Dr, (cuuint64_t)n12, (cuuint64_t)R1,
+                                (cuuint64_t)seg->Dl};
+      const cuuint64_t as[3] = {(cuuint64_t)(Dr * 2), (cuuint64_t)(n12 * Dr * 2),
+                                (cuuint64_t)(R1 * n12 * Dr * 2)};
+      const cuuint32_t ab[4] = {(cuuint32_t)BK, (cuuint32_t)n12, 1u, (cuuint32_t)(BM / n12)};
+      maps.a2[i] = make_map_nd(seg->A[i < na ? i : 0], 4, ad, as, ab);
+      const cuuint64_t bd[3] = {(cuuint64_t)Dr, (cuuint64_t)R1, (cuuint64_t)N};
+      const cuuint64_t bs[2] = {(cuuint64_t)(Dr * 2), (cuuint64_t)(R1 * Dr * 2)};
+      const cuuint32_t bb[3] = {(cuuint32_t)BK, 1u, (cuuint32_t)BN};
+      maps.b2[i] = make_map_nd(seg->B[i < nb ? i : 0], 3, bd, bs, bb);
+    }
+  } else {
+    for (int i = 0; i < 3; ++i) {
+      maps.a2[i] = maps.a[i];
+      maps.b2[i] = maps.b[i];
+    }
+  }
   const size_t smem = sizeof(TcSmem<BN, STAGES>) + 1024;
   static std::once_flag once;
   std::call_once(once, [smem] {
     A2_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   });
-  const int nk_total = (K + BK - 1) / BK;
+  static int num_sms = 0;
+  static std::once_flag sms_once;
+  std::call_once(sms_once, [] {
+    int dev = 0;
+    A2_CUDA(cudaGetDevice(&dev));
+    A2_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+  });
+  const int nk1 = (K + BK - 1) / BK;
+  const int nk_total = nk1 + nk2;
   splitk = std::max(1, std::min(splitk, nk_total));
   TcArgs args;
   args.M = M; args.N = N; args.K = K;
+  args.nk1 = nk1; args.nk2 = nk2; args.nbc2 = nbc2; args.n12 = n12;
   args.kblocks_per_split = (nk_total + splitk - 1) / splitk;
   splitk = (nk_total + args.kblocks_per_split - 1) / args.kblocks_per_split;
   args.C = C; args.ldc = ldc; args.out_kind = out_kind;
@@ -359,9 +522,11 @@ void launch(const __nv_bfloat16* const* A, long long lda, const __nv_bfloat16* c
     args.pa[p] = p < npairs ? pa[p] : 0;
     args.pb[p] = p < npairs ? pb[p] : 0;
   }
-  dim3 grid(cdiv(M, BM), cdiv(N, BN), splitk);
-  A2_REQUIRE(grid.y < 65536 && grid.z < 65536, "tcgen05 grid too large");
-  tc_gemm_kernel<BN, STAGES><<<grid, 128, smem, s>>>(maps, args);
+  args.splits = splitk;
+  const long long units = (long long)cdiv(M, BM) * cdiv(N, BN) * splitk;
+  A2_REQUIRE(units < (1LL << 31), "tcgen05 GEMM too large");
+  const int grid = (int)std::min<long long>(units, std::max(1, num_sms));
+  tc_gemm_kernel<BN, STAGES><<<grid, kThreads, smem, s>>>(maps, args);
   A2_CHECK_LAUNCH();
 }
 
@@ -391,22 +556,34 @@ void tc_gemm_bf16(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B,
 void tc_gemm_bf16_pairs(const __nv_bfloat16* const* A, long long lda,
                         const __nv_bfloat16* const* B, long long ldb, int M, int N, int K,
                         int npairs, const int* pa, const int* pb, void* C, long long ldc,
-                        int out_kind, int splitk, cudaStream_t s) {
+                        int out_kind, int splitk, cudaStream_t s, const TcSeg2* seg) {
   if (M <= 0 || N <= 0) return;
   A2_REQUIRE(K >= 1 && npairs >= 1 && npairs <= 6, "tc GEMM: K >= 1, 1..6 operand pairs");
   if (splitk > 1)
     A2_REQUIRE(out_kind == tc::OUT_F32_ATOMIC, "split-K needs atomic FP32 output");
   if (N <= 128)
-    tc::launch<128, 3>(A, lda, B, ldb, M, N, K, npairs, pa, pb, C, ldc, out_kind, splitk, s);
+    tc::launch<128, 6>(A, lda, B, ldb, M, N, K, npairs, pa, pb, seg, C, ldc, out_kind, splitk,
+                       s);
   else
-    tc::launch<256, 2>(A, lda, B, ldb, M, N, K, npairs, pa, pb, C, ldc, out_kind, splitk, s);
+    tc::launch<256, 4>(A, lda, B, ldb, M, N, K, npairs, pa, pb, seg, C, ldc, out_kind, splitk,
+                       s);
 }
 
 // -------------------------------------------------------------- BF16 H_eff chain
+namespace {
+int s4_splitk(long long M4, int Dr, long long kblocks) {
+  const long long tiles = (long long)cdiv(M4, 128) * cdiv(Dr, Dr <= 128 ? 128 : 256);
+  int splitk = (int)std::max<long long>(1, 2 * 152 / std::max<long long>(1, tiles));
+  return std::min<int>(splitk, std::max<int>(1, (int)(kblocks / 8)));
+}
+}  // namespace
+
 void tc_heff_bf16(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int Dl, int Dr,
                   const __nv_bfloat16* Lb, long long ldl, const __nv_bfloat16* Rb, long long ldr,
                   const double* x, float* y, const SparseRows<float>& W1,
-                  const SparseRows<float>& W2, DevBuf& t1, DevBuf& t2, DevBuf& xa) {
+                  const SparseRows<float>& W2, const HeffFold& F, DevBuf& t1, DevBuf& t2,
+                  DevBuf& xa, DevBuf& tf) {
+  (void)tf;
   const long long NX = (long long)n1 * n2 * Dr;          // columns of S1
   const long long ldx = pad8(Dl);
   const long long s1 = (long long)Dl * Rl * NX;
@@ -430,14 +607,20 @@ void tc_heff_bf16(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int Dl
     ProfScope ps(PK_TC_S1, s, 2.0 * M * N * K, 2.0 * (M * K + N * K + M * N));
     tc_gemm_bf16(Lb, ldl, XT, ldx, Dl * Rl, (int)NX, Dl, T1, NX, tc::OUT_BF16, 1, s);
   }
-  {  // S2
+  if (F.Lt) {   // folded G of A_k: T2[(a w1)][(s1 t2 b')] = sum_a' Lt[(a w1)][a'] XT
+    const double M = (double)Dl * R1, N = (double)NX, K = Dl;
+    ProfScope ps(PK_TC_S1, s, 2.0 * M * N * K, 2.0 * (M * K + N * K + M * N));
+    tc_gemm_bf16(F.Lt, ldl, XT, ldx, Dl * R1, (int)NX, Dl, T2, NX, tc::OUT_BF16, 1, s);
+  }
+  {  // S2 (W_rest added to the folded part when A_k is folded)
     ProfScope ps(PK_SPARSE_S2, s, 2.0 * W1.nnz_total * (double)n2 * Dr * Dl,
-                 2.0 * (double)(s1 + s2));
+                 2.0 * (double)(s1 + s2) * (F.Lt ? 1.5 : 1.0));
     SparseGeom gm;
     gm.veclen = n2 * Dr;
     gm.in_sw = NX; gm.in_st = (long long)n2 * Dr;
     gm.out_sw = NX; gm.out_ss = (long long)n2 * Dr;
     gm.B1 = Dl; gm.in_b1 = (long long)Rl * NX; gm.out_b1 = (long long)R1 * NX;
+    gm.accumulate = F.Lt ? 1 : 0;
     sparse_rows_apply<__nv_bfloat16, __nv_bfloat16, float>(W1, gm, T1, T2, s);
   }
   {  // S3 -> T3[(a s1 s2)][(w2 b')] with row stride ld3
@@ -453,15 +636,25 @@ void tc_heff_bf16(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int Dl
     sparse_rows_apply<__nv_bfloat16, __nv_bfloat16, float>(W2, gm, T2, T3, s);
   }
   // S4: y[(a s1 s2)][b] = sum_{(w2 b')} T3 HR[b][(w2 b')]   (split K, atomic FP32)
+  //     (+ sum_{(w1 b')} T2[a][w1][(s1 s2)][b'] Rt[b][w1][b'] when A_{k+1} is folded)
   const int M4 = Dl * n1 * n2;
-  const long long tiles = (long long)cdiv(M4, 128) * cdiv(Dr, Dr <= 128 ? 128 : 256);
-  int splitk = (int)std::max<long long>(1, 2 * 152 / std::max<long long>(1, tiles));
-  splitk = std::min<int>(splitk, std::max<int>(1, (int)(K4 / (8 * 64))));
+  TcSeg2 seg;
+  long long kb = (K4 + 63) / 64;
+  if (F.Rt) {
+    seg.A[0] = seg.A[1] = seg.A[2] = T2;
+    seg.B[0] = seg.B[1] = seg.B[2] = F.Rt;
+    seg.Dl = Dl; seg.n12 = n1 * n2; seg.R1 = R1; seg.Dr = Dr; seg.Nb = Dr;
+    kb += (long long)R1 * ((Dr + 63) / 64);
+  }
   {
-    const double M = M4, N = Dr, K = (double)K4;
+    const double M = M4, N = Dr, K = (double)K4 + (F.Rt ? (double)R1 * Dr : 0.0);
     ProfScope ps(PK_TC_S4, s, 2.0 * M * N * K, 2.0 * (M * K + N * K) + 4.0 * M * N);
     fill_zero(y, sizeof(float) * (size_t)M4 * Dr, s);
-    tc_gemm_bf16(T3, ld3, Rb, ldr, M4, Dr, (int)K4, y, Dr, tc::OUT_F32_ATOMIC, splitk, s);
+    const __nv_bfloat16* A[3] = {T3, T3, T3};
+    const __nv_bfloat16* B[3] = {Rb, Rb, Rb};
+    const int p0[1] = {0};
+    tc_gemm_bf16_pairs(A, ld3, B, ldr, M4, Dr, (int)K4, 1, p0, p0, y, Dr, tc::OUT_F32_ATOMIC,
+                       s4_splitk(M4, Dr, kb), s, F.Rt ? &seg : nullptr);
   }
 }
 
@@ -472,12 +665,13 @@ namespace a2 {
 // y = H_eff x with FP32-accurate tensor-core products: every BF16 GEMM operand is the
 // three-plane split of an FP32/FP64 value and six plane pairs are accumulated in TMEM;
 // the sparse MPO stages run in FP32.  L, R: three BF16 planes each (plane strides
-// lplane / rplane elements, row strides ldl / ldr).
+// lplane / rplane elements, row strides ldl / ldr).  When A_{k+1} is folded, T2 is kept
+// as three BF16 planes (the second K segment of S4 reads it through TMA).
 void tc_heff_f32emu(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int Dl, int Dr,
                     const __nv_bfloat16* Lp, long long ldl, long long lplane,
                     const __nv_bfloat16* Rp, long long ldr, long long rplane, const double* x,
                     float* y, const SparseRows<float>& W1, const SparseRows<float>& W2,
-                    DevBuf& t1, DevBuf& t2, DevBuf& xa) {
+                    const HeffFold& F, DevBuf& t1, DevBuf& t2, DevBuf& xa, DevBuf& tf) {
   static const int pa[6] = {0, 0, 1, 0, 1, 2};
   static const int pb[6] = {0, 1, 0, 2, 1, 0};
   const long long NX = (long long)n1 * n2 * Dr;
@@ -485,17 +679,26 @@ void tc_heff_f32emu(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int 
   const long long xplane = NX * ldx;
   const long long s1 = (long long)Dl * Rl * NX;
   const long long s2 = (long long)Dl * R1 * NX;
+  const long long p2 = (s2 + 63) / 64 * 64;          // T2 plane stride (split form)
   const long long K4 = (long long)Rr * Dr;
   const long long ld3 = pad8(K4);
   const long long M4 = (long long)Dl * n1 * n2;
   const long long plane3 = M4 * ld3;
+  const bool t2split = F.Rt != nullptr;
   xa.ensure(sizeof(__nv_bfloat16) * (size_t)(3 * xplane), s);
   t1.ensure(std::max(sizeof(float) * (size_t)s1, sizeof(__nv_bfloat16) * (size_t)(3 * plane3)), s);
-  t2.ensure(sizeof(float) * (size_t)s2, s);
+  t2.ensure(t2split ? sizeof(__nv_bfloat16) * (size_t)(3 * p2) : sizeof(float) * (size_t)s2, s);
   __nv_bfloat16* XT = xa.as<__nv_bfloat16>();
   float* T1 = t1.as<float>();
   float* T2 = t2.as<float>();
+  __nv_bfloat16* T2p = t2.as<__nv_bfloat16>();
   __nv_bfloat16* T3 = t1.as<__nv_bfloat16>();
+  // with both cores folded the S1-fold product needs its own FP32 buffer
+  float* Tg = nullptr;
+  if (F.Lt && t2split) {
+    tf.ensure(sizeof(float) * (size_t)s2, s);
+    Tg = tf.as<float>();
+  }
   transpose_split3(x, Dl, (int)NX, XT, ldx, xplane, s);
   {  // S1
     const __nv_bfloat16* A[3] = {Lp, Lp + lplane, Lp + 2 * lplane};
@@ -504,19 +707,32 @@ void tc_heff_f32emu(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int 
     ProfScope ps(PK_EMU_S1, s, 6.0 * 2.0 * M * N * K, 6.0 * (M * K + N * K) + 4.0 * M * N);
     tc_gemm_bf16_pairs(A, ldl, B, ldx, Dl * Rl, (int)NX, Dl, 6, pa, pb, T1, NX, tc::OUT_F32, 1, s);
   }
-  {  // S2 (FP32)
+  if (F.Lt) {   // folded G of A_k: Lt x, FP32 (into T2, or into Tg when T2 is split)
+    const __nv_bfloat16* A[3] = {F.Lt, F.Lt + F.ltplane, F.Lt + 2 * F.ltplane};
+    const __nv_bfloat16* B[3] = {XT, XT + xplane, XT + 2 * xplane};
+    const double M = (double)Dl * R1, N = (double)NX, K = Dl;
+    ProfScope ps(PK_EMU_S1, s, 6.0 * 2.0 * M * N * K, 6.0 * (M * K + N * K) + 4.0 * M * N);
+    tc_gemm_bf16_pairs(A, ldl, B, ldx, Dl * R1, (int)NX, Dl, 6, pa, pb, Tg ? Tg : T2, NX,
+                       tc::OUT_F32, 1, s);
+  }
+  {  // S2 (FP32; W_rest added to the folded part when A_k is folded)
     ProfScope ps(PK_EMU_S2, s, 2.0 * W1.nnz_total * (double)n2 * Dr * Dl,
-                 4.0 * (double)(s1 + s2));
+                 4.0 * (double)(s1 + s2) * (F.Lt ? 1.5 : 1.0));
     SparseGeom gm;
     gm.veclen = n2 * Dr;
     gm.in_sw = NX; gm.in_st = (long long)n2 * Dr;
     gm.out_sw = NX; gm.out_ss = (long long)n2 * Dr;
     gm.B1 = Dl; gm.in_b1 = (long long)Rl * NX; gm.out_b1 = (long long)R1 * NX;
-    sparse_rows_apply<float, float, float>(W1, gm, T1, T2, s);
+    if (t2split) {
+      sparse_rows_apply_split3<float, float>(W1, gm, T1, 0, Tg, T2p, p2, s);
+    } else {
+      gm.accumulate = F.Lt ? 1 : 0;
+      sparse_rows_apply<float, float, float>(W1, gm, T1, T2, s);
+    }
   }
-  {  // S3 (FP32 in, three BF16 planes out)
+  {  // S3 (FP32 or split input, three BF16 planes out)
     ProfScope ps(PK_EMU_S3, s, 2.0 * W2.nnz_total * (double)Dr * Dl * n1,
-                 4.0 * (double)s2 + 6.0 * (double)M4 * K4);
+                 (t2split ? 6.0 : 4.0) * (double)s2 + 6.0 * (double)M4 * K4);
     SparseGeom gm;
     gm.veclen = Dr;
     gm.in_sw = NX; gm.in_st = Dr;
@@ -524,19 +740,29 @@ void tc_heff_f32emu(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int 
     gm.B1 = Dl; gm.B2 = n1;
     gm.in_b1 = (long long)R1 * NX; gm.in_b2 = (long long)n2 * Dr;
     gm.out_b1 = (long long)n1 * n2 * ld3; gm.out_b2 = (long long)n2 * ld3;
-    sparse_rows_apply_split3<float, float>(W2, gm, T2, T3, plane3, s);
+    if (t2split)
+      sparse_rows_apply_split3<__nv_bfloat16, float>(W2, gm, T2p, p2, nullptr, T3, plane3, s);
+    else
+      sparse_rows_apply_split3<float, float>(W2, gm, T2, 0, nullptr, T3, plane3, s);
   }
-  {  // S4
+  {  // S4 (+ the folded G of A_{k+1} as a second K segment over T2)
     const __nv_bfloat16* A[3] = {T3, T3 + plane3, T3 + 2 * plane3};
     const __nv_bfloat16* B[3] = {Rp, Rp + rplane, Rp + 2 * rplane};
-    const long long tiles = (long long)cdiv(M4, 128) * cdiv(Dr, Dr <= 128 ? 128 : 256);
-    int splitk = (int)std::max<long long>(1, 2 * 152 / std::max<long long>(1, tiles));
-    splitk = std::min<int>(splitk, std::max<int>(1, (int)(K4 / (8 * 64))));
-    const double M = (double)M4, N = Dr, K = (double)K4;
+    TcSeg2 seg;
+    long long kb = (K4 + 63) / 64;
+    if (t2split) {
+      for (int i = 0; i < 3; ++i) {
+        seg.A[i] = T2p + i * p2;
+        seg.B[i] = F.Rt + i * F.rtplane;
+      }
+      seg.Dl = Dl; seg.n12 = n1 * n2; seg.R1 = R1; seg.Dr = Dr; seg.Nb = Dr;
+      kb += (long long)R1 * ((Dr + 63) / 64);
+    }
+    const double M = (double)M4, N = Dr, K = (double)K4 + (t2split ? (double)R1 * Dr : 0.0);
     ProfScope ps(PK_EMU_S4, s, 6.0 * 2.0 * M * N * K, 6.0 * (M * K + N * K) + 4.0 * M * N);
     fill_zero(y, sizeof(float) * (size_t)M4 * Dr, s);
     tc_gemm_bf16_pairs(A, ld3, B, ldr, (int)M4, Dr, (int)K4, 6, pa, pb, y, Dr,
-                       tc::OUT_F32_ATOMIC, splitk, s);
+                       tc::OUT_F32_ATOMIC, s4_splitk(M4, Dr, kb), s, t2split ? &seg : nullptr);
   }
 }
 

@@ -18,13 +18,34 @@ void tc_gemm_bf16(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B,
                   int M, int N, int K, void* C, long long ldc, int out_kind, int splitk,
                   cudaStream_t s);
 
+// Optional second K segment of a GEMM with M = Dl*n12 rows (a, s12) and N = Nb columns b:
+//   C[(a s12)][b] += sum_{w1, b'} A2[a][w1][s12][b'] * B2[b][w1][b'],
+// A2 dense [Dl][R1][n12][Dr], B2 dense [Nb][R1][Dr] (BF16 planes; Dr % 8 == 0,
+// 128 % n12 == 0, 16-byte aligned bases).  It folds an identity-on-physical MPO block
+// into the right environment (B2) of the last stage of H_eff.
+struct TcSeg2 {
+  const __nv_bfloat16* A[3] = {nullptr, nullptr, nullptr};
+  const __nv_bfloat16* B[3] = {nullptr, nullptr, nullptr};
+  int Dl = 0, n12 = 0, R1 = 0, Dr = 0, Nb = 0;
+};
+
 // Same GEMM accumulating npairs operand pairs (A[pa[p]], B[pb[p]]) into one FP32 tile:
 // with A = A0 + A1 + A2 and B = B0 + B1 + B2 split into BF16 planes, the six pairs
-// (0,0) (0,1) (1,0) (0,2) (1,1) (2,0) reproduce the FP32 product to ~2^-24.
+// (0,0) (0,1) (1,0) (0,2) (1,1) (2,0) reproduce the FP32 product to ~2^-24.  With seg,
+// the second K segment is accumulated into the same tile with the same pairs.
 void tc_gemm_bf16_pairs(const __nv_bfloat16* const* A, long long lda,
                         const __nv_bfloat16* const* B, long long ldb, int M, int N, int K,
                         int npairs, const int* pa, const int* pb, void* C, long long ldc,
-                        int out_kind, int splitk, cudaStream_t s);
+                        int out_kind, int splitk, cudaStream_t s, const TcSeg2* seg = nullptr);
+
+// Identity-on-physical MPO blocks folded into the environments (W = I (x) G + W_rest):
+// Lt [(a w1)][a'] (row stride = that of L) when A_k is folded, Rt [b][w1][b'] (dense)
+// when A_{k+1} is folded; BF16 planes as for L / R.  The sparse stages then get W_rest.
+struct HeffFold {
+  const __nv_bfloat16* Lt = nullptr;
+  const __nv_bfloat16* Rt = nullptr;
+  long long ltplane = 0, rtplane = 0;
+};
 
 // y = H_eff x: BF16 environments Lb [(a w)][a'] (row stride ldl) and Rb [b][(w2 b')]
 // (row stride ldr), FP64 x in, FP32 y out; intermediates T1..T3 in BF16 with FP32
@@ -32,7 +53,8 @@ void tc_gemm_bf16_pairs(const __nv_bfloat16* const* A, long long lda,
 void tc_heff_bf16(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int Dl, int Dr,
                   const __nv_bfloat16* Lb, long long ldl, const __nv_bfloat16* Rb, long long ldr,
                   const double* x, float* y, const SparseRows<float>& W1,
-                  const SparseRows<float>& W2, DevBuf& t1, DevBuf& t2, DevBuf& xa);
+                  const SparseRows<float>& W2, const HeffFold& F, DevBuf& t1, DevBuf& t2,
+                  DevBuf& xa, DevBuf& tf);
 
 // y = H_eff x with FP32-accurate tensor-core products (three BF16 planes per operand,
 // six plane pairs per GEMM); L / R given as three BF16 planes each.
@@ -40,7 +62,7 @@ void tc_heff_f32emu(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int 
                     const __nv_bfloat16* Lp, long long ldl, long long lplane,
                     const __nv_bfloat16* Rp, long long ldr, long long rplane, const double* x,
                     float* y, const SparseRows<float>& W1, const SparseRows<float>& W2,
-                    DevBuf& t1, DevBuf& t2, DevBuf& xa);
+                    const HeffFold& F, DevBuf& t1, DevBuf& t2, DevBuf& xa, DevBuf& tf);
 
 inline long long pad8(long long x) { return (x + 7) / 8 * 8; }
 

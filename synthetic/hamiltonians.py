@@ -19,6 +19,7 @@ Two families are built here:
   remaining operators (weighted), so that sums over the far indices collapse
   onto shared states (complementary operators).  No truncation is applied.
 """
+import bisect
 import functools
 import itertools
 
@@ -164,8 +165,9 @@ def _place_term(coef, ops, L, split_site, table):
         if r is None:
             return
         key, sg, m = r
-        table.setdefault(key, m)
-        local[k] = key
+        if key not in table:          # local operators are interned as small ints
+            table[key] = (len(table), m)
+        local[k] = table[key][0]
         sign *= sg
         nops[k] = sum(1 for p, _ in ops if p // 2 == k)
     # split site tau: at every cut left of tau the prefix holds at most two
@@ -221,10 +223,11 @@ def chemistry_mpo(h, eri, split_site=None, tol=0.0):
             r = _place_term(0.5 * v, ops, L, split_site, table)
             if r is not None:
                 placed.append(r)
-    return _assemble(placed, L, table, 4)
+    mats = [m for _, m in sorted(table.values(), key=lambda t: t[0])]
+    return _assemble(placed, L, mats, 4)
 
 
-def _assemble(placed, L, table, n):
+def _assemble(placed, L, mats, n):
     """Build MPO cores from placed terms (sites, local keys, nops, coef, tau)."""
     # state identity at cut c (between site c-1 and site c):
     #   ('I',)  nothing placed; ('F',) term complete;
@@ -245,27 +248,26 @@ def _assemble(placed, L, table, n):
         sid(c, ("F",))
     trans = [dict() for _ in range(L)]   # site -> {(a, b): matrix}
 
-    def state_at(c, sites, local, nops, tau):
-        if c <= tau:
-            content = tuple((k, local[k], nops[k]) for k in sites if k < c)
-            return ("p", content) if content else ("I",)
-        content = tuple((k, local[k], nops[k]) for k in sites if k >= c)
-        return ("s", content) if content else ("F",)
-
-    def passing(content):
-        par = sum(x[2] for x in content) % 2
-        return _PAR if par else _I4
-
     for sites, local, nops, coef, tau in placed:
-        for k in range(L):
-            a = state_at(k, sites, local, nops, tau)
-            b = state_at(k + 1, sites, local, nops, tau)
-            if k < sites[0] and k < tau:
-                continue          # I -> I, shared identity
-            if k > sites[-1] and k > tau:
-                continue          # F -> F, shared identity
+        items = [(k, local[k], nops[k]) for k in sites]
+        # cuts left of both the first operator and tau stay on the shared identity
+        # channel I -> I, cuts right of both on F -> F: only [k0, k1] gets transitions
+        k0, k1 = min(sites[0], tau), max(sites[-1], tau)
+
+        def state_at(c):
+            cnt = bisect.bisect_left(sites, c)     # operators on sites < c
+            if c <= tau:
+                return ("p", tuple(items[:cnt])) if cnt else ("I",)
+            return ("s", tuple(items[cnt:])) if cnt < len(items) else ("F",)
+
+        b = state_at(k0)
+        for k in range(k0, k1 + 1):
+            a, b = b, state_at(k + 1)
             ia, ib = sid(k, a), sid(k + 1, b)
-            op = table[local[k]] if k in local else passing(a[1])
+            if k in local:
+                op = mats[local[k]]
+            else:   # operator-free site: identity or the Jordan-Wigner parity
+                op = _PAR if sum(x[2] for x in a[1]) % 2 else _I4
             if k == tau:
                 t = trans[k]
                 if (ia, ib) in t:

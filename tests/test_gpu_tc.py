@@ -110,3 +110,97 @@ def test_bf16_sweep_energy_within_1e6_of_fp64(ctx):
                               svd_tol=1e-10, eig_tol=1e-8, coarse_eps=1e-10)
         res[prec] = a2.energy(ctx, t, mpo, "fp64")[0]
     assert abs(res["bf16"] - res["fp64"]) < 1e-6
+
+
+# ---- identity-on-physical fold of the hand-over core (W = I (x) G + W_rest)
+
+@pytest.fixture(scope="module")
+def chem16(ctx):
+    h, eri = chemistry_integrals(16, 2505)
+    m = chemistry_mpo(h, eri)
+    return m, a2.MPO(ctx, m)
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16", 2e-2), ("f32emu", 5e-6)])
+@pytest.mark.parametrize("k,Dl,Dr", [(7, 32, 32), (8, 32, 32), (7, 24, 40), (8, 40, 24),
+                                     (7, 16, 36), (8, 8, 12)])
+def test_heff_hand_over_fold(ctx, chem16, prec, tol, k, Dl, Dr):
+    """Bonds 7 / 8 of the L=16 chemistry MPO touch its hand-over core (site 8), whose
+    identity block is folded into the right (bond 7) or left (bond 8) environment;
+    Dr % 8 != 0 keeps the right fold off.  Folded and unfolded chains both match the
+    oracle."""
+    m, mpo = chem16
+    assert mpo.fold_info(8)[0] and not mpo.fold_info(7)[0]
+    rng = np.random.default_rng(100 + k + Dl)
+    Lh = rng.standard_normal((Dl, m[k].shape[0], Dl))
+    Rh = rng.standard_normal((Dr, m[k + 1].shape[3], Dr))
+    x = rng.standard_normal((Dl, 4, 4, Dr))
+    ref = oracle_heff(Lh, m[k], m[k + 1], Rh, x)
+    out = {}
+    for fold in (True, False):
+        mpo.set_fold(fold)
+        y = torch.zeros(x.shape, dtype=torch.float64, device="cuda")
+        a2.heff_apply(ctx, mpo, k, dev(Lh), dev(Rh), dev(x), y, prec=prec)
+        out[fold] = host(y, ctx)
+    mpo.set_fold(True)
+    assert rel(out[True], ref) < tol
+    assert rel(out[False], ref) < tol
+
+
+def _fold_mpo(seed, n=2, R=(64, 72, 80)):
+    """Four-site operator whose two middle cores both carry a large identity block."""
+    rng = np.random.default_rng(seed)
+    Ra, Rb, Rc = R
+    cores = [rng.standard_normal((1, n, n, Ra)) * 0.5]
+    for Rl, Rr in ((Ra, Rb), (Rb, Rc)):
+        W = np.zeros((Rl, n, n, Rr))
+        G = rng.standard_normal((Rl, Rr)) * (rng.random((Rl, Rr)) < 0.7)
+        for s in range(n):
+            W[:, s, s, :] = G
+        W[:, 0, n - 1, :] = rng.standard_normal((Rl, Rr)) * (rng.random((Rl, Rr)) < 0.05)
+        W[:, n - 1, n - 1, :] += rng.standard_normal((Rl, Rr)) * (rng.random((Rl, Rr)) < 0.05)
+        cores.append(W)
+    cores.append(rng.standard_normal((Rc, n, n, 1)) * 0.5)
+    return cores
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16", 2e-2), ("f32emu", 5e-6)])
+@pytest.mark.parametrize("n,Dl,Dr", [(2, 48, 64), (4, 16, 24), (2, 33, 8)])
+def test_heff_both_cores_folded(ctx, prec, tol, n, Dl, Dr):
+    m = _fold_mpo(7 + n, n=n)
+    mpo = a2.MPO(ctx, m)
+    assert mpo.fold_info(1)[0] and mpo.fold_info(2)[0]
+    rng = np.random.default_rng(Dl)
+    Lh = rng.standard_normal((Dl, m[1].shape[0], Dl))
+    Rh = rng.standard_normal((Dr, m[2].shape[3], Dr))
+    x = rng.standard_normal((Dl, n, n, Dr))
+    ref = oracle_heff(Lh, m[1], m[2], Rh, x)
+    y = torch.zeros(x.shape, dtype=torch.float64, device="cuda")
+    a2.heff_apply(ctx, mpo, 1, dev(Lh), dev(Rh), dev(x), y, prec=prec)
+    assert rel(host(y, ctx), ref) < tol
+    mpo.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16", "f32emu"])
+def test_heff_operator_handle(ctx, chem16, prec):
+    """a2_heff_create / a2_heff_apply_op (environments converted once) give the same
+    result as a2_heff_apply, call after call (up to the summation order of the split-K
+    atomic accumulation)."""
+    tol = {"fp64": 1e-13, "fp32": 1e-6, "bf16": 1e-5, "f32emu": 1e-6}[prec]
+    m, mpo = chem16
+    k, Dl, Dr = 7, 16, 24
+    rng = np.random.default_rng(3)
+    Lh = dev(rng.standard_normal((Dl, m[k].shape[0], Dl)))
+    Rh = dev(rng.standard_normal((Dr, m[k + 1].shape[3], Dr)))
+    x = dev(rng.standard_normal((Dl, 4, 4, Dr)))
+    y0 = torch.zeros(x.shape, dtype=torch.float64, device="cuda")
+    a2.heff_apply(ctx, mpo, k, Lh, Rh, x, y0, prec=prec)
+    ref = host(y0, ctx)
+    op = a2.HeffOp(ctx, mpo, k, Lh, Rh, prec=prec)
+    del Lh, Rh
+    for _ in range(2):
+        y = torch.full(x.shape, float("nan"), dtype=torch.float64, device="cuda")
+        op.apply(x, y)
+        got = host(y, ctx)
+        assert np.all(np.isfinite(got)) and rel(got, ref) < tol
+    op.close()
