@@ -158,6 +158,7 @@ struct TcArgs {
   int out_kind;
   int npairs;              // operand pairs accumulated into one tile (split precision)
   int pa[6], pb[6];        // A / B plane of each pair
+  int tma_store;           // 1: epilogue through shared memory + TMA bulk tensor store
 };
 
 // Up to three BF16 planes per operand (a value split into high, middle and low parts).
@@ -169,6 +170,7 @@ struct TcMaps {
   CUtensorMap b[3];
   CUtensorMap a2[3];
   CUtensorMap b2[3];
+  CUtensorMap c;           // output (FP32 box 32 x 32 or BF16 box 64 x 32, 128B swizzle)
 };
 
 constexpr int kEpiWarps = 4;                       // one per TMEM lane quarter
@@ -178,7 +180,7 @@ template <int BN, int STAGES>
 struct TcSmem {
   alignas(1024) __nv_bfloat16 a[STAGES][BM * BK];
   alignas(1024) __nv_bfloat16 b[STAGES][BN * BK];
-  float stage[kEpiWarps][32 * 33];                 // epilogue transpose buffers
+  alignas(1024) unsigned char cbuf[kEpiWarps][2][4096];   // epilogue staging, 2 per warp
   alignas(8) uint64_t full[STAGES];                // TMA -> MMA
   alignas(8) uint64_t empty[STAGES];               // MMA -> TMA
   alignas(8) uint64_t acc_full[2];                 // MMA -> epilogue (per TMEM buffer)
@@ -187,6 +189,42 @@ struct TcSmem {
   uint32_t tmem_base;
   int abort_flag;
 };
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x,
+                                             int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(x), "r"(y), "r"(smem_u32(src))
+      : "memory");
+}
+__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap* map, const void* src, int x,
+                                                  int y) {
+  asm volatile(
+      "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.bulk_group [%0, {%1, %2}], [%3];" ::
+          "l"(reinterpret_cast<uint64_t>(map)),
+      "r"(x), "r"(y), "r"(smem_u32(src))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read1() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
+                                             uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
+               "r"(d)
+               : "memory");
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
 
 static_assert(sizeof(TcSmem<256, 4>) + 1024 <= 227 * 1024, "BN=256 ring exceeds shared memory");
 static_assert(sizeof(TcSmem<128, 6>) + 1024 <= 227 * 1024, "BN=128 ring exceeds shared memory");
@@ -351,8 +389,9 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
   } else {
     // ---------------- epilogue warps
     const int q = warp & 3;                          // TMEM lane quarter of this warp
-    float* stage = S.stage[warp - 2];
-    uint32_t lu = 0;
+    unsigned char* wbuf = S.cbuf[warp - 2][0];       // 2 x 4 KB, 1024-byte aligned
+    const bool bf16_out = args.out_kind == OUT_BF16;
+    uint32_t lu = 0, chunk = 0;
     for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++lu) {
       const uint32_t buf = lu & 1, use = lu >> 1;
       if (!mbar_wait_or_abort(&S.acc_full[buf], use & 1, 4, &S.abort_flag)) {
@@ -364,36 +403,83 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
       const int n0 = ((u / tiles_m) % tiles_n) * BN;
       const uint32_t tl = tmem + buf * BN + ((uint32_t)(q * 32) << 16);
       const int row0 = m0 + q * 32;
+      if (args.tma_store && row0 < args.M) {
+        // Each lane owns one row of the 32-row slab: it writes its 128-byte row segment
+        // into a 128B-swizzled staging buffer (16-byte chunk j of row r lands at chunk
+        // j ^ (r % 8)), then lane 0 issues one TMA store (or reduce-add) of the 32-row box;
+        // the box is clipped at the matrix edges by the tensor map.
+        const int cw = bf16_out ? 64 : 32;
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
-        if (n0 + c0 >= args.N) break;
-        float v[32];
-        tmem_ld32(tl + (uint32_t)c0, v);
+        for (int c0 = 0; c0 < BN; c0 += cw, ++chunk) {
+          if (n0 + c0 >= args.N) break;
+          unsigned char* sb = wbuf + (chunk & 1) * 4096;
+          if (lane == 0) bulk_wait_read1();   // the store issued from sb two chunks ago
+          __syncwarp();
+          const uint32_t rowa = smem_u32(sb) + lane * 128;
+          if (bf16_out) {
+            float v0[32], v1[32];
+            tmem_ld32(tl + (uint32_t)c0, v0);
+            tmem_ld32(tl + (uint32_t)(c0 + 32), v1);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) stage[lane * 33 + i] = v[i];
-        __syncwarp();
-        const int col = n0 + c0 + lane;
-        if (col < args.N) {
-#pragma unroll 4
-          for (int r = 0; r < 32; ++r) {
-            const int row = row0 + r;
-            if (row >= args.M) break;
-            const float x = stage[r * 33 + lane];
-            const long long off = (long long)row * args.ldc + col;
-            if (args.out_kind == OUT_BF16)
-              reinterpret_cast<__nv_bfloat16*>(args.C)[off] = __float2bfloat16_rn(x);
-            else if (args.out_kind == OUT_F32_ATOMIC)
-              atomicAdd(reinterpret_cast<float*>(args.C) + off, x);
-            else
-              reinterpret_cast<float*>(args.C)[off] = x;
+            for (int j = 0; j < 8; ++j) {
+              const float* v = j < 4 ? v0 + 8 * j : v1 + 8 * (j - 4);
+              st_shared_v4(rowa + ((j ^ (lane & 7)) << 4), pack_bf16(v[0], v[1]),
+                           pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+            }
+          } else {
+            float v[32];
+            tmem_ld32(tl + (uint32_t)c0, v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              st_shared_v4(rowa + ((j ^ (lane & 7)) << 4), __float_as_uint(v[4 * j]),
+                           __float_as_uint(v[4 * j + 1]), __float_as_uint(v[4 * j + 2]),
+                           __float_as_uint(v[4 * j + 3]));
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          // every chunk that wrote a staging buffer commits exactly one bulk group, which
+          // is what the wait_group.read accounting above relies on
+          if (lane == 0) {
+            if (args.out_kind == OUT_F32_ATOMIC) tma_reduce_add_2d(&maps.c, sb, n0 + c0, row0);
+            else tma_store_2d(&maps.c, sb, n0 + c0, row0);
+            bulk_commit();
           }
         }
-        __syncwarp();
+      } else if (!args.tma_store) {
+        // plain stores through a padded transpose buffer (row strides of C not TMA-able)
+        float* stage = reinterpret_cast<float*>(wbuf);
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+          if (n0 + c0 >= args.N) break;
+          float v[32];
+          tmem_ld32(tl + (uint32_t)c0, v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) stage[lane * 33 + i] = v[i];
+          __syncwarp();
+          const int col = n0 + c0 + lane;
+          const int nrow = min(32, args.M - row0);
+          if (col < args.N) {
+            if (args.out_kind == OUT_BF16) {
+              __nv_bfloat16* cp = reinterpret_cast<__nv_bfloat16*>(args.C) +
+                                  (long long)row0 * args.ldc + col;
+              for (int r = 0; r < nrow; ++r)
+                cp[(long long)r * args.ldc] = __float2bfloat16_rn(stage[r * 33 + lane]);
+            } else if (args.out_kind == OUT_F32_ATOMIC) {
+              float* cp = reinterpret_cast<float*>(args.C) + (long long)row0 * args.ldc + col;
+              for (int r = 0; r < nrow; ++r) atomicAdd(cp + (long long)r * args.ldc, stage[r * 33 + lane]);
+            } else {
+              float* cp = reinterpret_cast<float*>(args.C) + (long long)row0 * args.ldc + col;
+              for (int r = 0; r < nrow; ++r) cp[(long long)r * args.ldc] = stage[r * 33 + lane];
+            }
+          }
+          __syncwarp();
+        }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(&S.acc_empty[buf]);
     }
+    if (args.tma_store && lane == 0) bulk_wait_all();   // stores complete before exit
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -523,6 +609,25 @@ void launch(const __nv_bfloat16* const* A, long long lda, const __nv_bfloat16* c
     args.pb[p] = p < npairs ? pb[p] : 0;
   }
   args.splits = splitk;
+  // TMA store epilogue when C's base and row stride allow it
+  {
+    const size_t es = out_kind == OUT_BF16 ? 2 : 4;
+    args.tma_store = ((reinterpret_cast<uintptr_t>(C) & 15) == 0 && (ldc * es) % 16 == 0 &&
+                      ldc >= N) ? 1 : 0;
+    if (args.tma_store) {
+      const cuuint64_t cd[2] = {(cuuint64_t)N, (cuuint64_t)M};
+      const cuuint64_t cs[1] = {(cuuint64_t)(ldc * es)};
+      const cuuint32_t cb[2] = {(cuuint32_t)(out_kind == OUT_BF16 ? 64 : 32), 32u};
+      const cuuint32_t ce[2] = {1, 1};
+      CUresult r = encode_fn()(&maps.c,
+                               out_kind == OUT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                               2, C, cd, cs, cb, ce, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) args.tma_store = 0;
+    }
+  }
   const long long units = (long long)cdiv(M, BM) * cdiv(N, BN) * splitk;
   A2_REQUIRE(units < (1LL << 31), "tcgen05 GEMM too large");
   const int grid = (int)std::min<long long>(units, std::max(1, num_sms));

@@ -34,7 +34,9 @@ def _bf16(rows, k, ld, seed):
 @pytest.mark.parametrize("M,N,K,splitk", [
     (128, 128, 64, 1), (256, 256, 256, 1), (200, 300, 72, 1), (1000, 130, 520, 1),
     (129, 257, 8, 1), (64, 40, 16, 1), (4096, 256, 8192, 8), (333, 96, 1000, 3),
-    (512, 2048, 256, 1)])
+    (512, 2048, 256, 1),
+    # many tiles per persistent CTA with a ragged last row tile (TMA-store epilogue)
+    (58438, 512, 64, 1), (20070, 136, 200, 3), (19999, 300, 40, 1)])
 def test_gemm_bf16_matches_definition(ctx, M, N, K, splitk):
     ld = (K + 7) // 8 * 8
     A = _bf16(M, K, ld, 1)
