@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--profile-matvec", action="store_true",
                    help="small case for ncu: H_eff applications at the middle bond only")
     p.add_argument("--D", type=int, default=128, help="bond dimension of --profile-matvec")
+    p.add_argument("--bond", type=int, default=None,
+                   help="bond of --profile-matvec (default: the one left of the middle)")
     p.add_argument("--reps", type=int, default=3)
     return p.parse_args()
 
@@ -197,14 +199,15 @@ def est_iteration_flops(cfg, mpo, matvecs_per_bond=30):
 
 
 def profile_matvec(args):
-    """H_eff at the middle bond of the L=16 chemistry MPO with random environments of
-    bond dimension --D: BF16 and FP32-accurate tensor-core chains, --reps times each."""
+    """H_eff at one bond of the L=16 chemistry MPO with random environments of bond
+    dimension --D: BF16 and FP32-accurate tensor-core chains (operator handles, the
+    environments converted once), --reps applications each."""
     import torch
     import paper_2505_23429_gb300 as a2
     cfg, cores, _ = workload(args.config)
     ctx = a2.Context(0)
     mpo = a2.MPO(ctx, cores)
-    k = cfg["L"] // 2 - 1
+    k = cfg["L"] // 2 - 1 if args.bond is None else args.bond
     D, n = args.D, cfg["n"]
     g = torch.Generator(device="cuda").manual_seed(0)
     HL = torch.randn(D, cores[k].shape[0], D, device="cuda", dtype=torch.float64, generator=g)
@@ -213,9 +216,11 @@ def profile_matvec(args):
     y = torch.empty_like(x)
     torch.cuda.synchronize()
     for prec in ("bf16", "f32emu"):
+        op = a2.HeffOp(ctx, mpo, k, HL, HR, prec=prec)
         for _ in range(args.reps):
-            a2.heff_apply(ctx, mpo, k, HL, HR, x, y, prec=prec)
-    ctx.synchronize()
+            op.apply(x, y)
+        ctx.synchronize()
+        op.close()
     print(json.dumps(dict(profile_matvec=True, D=D, bond=k, error_flag=a2.device_error(ctx))))
 
 

@@ -54,6 +54,24 @@ def heff_apply(HL, W1, W2, HR, x):
     return T
 
 
+def heff_apply_entry(HL, W1, W2, HR, x, a, b):
+    """The slice y[a, :, :, b] of heff_apply, contracted for that one pair of outer bond
+    indices only (the same sum as above with a and b fixed), so that single outputs of a
+    full-size application can be checked without forming the whole product."""
+    T = np.tensordot(HL[a], x, axes=(1, 0))                      # w t1 t2 b'
+    T = np.tensordot(T, HR[b], axes=(3, 1))                      # w t1 t2 w2
+    T = np.tensordot(W1, T, axes=([0, 2], [0, 1]))               # s1 w1 t2 w2
+    return np.tensordot(T, W2, axes=([1, 2, 3], [0, 2, 3]))      # s1 s2
+
+
+def env_left_update_entry(HL, U_bra, W, U_ket, b, bp):
+    """The slice out[b, :, bp] of env_left_update (eq. env_L update with bra index b and
+    ket index bp fixed)."""
+    X = np.tensordot(HL, U_ket[:, :, bp], axes=(2, 0))           # a w t
+    Z = np.tensordot(U_bra[:, :, b], X, axes=(0, 0))             # s w t
+    return np.tensordot(Z, W, axes=([0, 1, 2], [1, 0, 2]))       # w'
+
+
 def heff_dense(HL, W1, W2, HR):
     Dl, n1, n2, Dr = HL.shape[0], W1.shape[1], W2.shape[1], HR.shape[0]
     N = Dl * n1 * n2 * Dr

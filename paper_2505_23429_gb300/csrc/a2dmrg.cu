@@ -41,6 +41,10 @@ struct a2_ctx {
   DevBuf t1, t2, t3, xa, ya, cb, ck, gram, wv, tmp1, tmp2, tf;   // scratch
   std::vector<a2_ctx*> lanes;   // per-group contexts (own stream, scratch, solver)
   std::mutex lane_mu;
+  // group lanes only: a high-priority stream for the latency-bound factorisations, so
+  // that their many small kernels are not queued behind the other groups' matvecs
+  cudaStream_t hi = nullptr;
+  cudaEvent_t ev_to_hi = nullptr, ev_from_hi = nullptr;
 };
 
 struct a2_tt {
@@ -211,6 +215,11 @@ a2_ctx* lane(a2_ctx* c, int i) {
     l->device = c->device;
     A2_CUDA(cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking));
     l->own_stream = true;
+    int least = 0, greatest = 0;
+    A2_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    A2_CUDA(cudaStreamCreateWithPriority(&l->hi, cudaStreamNonBlocking, greatest));
+    A2_CUDA(cudaEventCreateWithFlags(&l->ev_to_hi, cudaEventDisableTiming));
+    A2_CUDA(cudaEventCreateWithFlags(&l->ev_from_hi, cudaEventDisableTiming));
     l->solver.init(l->stream);
     l->scal.ensure(sizeof(double) * 16384, l->stream);
     l->partial.ensure(sizeof(double) * kReduceBlocks * 64, l->stream);
@@ -220,6 +229,31 @@ a2_ctx* lane(a2_ctx* c, int i) {
   }
   return c->lanes[i];
 }
+
+// Runs the enclosed work of a group lane on its high-priority stream (ordered after and
+// before the lane's normal stream by events); a no-op for contexts without one.
+struct HiScope {
+  a2_ctx* c;
+  cudaStream_t saved = nullptr;
+  explicit HiScope(a2_ctx* ctx) : c(ctx) {
+    if (!c->hi) return;
+    A2_CUDA(cudaEventRecord(c->ev_to_hi, c->stream));
+    A2_CUDA(cudaStreamWaitEvent(c->hi, c->ev_to_hi, 0));
+    saved = c->stream;
+    c->stream = c->hi;
+    c->solver.set_stream(c->hi);
+  }
+  ~HiScope() {
+    if (!saved) return;
+    cudaEventRecord(c->ev_from_hi, c->hi);
+    cudaStreamWaitEvent(saved, c->ev_from_hi, 0);
+    c->stream = saved;
+    try {
+      c->solver.set_stream(saved);
+    } catch (...) {
+    }
+  }
+};
 
 void destroy_ctx_resources(a2_ctx* c) {
   cudaStreamSynchronize(c->stream);
@@ -1014,13 +1048,8 @@ int svd_split_dev(a2_ctx* c, const double* M, int rows, int cols, int D_max, dou
   r = std::max(1, std::min(r, D_max));
   if (discarded) *discarded = std::sqrt(std::max(tail[r], 0.0));
   if (sv_out) *sv_out = sv;
-  // P[i][c] = evec column (rows-1-c): G column-major, column j at G + j*rows
-  c->tmp1.ensure(sizeof(double) * (size_t)rows * r, s);
-  double* Pcm = c->tmp1.as<double>();   // r columns, column-major (rows x r)
-  for (int cc = 0; cc < r; ++cc)
-    A2_CUDA(cudaMemcpyAsync(Pcm + (size_t)cc * rows, G + (size_t)(col_of_first - cc) * rows,
-                            sizeof(double) * rows, cudaMemcpyDeviceToDevice, s));
-  transpose2d<double, double>(Pcm, P, r, rows, s);      // -> row-major rows x r
+  // P[i][c] = eigenvector column (col_of_first - c) of G (column-major, leading dim rows)
+  cols_rev_to_rows(G, rows, rows, col_of_first, r, P, s);
   {  // SQ = P^T M : (r x cols)
     SimtGemm<double, double> g;
     g.M = r; g.N = cols; g.K = rows;
@@ -1245,8 +1274,12 @@ struct Sweeper {
       P.ensure(sizeof(double) * (size_t)rows * kmax, s);
       SQ.ensure(sizeof(double) * (size_t)kmax * cols, s);
       double disc = 0.0;
-      const int r = svd_split_dev(c, x.as<double>(), rows, cols, o.D_max, o.svd_tol,
-                                  P.as<double>(), SQ.as<double>(), &disc);
+      int r = 0;
+      {
+        HiScope hs(c);
+        r = svd_split_dev(c, x.as<double>(), rows, cols, o.D_max, o.svd_tol, P.as<double>(),
+                          SQ.as<double>(), &disc);
+      }
       G.disc = std::max(G.disc, disc);
       // group-local left environment with the new left-orthogonal core
       DevBuf Hn;
@@ -1761,12 +1794,27 @@ a2_status a2_ctx_destroy(a2_ctx* c) {
   if (!c) return A2_EINVAL;
   for (a2_ctx* l : c->lanes) {
     destroy_ctx_resources(l);
+    if (l->hi) {
+      cudaStreamSynchronize(l->hi);
+      cudaStreamDestroy(l->hi);
+      cudaEventDestroy(l->ev_to_hi);
+      cudaEventDestroy(l->ev_from_hi);
+    }
     cudaStreamDestroy(l->stream);
     delete l;
   }
   c->lanes.clear();
   destroy_ctx_resources(c);
   if (c->own_stream) cudaStreamDestroy(c->stream);
+  // hand the pool's cached, now unused memory back (other contexts keep theirs)
+  try {
+    int prev = 0;
+    if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(c->device) == cudaSuccess) {
+      cudaMemPoolTrimTo(lib_pool(), 0);   // the context's streams were synchronised above
+      cudaSetDevice(prev);
+    }
+  } catch (...) {
+  }
   delete c;
   return A2_OK;
 }

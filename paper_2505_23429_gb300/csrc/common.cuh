@@ -43,7 +43,13 @@ long long launch_count();
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
-// Stream-ordered device buffer (cudaMallocAsync pool).
+// The library's stream-ordered memory pool of the current device: memory stays cached
+// in the pool (no release at stream synchronisation) and is never handed to another
+// stream with an implicit dependency on the freeing stream (the concurrent group
+// streams must not serialise through their scratch).
+cudaMemPool_t lib_pool();
+
+// Stream-ordered device buffer (allocated from lib_pool()).
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -71,7 +77,7 @@ struct DevBuf {
     release();
     s = stream;
     size_t nb = nbytes ? nbytes : 16;
-    A2_CUDA(cudaMallocAsync(&p, nb, stream));
+    A2_CUDA(cudaMallocFromPoolAsync(&p, nb, lib_pool(), stream));
     bytes = nb;
   }
   template <typename T> T* as() const { return reinterpret_cast<T*>(p); }

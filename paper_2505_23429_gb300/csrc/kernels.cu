@@ -8,6 +8,30 @@
 
 namespace a2 {
 
+// ----------------------------------------------------------------------------- memory pool
+cudaMemPool_t lib_pool() {
+  static std::mutex mu;
+  static std::vector<cudaMemPool_t> pools;
+  int dev = 0;
+  A2_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> g(mu);
+  if ((int)pools.size() <= dev) pools.resize(dev + 1, nullptr);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool;
+    A2_CUDA(cudaMemPoolCreate(&pool, &props));
+    uint64_t keep = ~0ull;
+    A2_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    int no = 0;
+    A2_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no));
+    pools[dev] = pool;
+  }
+  return pools[dev];
+}
+
 // ----------------------------------------------------------------------------- launch count
 namespace {
 std::atomic<long long> g_launches{0};
@@ -1184,6 +1208,30 @@ void precondition(const double* r, const double* diag, const double* theta, doub
 }
 
 // ----------------------------------------------------------------------------- assorted
+__global__ void cols_rev_to_rows_kernel(const double* __restrict__ G, long long ld, int rows,
+                                        int col_first, int r, double* __restrict__ P) {
+  __shared__ double tile[32][33];
+  const int i0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += 8) {           // read columns (contiguous in i)
+    const int c = c0 + j, i = i0 + threadIdx.x;
+    if (c < r && i < rows) tile[j][threadIdx.x] = G[(long long)(col_first - c) * ld + i];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += 8) {           // write rows of P (contiguous in c)
+    const int i = i0 + j, c = c0 + threadIdx.x;
+    if (c < r && i < rows) P[(long long)i * r + c] = tile[threadIdx.x][j];
+  }
+}
+void cols_rev_to_rows(const double* G, long long ld, int rows, int col_first, int r, double* P,
+                      cudaStream_t s) {
+  if (rows <= 0 || r <= 0) return;
+  A2_REQUIRE(col_first - (r - 1) >= 0, "cols_rev_to_rows: column range");
+  dim3 grid(cdiv(rows, 32), cdiv(r, 32));
+  A2_REQUIRE(grid.y < 65536, "cols_rev_to_rows: grid too large");
+  cols_rev_to_rows_kernel<<<grid, dim3(32, 8), 0, s>>>(G, ld, rows, col_first, r, P);
+  A2_CHECK_LAUNCH();
+}
+
 void fill_zero(void* p, size_t bytes, cudaStream_t s) {
   if (bytes) A2_CUDA(cudaMemsetAsync(p, 0, bytes, s));
 }

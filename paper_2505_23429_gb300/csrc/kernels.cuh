@@ -131,6 +131,10 @@ void precondition(const double* r, const double* diag, const double* theta, doub
                   long long n, cudaStream_t s);
 
 // ---- assorted
+// P[i][c] = G[(col_first - c) * ld + i] for i < rows, c < r (P row-major rows x r): the
+// columns col_first, col_first - 1, ... of a column-major matrix, as rows of P.
+void cols_rev_to_rows(const double* G, long long ld, int rows, int col_first, int r, double* P,
+                      cudaStream_t s);
 void fill_zero(void* p, size_t bytes, cudaStream_t s);
 void sign_fix_qr(double* Q, int ldq, int rows, double* R, int ldr, int k, cudaStream_t s);
 void scale_rows(double* M, int rows, int cols, const double* svals, cudaStream_t s); // M[r,:]*=s[r]

@@ -17,6 +17,8 @@ void Solver::init(cudaStream_t s) {
   info.ensure(sizeof(int) * 4, s);
 }
 
+void Solver::set_stream(cudaStream_t s) { A2_SOLVER(cusolverDnSetStream(h, s)); }
+
 void Solver::destroy() {
   if (h) cusolverDnDestroy(h);
   h = nullptr;

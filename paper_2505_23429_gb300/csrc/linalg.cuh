@@ -11,6 +11,7 @@ struct Solver {
   DevBuf work, info, tmp;
   void init(cudaStream_t s);
   void destroy();
+  void set_stream(cudaStream_t s);
   // LQ of a row-major (rows x cols) matrix M: M = L Q, Q (k x cols) orthonormal rows,
   // L (rows x k) lower-trapezoidal with diag >= 0, k = min(rows, cols).
   // Q is written row-major (k x cols), L row-major (rows x k).  M is not modified.
