@@ -11,6 +11,7 @@
 //   S3 T3[a,s1,s2,w2,b'] = sum_{w1,t2} A_k+1[w1,s2,t2,w2] T2[...]   sparse MPO action
 //   S4 y[a,s1,s2,b]      = sum_{w2,b'} T3[...] R[b,w2,b']            dense GEMM (split K)
 #include <algorithm>
+#include <atomic>
 #include <array>
 #include <chrono>
 #include <cmath>
@@ -1397,6 +1398,43 @@ struct Sweeper {
     return dot_dev(c, e64, r64, ne, 7);
   }
 
+  // Device bytes one group lane needs at its largest local problem (bond dims capped by
+  // D_max): the H_eff intermediates of the tensor-core chain (or of the SIMT chain), the
+  // converted environments, the Lanczos basis and the environment-update scratch.
+  double lane_bytes() const {
+    // exact-rank caps of the bond dims: prod of the physical dims on either side
+    std::vector<double> lcap(L + 1, 1.0), rcap(L + 1, 1.0);
+    for (int j = 0; j < L; ++j) lcap[j + 1] = std::min<double>(o.D_max, lcap[j] * tt->phys[j]);
+    for (int j = L - 1; j >= 0; --j) rcap[j] = std::min<double>(o.D_max, rcap[j + 1] * tt->phys[j]);
+    double worst = 0.0;
+    const double m = std::min(o.max_krylov, 63) + 3;
+    const double es = sizeof(T);
+    for (int k = 0; k + 1 < L; ++k) {
+      const double n1 = tt->phys[k], n2 = tt->phys[k + 1];
+      const double Dl = lcap[k], Dr = rcap[k + 2];
+      const double Rl = mpo->R[k], R1 = mpo->R[k + 1], Rr = mpo->R[k + 2];
+      const double N = Dl * n1 * n2 * Dr;
+      double heff;
+      if (sizeof(T) == 4 && o.prec != A2_FP32)      // tensor-core chains (split planes)
+        heff = std::max(4.0 * Dl * Rl, 6.0 * Dl * Rr) * n1 * n2 * Dr + 6.0 * Dl * R1 * n1 * n2 * Dr +
+               12.0 * (Dl * Rl * Dl + Dr * Rr * Dr + 2.0 * Dl * R1 * Dl);
+      else                                           // SIMT chain: t1 = max(T1, T3), t2 = T2
+        heff = es * (std::max(Rl, Rr) + R1) * Dl * n1 * n2 * Dr;
+      const double env = 2.0 * es * Dl * std::max(Rl, Rr) * n1 * Dr;
+      worst = std::max(worst, heff + env + 8.0 * m * N + 16.0 * N);
+    }
+    return worst;
+  }
+
+  // Number of group lanes that fit in the free device memory next to what is resident.
+  int concurrent_lanes(int P) const {
+    size_t free_b = 0, total_b = 0;
+    A2_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const double need = std::max(1.0, lane_bytes());
+    const int fit = (int)std::floor(0.8 * (double)free_b / need);
+    return std::max(1, std::min(P, fit));
+  }
+
   void run(a2_sweep_report* rep, bool classical) {
     cudaStream_t s = c->stream;
     auto t0 = std::chrono::steady_clock::now();
@@ -1425,22 +1463,27 @@ struct Sweeper {
       groups[g].mg = k0 + sizes[g] - 1;
       k0 += sizes[g];
     }
-    if (P > 1 && o.group_streams != 1) {
-      // the groups are independent (Alg. 2 step 2): one host thread and one stream each
+    const int nl = (P > 1 && o.group_streams != 1) ? concurrent_lanes(P) : 1;
+    if (nl > 1) {
+      // the groups are independent (Alg. 2 step 2): nl host threads, each with its own
+      // stream, scratch and solver, take the groups one after another
       A2_CUDA(cudaStreamSynchronize(s));                 // environments are ready
       std::vector<std::unique_ptr<Engine<T>>> engs;
-      for (int g = 0; g < P; ++g) engs.emplace_back(new Engine<T>(lane(c, g), mpo, o.prec));
-      std::vector<std::exception_ptr> errs(P);
+      for (int i = 0; i < nl; ++i) engs.emplace_back(new Engine<T>(lane(c, i), mpo, o.prec));
+      std::vector<std::exception_ptr> errs(nl);
+      std::atomic<int> next{0};
       std::vector<std::thread> th;
-      for (int g = 0; g < P; ++g)
-        th.emplace_back([&, g] {
+      for (int i = 0; i < nl; ++i)
+        th.emplace_back([&, i] {
           try {
             A2_CUDA(cudaSetDevice(c->device));
-            a2_ctx* lc = lane(c, g);
-            solve_group(groups[g], lc, *engs[g]);
+            a2_ctx* lc = lane(c, i);
+            for (int g = next.fetch_add(1); g < P; g = next.fetch_add(1))
+              solve_group(groups[g], lc, *engs[i]);
             A2_CUDA(cudaStreamSynchronize(lc->stream));
           } catch (...) {
-            errs[g] = std::current_exception();
+            errs[i] = std::current_exception();
+            next.store(P);                         // the other lanes stop at their next group
           }
         });
       for (auto& t : th) t.join();

@@ -173,14 +173,16 @@ struct TcMaps {
   CUtensorMap c;           // output (FP32 box 32 x 32 or BF16 box 64 x 32, 128B swizzle)
 };
 
-constexpr int kEpiWarps = 4;                       // one per TMEM lane quarter
-constexpr int kThreads = 64 + 32 * kEpiWarps;      // producer warp, MMA warp, epilogue warps
+// Epilogue warps: 4 (one per TMEM lane quarter, each draining all BN columns), or 8 in
+// the promoted mode (two per lane quarter, 128 columns each, FP32 register accumulators).
+__host__ __device__ constexpr int epi_warps(bool promote) { return promote ? 8 : 4; }
+__host__ __device__ constexpr int tc_threads(bool promote) { return 64 + 32 * epi_warps(promote); }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, int EPI, int NBUF>
 struct TcSmem {
   alignas(1024) __nv_bfloat16 a[STAGES][BM * BK];
   alignas(1024) __nv_bfloat16 b[STAGES][BN * BK];
-  alignas(1024) unsigned char cbuf[kEpiWarps][2][4096];   // epilogue staging, 2 per warp
+  alignas(1024) unsigned char cbuf[EPI][NBUF][4096];      // epilogue staging buffers
   alignas(8) uint64_t full[STAGES];                // TMA -> MMA
   alignas(8) uint64_t empty[STAGES];               // MMA -> TMA
   alignas(8) uint64_t acc_full[2];                 // MMA -> epilogue (per TMEM buffer)
@@ -212,6 +214,9 @@ __device__ __forceinline__ void bulk_commit() {
 __device__ __forceinline__ void bulk_wait_read1() {
   asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
 }
+__device__ __forceinline__ void bulk_wait_read0() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
 __device__ __forceinline__ void bulk_wait_all() {
   asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
@@ -226,8 +231,9 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-static_assert(sizeof(TcSmem<256, 4>) + 1024 <= 227 * 1024, "BN=256 ring exceeds shared memory");
-static_assert(sizeof(TcSmem<128, 6>) + 1024 <= 227 * 1024, "BN=128 ring exceeds shared memory");
+static_assert(sizeof(TcSmem<256, 4, 4, 2>) + 1024 <= 227 * 1024, "BN=256 ring exceeds smem");
+static_assert(sizeof(TcSmem<128, 6, 4, 2>) + 1024 <= 227 * 1024, "BN=128 ring exceeds smem");
+static_assert(sizeof(TcSmem<256, 4, 8, 1>) + 1024 <= 227 * 1024, "promoted ring exceeds smem");
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -252,13 +258,23 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parit
 // TMEM lanes 32*(w%4)..+31) and store it, so the epilogue of one unit overlaps the MMAs
 // of the next.  Every wait is bounded; a timeout raises the device error flag and all
 // roles leave their loops, wait (bounded) for their copies / MMAs in flight and exit.
-template <int BN, int STAGES>
-__global__ void __launch_bounds__(kThreads, 1)
+// PROMOTE (FP32 outputs, BN = 256): the tensor cores' FP32 accumulator truncates, so
+// over long reductions its error grows with the number of accumulate steps.  In this
+// mode every kPromoteKB K blocks (with their operand pairs) are accumulated into a fresh
+// TMEM buffer and the eight epilogue warps add the partials into IEEE FP32 registers
+// (round to nearest), 128 columns of one row per thread.
+constexpr int kPromoteKB = 2;
+
+template <int BN, int STAGES, bool PROMOTE>
+__global__ void __launch_bounds__(tc_threads(PROMOTE), 1)
 tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
+  constexpr int EPI = epi_warps(PROMOTE);
+  constexpr int NBUF = PROMOTE ? 1 : 2;
+  static_assert(!PROMOTE || BN == 256, "promoted accumulation: two warps x 128 columns");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t base = smem_u32(smem_raw);
   const uint32_t pad = (1024u - (base & 1023u)) & 1023u;
-  auto& S = *reinterpret_cast<TcSmem<BN, STAGES>*>(smem_raw + pad);
+  auto& S = *reinterpret_cast<TcSmem<BN, STAGES, EPI, NBUF>*>(smem_raw + pad);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tiles_m = (args.M + BM - 1) / BM;
@@ -275,7 +291,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&S.acc_full[i], 1);
-      mbar_init(&S.acc_empty[i], kEpiWarps);
+      mbar_init(&S.acc_empty[i], EPI);
     }
     mbar_init(&S.drain, 1);
     S.abort_flag = 0;
@@ -343,44 +359,45 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
     if (lane == 0) {
       // ---------------- MMA issuer
       constexpr uint32_t idesc = idesc_bf16(BM, BN);
-      uint32_t g = 0, lu = 0;
-      bool issued_any = false;
-      for (int u = blockIdx.x; u < nunits && !*(volatile int*)&S.abort_flag;
-           u += gridDim.x, ++lu) {
-        const uint32_t buf = lu & 1, use = lu >> 1;
-        if (use > 0 &&
-            !mbar_wait_or_abort(&S.acc_empty[buf], (use - 1) & 1, 5, &S.abort_flag)) {
-          S.abort_flag = 1;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t d = tmem + buf * BN;
+      uint32_t g = 0, ch = 0;                        // ring steps, accumulator chunks
+      bool issued_any = false, ok = true;
+      for (int u = blockIdx.x; ok && u < nunits && !*(volatile int*)&S.abort_flag;
+           u += gridDim.x) {
         int kb0, nkb;
         unit_k(u, kb0, nkb);
         const int steps = nkb * np;
-        bool ok = true;
-        for (int kb = 0; kb < steps; ++kb, ++g) {
-          const int s = g % STAGES;
-          if (!mbar_wait_or_abort(&S.full[s], (g / STAGES) & 1, 3, &S.abort_flag)) {
+        const int cs = PROMOTE ? kPromoteKB * np : steps;   // steps per accumulator chunk
+        for (int st0 = 0; st0 < steps; st0 += cs, ++ch) {
+          const uint32_t buf = ch & 1, use = ch >> 1;
+          if (use > 0 &&
+              !mbar_wait_or_abort(&S.acc_empty[buf], (use - 1) & 1, 5, &S.abort_flag)) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint64_t da = smem_desc(S.a[s]);
-          const uint64_t db = smem_desc(S.b[s]);
+          const uint32_t d = tmem + buf * BN;
+          const int st1 = min(steps, st0 + cs);
+          for (int kb = st0; kb < st1; ++kb, ++g) {
+            const int s = g % STAGES;
+            if (!mbar_wait_or_abort(&S.full[s], (g / STAGES) & 1, 3, &S.abort_flag)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint64_t da = smem_desc(S.a[s]);
+            const uint64_t db = smem_desc(S.b[s]);
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk)
-            mma_bf16(d, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
-                     (kb > 0 || kk > 0) ? 1u : 0u);
-          issued_any = true;
-          mma_commit(&S.empty[s]);   // frees the stage once these MMAs have read it
+            for (int kk = 0; kk < BK / 16; ++kk)
+              mma_bf16(d, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+                       (kb > st0 || kk > 0) ? 1u : 0u);
+            issued_any = true;
+            mma_commit(&S.empty[s]);   // frees the stage once these MMAs have read it
+          }
+          if (!ok) break;
+          mma_commit(&S.acc_full[buf]);
         }
-        if (!ok) {
-          S.abort_flag = 1;
-          break;
-        }
-        mma_commit(&S.acc_full[buf]);
       }
+      if (!ok) S.abort_flag = 1;
       if (*(volatile int*)&S.abort_flag && issued_any) {
         mma_commit(&S.drain);      // wait (bounded) for the MMAs still in flight
         mbar_wait(&S.drain, 0, 6);
@@ -389,96 +406,166 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
   } else {
     // ---------------- epilogue warps
     const int q = warp & 3;                          // TMEM lane quarter of this warp
-    unsigned char* wbuf = S.cbuf[warp - 2][0];       // 2 x 4 KB, 1024-byte aligned
+    const int ew = warp - 2;                         // epilogue warp index
+    const int colbase = PROMOTE ? (ew >> 2) * 128 : 0;   // columns of this warp (promoted)
+    unsigned char* wbuf = S.cbuf[ew][0];             // NBUF x 4 KB, 1024-byte aligned
     const bool bf16_out = args.out_kind == OUT_BF16;
-    uint32_t lu = 0, chunk = 0;
-    for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++lu) {
-      const uint32_t buf = lu & 1, use = lu >> 1;
-      if (!mbar_wait_or_abort(&S.acc_full[buf], use & 1, 4, &S.abort_flag)) {
-        S.abort_flag = 1;
-        break;
-      }
+    uint32_t ch = 0, chunk = 0;
+    bool ok = true;
+    // wait for accumulator chunk `ch` and return its TMEM base
+    auto acquire = [&](uint32_t& tl) -> bool {
+      const uint32_t buf = ch & 1, use = ch >> 1;
+      if (!mbar_wait_or_abort(&S.acc_full[buf], use & 1, 4, &S.abort_flag)) return false;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      tl = tmem + buf * BN + (uint32_t)colbase + ((uint32_t)(q * 32) << 16);
+      return true;
+    };
+    auto release = [&]() {
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.acc_empty[ch & 1]);
+      ++ch;
+    };
+    // stage one row segment of 32 FP32 values (this lane's row) and store the 32-row slab
+    auto store32 = [&](const float (&v)[32], int n0c, int row0) {
+      unsigned char* sb = wbuf + (chunk % NBUF) * 4096;
+      if (lane == 0) {                    // the store issued from sb NBUF chunks ago
+        if (NBUF == 1) bulk_wait_read0();
+        else bulk_wait_read1();
+      }
+      __syncwarp();
+      const uint32_t rowa = smem_u32(sb) + lane * 128;
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        st_shared_v4(rowa + ((j ^ (lane & 7)) << 4), __float_as_uint(v[4 * j]),
+                     __float_as_uint(v[4 * j + 1]), __float_as_uint(v[4 * j + 2]),
+                     __float_as_uint(v[4 * j + 3]));
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      // every chunk that wrote a staging buffer commits exactly one bulk group, which is
+      // what the wait_group.read accounting above relies on
+      if (lane == 0) {
+        if (args.out_kind == OUT_F32_ATOMIC) tma_reduce_add_2d(&maps.c, sb, n0c, row0);
+        else tma_store_2d(&maps.c, sb, n0c, row0);
+        bulk_commit();
+      }
+      ++chunk;
+    };
+    // plain stores of one 32 x 32 block through a 4 KB transpose buffer: row r, column c
+    // lives at r * 32 + (c ^ r), so that both the row writes and the column reads below
+    // touch 32 different banks
+    auto plain32 = [&](const float (&v)[32], int n0c, int row0) {
+      float* stage = reinterpret_cast<float*>(wbuf);     // (used only without TMA stores)
+#pragma unroll
+      for (int i = 0; i < 32; ++i) stage[lane * 32 + (i ^ lane)] = v[i];
+      __syncwarp();
+      const int col = n0c + lane;
+      const int nrow = min(32, args.M - row0);
+      if (col < args.N) {
+        if (args.out_kind == OUT_BF16) {
+          __nv_bfloat16* cp =
+              reinterpret_cast<__nv_bfloat16*>(args.C) + (long long)row0 * args.ldc + col;
+          for (int r = 0; r < nrow; ++r)
+            cp[(long long)r * args.ldc] = __float2bfloat16_rn(stage[r * 32 + (lane ^ r)]);
+        } else if (args.out_kind == OUT_F32_ATOMIC) {
+          float* cp = reinterpret_cast<float*>(args.C) + (long long)row0 * args.ldc + col;
+          for (int r = 0; r < nrow; ++r)
+            atomicAdd(cp + (long long)r * args.ldc, stage[r * 32 + (lane ^ r)]);
+        } else {
+          float* cp = reinterpret_cast<float*>(args.C) + (long long)row0 * args.ldc + col;
+          for (int r = 0; r < nrow; ++r) cp[(long long)r * args.ldc] = stage[r * 32 + (lane ^ r)];
+        }
+      }
+      __syncwarp();
+    };
+    for (int u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
       const int m0 = (u % tiles_m) * BM;
       const int n0 = ((u / tiles_m) % tiles_n) * BN;
-      const uint32_t tl = tmem + buf * BN + ((uint32_t)(q * 32) << 16);
       const int row0 = m0 + q * 32;
-      if (args.tma_store && row0 < args.M) {
-        // Each lane owns one row of the 32-row slab: it writes its 128-byte row segment
-        // into a 128B-swizzled staging buffer (16-byte chunk j of row r lands at chunk
-        // j ^ (r % 8)), then lane 0 issues one TMA store (or reduce-add) of the 32-row box;
-        // the box is clipped at the matrix edges by the tensor map.
-        const int cw = bf16_out ? 64 : 32;
-#pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += cw, ++chunk) {
-          if (n0 + c0 >= args.N) break;
-          unsigned char* sb = wbuf + (chunk & 1) * 4096;
-          if (lane == 0) bulk_wait_read1();   // the store issued from sb two chunks ago
-          __syncwarp();
-          const uint32_t rowa = smem_u32(sb) + lane * 128;
-          if (bf16_out) {
-            float v0[32], v1[32];
-            tmem_ld32(tl + (uint32_t)c0, v0);
-            tmem_ld32(tl + (uint32_t)(c0 + 32), v1);
+      const bool rows_here = row0 < args.M;
+      if constexpr (PROMOTE) {
+        int kb0, nkb;
+        unit_k(u, kb0, nkb);
+        const int steps = nkb * np, cs = kPromoteKB * np;
+        float acc[128];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const float* v = j < 4 ? v0 + 8 * j : v1 + 8 * (j - 4);
-              st_shared_v4(rowa + ((j ^ (lane & 7)) << 4), pack_bf16(v[0], v[1]),
-                           pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
-            }
-          } else {
+        for (int i = 0; i < 128; ++i) acc[i] = 0.f;
+        for (int st0 = 0; st0 < steps; st0 += cs) {
+          uint32_t tl;
+          if (!acquire(tl)) { ok = false; break; }
+#pragma unroll
+          for (int c0 = 0; c0 < 128; c0 += 32) {
             float v[32];
             tmem_ld32(tl + (uint32_t)c0, v);
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-              st_shared_v4(rowa + ((j ^ (lane & 7)) << 4), __float_as_uint(v[4 * j]),
-                           __float_as_uint(v[4 * j + 1]), __float_as_uint(v[4 * j + 2]),
-                           __float_as_uint(v[4 * j + 3]));
+            for (int i = 0; i < 32; ++i) acc[c0 + i] += v[i];
           }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          __syncwarp();
-          // every chunk that wrote a staging buffer commits exactly one bulk group, which
-          // is what the wait_group.read accounting above relies on
-          if (lane == 0) {
-            if (args.out_kind == OUT_F32_ATOMIC) tma_reduce_add_2d(&maps.c, sb, n0 + c0, row0);
-            else tma_store_2d(&maps.c, sb, n0 + c0, row0);
-            bulk_commit();
+          release();
+        }
+        if (!ok) break;
+#pragma unroll
+        for (int c0 = 0; c0 < 128; c0 += 32) {
+          const int col = n0 + colbase + c0;
+          if (col < args.N && rows_here) {
+            float v[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = acc[c0 + i];
+            if (args.tma_store) store32(v, col, row0);
+            else plain32(v, col, row0);
           }
         }
-      } else if (!args.tma_store) {
-        // plain stores through a padded transpose buffer (row strides of C not TMA-able)
-        float* stage = reinterpret_cast<float*>(wbuf);
+      } else {
+        uint32_t tl;
+        if (!acquire(tl)) { ok = false; break; }
+        if (args.tma_store && rows_here) {
+          // Each lane owns one row of the 32-row slab: it writes its 128-byte row segment
+          // into a 128B-swizzled staging buffer (16-byte chunk j of row r lands at chunk
+          // j ^ (r % 8)), then lane 0 issues one TMA store (or reduce-add) of the 32-row
+          // box; the box is clipped at the matrix edges by the tensor map.
+          const int cw = bf16_out ? 64 : 32;
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-          if (n0 + c0 >= args.N) break;
-          float v[32];
-          tmem_ld32(tl + (uint32_t)c0, v);
+          for (int c0 = 0; c0 < BN; c0 += cw) {
+            if (n0 + c0 >= args.N) break;
+            if (bf16_out) {
+              unsigned char* sb = wbuf + (chunk & 1) * 4096;
+              if (lane == 0) bulk_wait_read1();
+              __syncwarp();
+              const uint32_t rowa = smem_u32(sb) + lane * 128;
+              float v0[32], v1[32];
+              tmem_ld32(tl + (uint32_t)c0, v0);
+              tmem_ld32(tl + (uint32_t)(c0 + 32), v1);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) stage[lane * 33 + i] = v[i];
-          __syncwarp();
-          const int col = n0 + c0 + lane;
-          const int nrow = min(32, args.M - row0);
-          if (col < args.N) {
-            if (args.out_kind == OUT_BF16) {
-              __nv_bfloat16* cp = reinterpret_cast<__nv_bfloat16*>(args.C) +
-                                  (long long)row0 * args.ldc + col;
-              for (int r = 0; r < nrow; ++r)
-                cp[(long long)r * args.ldc] = __float2bfloat16_rn(stage[r * 33 + lane]);
-            } else if (args.out_kind == OUT_F32_ATOMIC) {
-              float* cp = reinterpret_cast<float*>(args.C) + (long long)row0 * args.ldc + col;
-              for (int r = 0; r < nrow; ++r) atomicAdd(cp + (long long)r * args.ldc, stage[r * 33 + lane]);
+              for (int j = 0; j < 8; ++j) {
+                const float* v = j < 4 ? v0 + 8 * j : v1 + 8 * (j - 4);
+                st_shared_v4(rowa + ((j ^ (lane & 7)) << 4), pack_bf16(v[0], v[1]),
+                             pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+              }
+              asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+              __syncwarp();
+              if (lane == 0) {
+                tma_store_2d(&maps.c, sb, n0 + c0, row0);
+                bulk_commit();
+              }
+              ++chunk;
             } else {
-              float* cp = reinterpret_cast<float*>(args.C) + (long long)row0 * args.ldc + col;
-              for (int r = 0; r < nrow; ++r) cp[(long long)r * args.ldc] = stage[r * 33 + lane];
+              float v[32];
+              tmem_ld32(tl + (uint32_t)c0, v);
+              store32(v, n0 + c0, row0);
             }
           }
-          __syncwarp();
+        } else if (!args.tma_store) {
+#pragma unroll 1
+          for (int c0 = 0; c0 < BN; c0 += 32) {
+            if (n0 + c0 >= args.N) break;
+            float v[32];
+            tmem_ld32(tl + (uint32_t)c0, v);
+            plain32(v, n0 + c0, row0);
+          }
         }
+        release();
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&S.acc_empty[buf]);
     }
+    if (!ok) S.abort_flag = 1;
     if (args.tma_store && lane == 0) bulk_wait_all();   // stores complete before exit
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -539,7 +626,7 @@ CUtensorMap make_map_nd(const __nv_bfloat16* ptr, int rank, const cuuint64_t* di
   return m;
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool PROMOTE>
 void launch(const __nv_bfloat16* const* A, long long lda, const __nv_bfloat16* const* B,
             long long ldb, int M, int N, int K, int npairs, const int* pa, const int* pb,
             const TcSeg2* seg, void* C, long long ldc, int out_kind, int splitk,
@@ -581,10 +668,11 @@ void launch(const __nv_bfloat16* const* A, long long lda, const __nv_bfloat16* c
       maps.b2[i] = maps.b[i];
     }
   }
-  const size_t smem = sizeof(TcSmem<BN, STAGES>) + 1024;
+  constexpr int EPI = epi_warps(PROMOTE);
+  const size_t smem = sizeof(TcSmem<BN, STAGES, EPI, PROMOTE ? 1 : 2>) + 1024;
   static std::once_flag once;
   std::call_once(once, [smem] {
-    A2_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES>,
+    A2_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES, PROMOTE>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   });
   static int num_sms = 0;
@@ -631,7 +719,7 @@ void launch(const __nv_bfloat16* const* A, long long lda, const __nv_bfloat16* c
   const long long units = (long long)cdiv(M, BM) * cdiv(N, BN) * splitk;
   A2_REQUIRE(units < (1LL << 31), "tcgen05 GEMM too large");
   const int grid = (int)std::min<long long>(units, std::max(1, num_sms));
-  tc_gemm_kernel<BN, STAGES><<<grid, kThreads, smem, s>>>(maps, args);
+  tc_gemm_kernel<BN, STAGES, PROMOTE><<<grid, tc_threads(PROMOTE), smem, s>>>(maps, args);
   A2_CHECK_LAUNCH();
 }
 
@@ -666,12 +754,15 @@ void tc_gemm_bf16_pairs(const __nv_bfloat16* const* A, long long lda,
   A2_REQUIRE(K >= 1 && npairs >= 1 && npairs <= 6, "tc GEMM: K >= 1, 1..6 operand pairs");
   if (splitk > 1)
     A2_REQUIRE(out_kind == tc::OUT_F32_ATOMIC, "split-K needs atomic FP32 output");
-  if (N <= 128)
-    tc::launch<128, 6>(A, lda, B, ldb, M, N, K, npairs, pa, pb, seg, C, ldc, out_kind, splitk,
-                       s);
+  if (npairs > 1 && out_kind != tc::OUT_BF16)   // split-precision products: promoted sums
+    tc::launch<256, 4, true>(A, lda, B, ldb, M, N, K, npairs, pa, pb, seg, C, ldc, out_kind,
+                             splitk, s);
+  else if (N <= 128)
+    tc::launch<128, 6, false>(A, lda, B, ldb, M, N, K, npairs, pa, pb, seg, C, ldc, out_kind,
+                              splitk, s);
   else
-    tc::launch<256, 4>(A, lda, B, ldb, M, N, K, npairs, pa, pb, seg, C, ldc, out_kind, splitk,
-                       s);
+    tc::launch<256, 4, false>(A, lda, B, ldb, M, N, K, npairs, pa, pb, seg, C, ldc, out_kind,
+                              splitk, s);
 }
 
 // -------------------------------------------------------------- BF16 H_eff chain
@@ -867,7 +958,8 @@ void tc_heff_f32emu(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int 
     ProfScope ps(PK_EMU_S4, s, 6.0 * 2.0 * M * N * K, 6.0 * (M * K + N * K) + 4.0 * M * N);
     fill_zero(y, sizeof(float) * (size_t)M4 * Dr, s);
     tc_gemm_bf16_pairs(A, ld3, B, ldr, (int)M4, Dr, (int)K4, 6, pa, pb, y, Dr,
-                       tc::OUT_F32_ATOMIC, s4_splitk(M4, Dr, kb), s, t2split ? &seg : nullptr);
+                       tc::OUT_F32_ATOMIC, s4_splitk(M4, Dr, kb), s,
+                       t2split ? &seg : nullptr);
   }
 }
 

@@ -19,6 +19,10 @@ from gpu_common import dev, host  # noqa: E402
 
 D = 256
 SAMPLES = [(0, 0), (17, 255), (128, 3), (255, 130), (77, 77)]
+# FP32-class arithmetic (FP32 SIMT, or split BF16 products with FP32 sums): one output of
+# H_eff at D = 256 sums ~1e6 signed products, so rounding at eps32 = 6e-8 leaves an error
+# of order eps32 * sqrt(1e6) relative to the output scale.
+TOL32 = 6e-8 * 1e3
 
 
 @pytest.fixture(scope="module")
@@ -40,7 +44,8 @@ def _scaled_err(got, ref, scale):
     return float(np.abs(np.asarray(got) - np.asarray(ref)).max() / scale)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("f32emu", 5e-6), ("bf16", 3e-2)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", TOL32), ("f32emu", TOL32),
+                                      ("bf16", 3e-2)])
 @pytest.mark.parametrize("k", [5, 7, 8])
 def test_heff_full_size_sampled(ctx, chem16, prec, tol, k):
     """Bond 5: a typical middle bond; 7 / 8: the hand-over core on the right / left
@@ -63,7 +68,7 @@ def test_heff_full_size_sampled(ctx, chem16, prec, tol, k):
         assert _scaled_err(yh[a, :, :, b], ref, scale) < tol, (a, b)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("f32emu", 5e-6)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", TOL32), ("f32emu", TOL32)])
 @pytest.mark.parametrize("j", [5, 8])
 def test_env_update_full_size_sampled(ctx, chem16, prec, tol, j):
     m, mpo = chem16
