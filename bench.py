@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = ("additive-sweep time to |dE|<1e-6 vs FP64 oracle; "
           "H_eff matvec TFLOP/s vs plain")
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+FP64_PEAK_TFLOPS = 1.2   # FP64 (SIMT) rate measured on this part with a DGEMM loop
 
 
 def parse():
@@ -55,6 +56,8 @@ def parse():
     p.add_argument("--config", default="chem_L16_D256")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-mv", action="store_true",
+                   help="skip the H_eff matvec comparison (e.g. under a profiler)")
     p.add_argument("--profile-matvec", action="store_true",
                    help="small case for ncu: H_eff applications at the middle bond only")
     p.add_argument("--D", type=int, default=128, help="bond dimension of --profile-matvec")
@@ -224,6 +227,22 @@ def profile_matvec(args):
     print(json.dumps(dict(profile_matvec=True, D=D, bond=k, error_flag=a2.device_error(ctx))))
 
 
+def class_roofline(name, d, peaks, prec):
+    """(bound, unit, peak, achieved) of one kernel class from its CUDA-event totals and
+    the algorithmic flops / bytes the library counts for it."""
+    rate_f = d["flops"] / (d["ms"] * 1e-3) / 1e12
+    rate_b = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+    if name in ("tc_s1", "tc_s4", "emu_s1", "emu_s4"):
+        return "tensor", "TFLOP/s", peaks["bf16_sus"], rate_f
+    if name in ("sparse_s2", "sparse_s3", "emu_s2", "emu_s3", "lanczos"):
+        return "hbm", "GB/s", peaks["hbm"], rate_b
+    if name == "env" and prec in ("bf16", "f32emu"):
+        return "tensor", "TFLOP/s", peaks["bf16_sus"], rate_f
+    if name in ("heff_simt", "env") and prec != "fp64":
+        return "alu", "TFLOP/s", FP32_SIMT_PEAK_TFLOPS, rate_f
+    return "alu", "TFLOP/s", FP64_PEAK_TFLOPS, rate_f        # FP64 factorisations / SIMT
+
+
 def nvtx(torch, name):
     """Push (name) or pop (None) an NVTX range on this thread, if NVTX is available."""
     try:
@@ -339,26 +358,21 @@ def main():
             t_conv, it_conv = cum, i + 1
             break
 
-    # dominant kernel class and its roofline
+    # dominant kernel class and its roofline (and the same figures for every class)
     peaks = read_peaks()
     dom = max(prof, key=lambda k: prof[k]["ms"])
     d = prof[dom]
-    if dom in ("tc_s1", "tc_s4", "emu_s1", "emu_s4"):
-        bound, unit, peak = "tensor", "TFLOP/s", peaks["bf16_sus"]
-        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
-    elif dom in ("sparse_s2", "sparse_s3", "emu_s2", "emu_s3", "lanczos"):
-        bound, unit, peak = "hbm", "GB/s", peaks["hbm"]
-        achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
-    elif dom in ("heff_simt", "env"):
-        bound, unit, peak = "alu", "TFLOP/s", FP32_SIMT_PEAK_TFLOPS
-        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
-    else:
-        bound, unit, peak = "alu", "TFLOP/s", 1.2
-        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+    bound, unit, peak, achieved = class_roofline(dom, d, peaks, args.prec)
     per_launch = d["ms"] / max(d["launches"], 1)
+    rooflines = {}
+    for k, v in prof.items():
+        if v["launches"] and v["ms"] > 0:
+            b_, u_, p_, a_ = class_roofline(k, v, peaks, args.prec)
+            rooflines[k] = dict(bound=b_, achieved=round(a_, 2), peak=p_, unit=u_,
+                                frac=round(a_ / p_, 4))
 
     # H_eff matvec TFLOP/s: tensor-core chain vs a plain torch.einsum chain (dense MPO, BF16)
-    mv = matvec_compare(a2, ctx, mpo, mpo_cores, cfg, torch, stream)
+    mv = None if args.no_mv else matvec_compare(a2, ctx, mpo, mpo_cores, cfg, torch, stream)
 
     value = job_throughput(args.steps, ms, world)
     line = dict(metric=METRIC, value=value, unit="additive sweeps/s", n_gpus=world,
@@ -380,6 +394,7 @@ def main():
                               frac=achieved / peak, traffic=None,
                               per_launch_ms=per_launch, launches=d["launches"],
                               peak_source=peaks["src"]),
+                roofline_classes=rooflines,
                 kernel_classes={k: dict(ms=round(v["ms"], 3), launches=v["launches"],
                                         tflops=round(v["flops"] / (v["ms"] * 1e9), 2)
                                         if v["ms"] > 0 else None,

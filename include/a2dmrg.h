@@ -173,6 +173,25 @@ a2_status a2_coarse_solve(a2_ctx* ctx, int m, const double* A_hat, const double*
 a2_status a2_energy(a2_ctx* ctx, const a2_tt* tt, const a2_mpo* mpo, a2_precision prec,
                     double* E_out, double* norm_out);
 
+/* ---- gradients with respect to the Hamiltonian's parameters --------------- */
+
+/* dE/dtheta of E(theta) = <x, A(theta) x>/<x, x> at the fixed TT x (Hellmann-Feynman:
+ * at a converged iterate this is the total derivative of the ground energy), for an MPO
+ * whose cores are affine in the parameters, W_j(theta) = W_j(0) + sum_p theta_p M_p,j.
+ * The map lists the nonzero entries of every M_p,j: entry e says that core
+ * map_site[e] (flat index map_index[e] into its [R_l][n][n][R_r] array) has
+ * dW/dtheta_{map_param[e]} = map_factor[e] (host arrays of length nmap, copied).
+ * The adjoint of the sandwich, G_j = dE/dW_j (App. A contraction with core j taken out:
+ * left environment, core j as bra and ket, right environment), is formed for every
+ * core that the map touches, in FP64 on the device, and contracted with the map;
+ * grad_out (host, nparam) receives dE/dtheta, E_out (host, may be NULL) the energy.
+ * Not a step of the paper's method (the gradient configuration of the benchmark).
+ * Errors: A2_EINVAL on NULL / out-of-range map entries or mismatched handles. */
+a2_status a2_energy_gradient(a2_ctx* ctx, const a2_tt* tt, const a2_mpo* mpo, long long nparam,
+                             long long nmap, const long long* map_param, const int* map_site,
+                             const long long* map_index, const double* map_factor,
+                             double* grad_out, double* E_out);
+
 /* ---- kernel-level entry points (device pointers, FP64 in/out) ------------- */
 
 /* y = H_eff x for the two-site problem at bond k (sites k, k+1), the

@@ -80,6 +80,9 @@ def lib():
                            _P, ctypes.POINTER(_P)],
         "a2_heff_apply_op": [_P, _P, _P],
         "a2_heff_destroy": [_P],
+        "a2_energy_gradient": [_P, _P, _P, ctypes.c_longlong, ctypes.c_longlong,
+                               ctypes.POINTER(ctypes.c_longlong), _I,
+                               ctypes.POINTER(ctypes.c_longlong), _D, _D, _D],
         "a2_additive_sweep": [_P, _P, _P, ctypes.POINTER(SweepOpts), ctypes.POINTER(SweepReport)],
         "a2_classical_sweep": [_P, _P, _P, ctypes.POINTER(SweepOpts), ctypes.POINTER(SweepReport)],
         "a2_coarse_solve": [_P, ctypes.c_int, _D, _D, ctypes.c_double, _D, _D, _I],
@@ -118,7 +121,7 @@ def exported_symbols():
             "a2_heff_apply", "a2_env_update", "a2_svd_split", "a2_gemm_bf16",
             "a2_device_error", "a2_profile", "a2_heff_apply_noalloc", "a2_mpo_fold_split",
             "a2_mpo_fold_info", "a2_mpo_set_fold", "a2_heff_create", "a2_heff_apply_op",
-            "a2_heff_destroy"]
+            "a2_heff_destroy", "a2_energy_gradient"]
 
 
 def _dp(a):
@@ -434,3 +437,45 @@ def fold_split(W):
     if st != 0:
         raise A2Error(st, "a2_mpo_fold_split failed")
     return G, nz.value, bool(f.value)
+
+
+def energy_gradient(ctx, tt, mpo, cmap):
+    """(E, dE/dtheta) at the fixed TT for an MPO built with a coefficient map
+    (synthetic.chemistry_mpo(..., coeff_map=True)): cmap holds param, site, index,
+    factor arrays and nparam."""
+    p = np.ascontiguousarray(cmap["param"], dtype=np.int64)
+    st = np.ascontiguousarray(cmap["site"], dtype=np.int32)
+    ix = np.ascontiguousarray(cmap["index"], dtype=np.int64)
+    fa = np.ascontiguousarray(cmap["factor"], dtype=np.float64)
+    nparam = int(cmap["nparam"])
+    grad = np.zeros(nparam)
+    E = ctypes.c_double()
+    LL = ctypes.POINTER(ctypes.c_longlong)
+    ctx.check(lib().a2_energy_gradient(ctx._h, tt._h, mpo._h, nparam, len(p),
+                                       p.ctypes.data_as(LL), st.ctypes.data_as(_I),
+                                       ix.ctypes.data_as(LL), _dp(fa), _dp(grad),
+                                       ctypes.byref(E)))
+    return E.value, grad
+
+
+def energy_autograd(h, eri, ctx, tt, mpo, cmap):
+    """Energy of the fixed TT as a differentiable function of the one- and two-body
+    coefficients (torch tensors h [L, L], eri [L, L, L, L]); the MPO must have been built
+    from the same values.  Backward returns dE/dh, dE/deri (Hellmann-Feynman at the TT)."""
+    import torch
+
+    class _Energy(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, h_, eri_):
+            E, g = energy_gradient(ctx, tt, mpo, cmap)
+            L = h_.shape[0]
+            fctx.save_for_backward(torch.from_numpy(g[: L * L].reshape(L, L)).to(h_),
+                                   torch.from_numpy(g[L * L:].reshape(L, L, L, L)).to(eri_))
+            return torch.tensor(E, dtype=torch.float64, device=h_.device)
+
+        @staticmethod
+        def backward(fctx, gE):
+            gh, geri = fctx.saved_tensors
+            return gE * gh, gE * geri
+
+    return _Energy.apply(h, eri)

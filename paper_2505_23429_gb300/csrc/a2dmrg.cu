@@ -996,7 +996,16 @@ LanczosResult davidson(a2_ctx* c, MV&& mv, const double* diag, double* x, long l
 int svd_split_dev(a2_ctx* c, const double* M, int rows, int cols, int D_max, double tol,
                   double* P, double* SQ, double* discarded, std::vector<double>* sv_out = nullptr) {
   cudaStream_t s = c->stream;
-  ProfScope ps(PK_SVD, s, 2.0 * rows * rows * (double)cols * 2 + 10.0 * rows * rows * (double)rows,
+  // Only the top min(D_max, rows) eigenpairs can be kept; the discarded weight of any
+  // rank is ||M||_F^2 minus the kept eigenvalues, so the rest need not be computed.
+  const int kmax = std::min(rows, cols);
+  const bool partial = (D_max < kmax) && (D_max * 4 <= rows * 3);
+  const int nev = partial ? D_max : kmax;   // eigenpairs computed (largest first)
+  // algorithmic flops: Gram, Householder tridiagonalisation, back-transformation of the
+  // nev eigenvectors, the product P^T M
+  ProfScope ps(PK_SVD, s,
+               2.0 * rows * rows * (double)cols + 4.0 / 3.0 * rows * rows * (double)rows +
+                   2.0 * rows * rows * (double)nev + 2.0 * nev * (double)rows * cols,
                8.0 * (2.0 * rows * cols + 2.0 * rows * rows));
   c->gram.ensure(sizeof(double) * ((size_t)rows * rows + rows), s);
   double* G = c->gram.as<double>();
@@ -1009,11 +1018,6 @@ int svd_split_dev(a2_ctx* c, const double* M, int rows, int cols, int D_max, dou
     g.C = G; g.scm = rows; g.scn = 1;
     simt_gemm(g, s);
   }
-  // Only the top min(D_max, rows) eigenpairs can be kept; the discarded weight of any
-  // rank is ||M||_F^2 minus the kept eigenvalues, so the rest need not be computed.
-  const int kmax = std::min(rows, cols);
-  const bool partial = (D_max < kmax) && (D_max * 4 <= rows * 3);
-  const int nev = partial ? D_max : kmax;   // eigenpairs computed (largest first)
   std::vector<double> sv(nev);              // singular values, descending
   int col_of_first = rows - 1;              // column of the largest eigenvector in G
   double rest = 0.0;                        // weight beyond the computed eigenpairs
@@ -1795,6 +1799,50 @@ uint64_t splitmix_next(uint64_t& state) {
   return z ^ (z >> 31);
 }
 
+// Adjoint of the energy sandwich with respect to one MPO core (the Hellmann-Feynman
+// derivative at a fixed TT): G[w,s,t,w'] = sum HL[a,w,a'] U[a,s,b] U[a',t,b'] HR[b,w',b']
+// with HL the environment of the sites left of the core and HR of those right of it,
+// both built from the same TT (any gauge).  FP64 SIMT contractions:
+//   X[a,w,t,b'] = sum_a' HL U;  Z[(s b)][(w t b')] = sum_a U X;
+//   G[w,s,t,w'] = sum_{b,b'} Z HR   (batched over b, one launch per (s, t)).
+void core_gradient(a2_ctx* c, const double* HL, int Dl, int Rl, const double* U, int n, int Dr,
+                   const double* HR, int Rr, double* G, DevBuf& bx, DevBuf& bz) {
+  cudaStream_t s = c->stream;
+  bx.ensure(sizeof(double) * (size_t)Dl * Rl * n * Dr, s);
+  bz.ensure(sizeof(double) * (size_t)n * Dr * Rl * n * Dr, s);
+  double* X = bx.as<double>();
+  double* Z = bz.as<double>();
+  const long long nD = (long long)n * Dr, RnD = (long long)Rl * n * Dr;
+  {
+    SimtGemm<double, double> g;
+    g.M = Dl * Rl; g.N = (int)nD; g.K = Dl;
+    g.A = HL; g.sam = Dl; g.sak = 1;
+    g.B = U; g.sbn = 1; g.sbk = nD;
+    g.C = X; g.scm = nD; g.scn = 1;
+    simt_gemm(g, s);
+  }
+  {
+    SimtGemm<double, double> g;
+    g.M = (int)nD; g.N = (int)RnD; g.K = Dl;
+    g.A = U; g.sam = 1; g.sak = nD;
+    g.B = X; g.sbn = 1; g.sbk = RnD;
+    g.C = Z; g.scm = RnD; g.scn = 1;
+    simt_gemm(g, s);
+  }
+  fill_zero(G, sizeof(double) * (size_t)Rl * n * n * Rr, s);
+  for (int sx = 0; sx < n; ++sx)
+    for (int t = 0; t < n; ++t) {
+      SimtGemm<double, double> g;
+      g.M = Rl; g.N = Rr; g.K = Dr;
+      g.A = Z + (long long)sx * Dr * RnD + (long long)t * Dr; g.sam = nD; g.sak = 1;
+      g.B = HR; g.sbn = Dr; g.sbk = 1;
+      g.C = G + ((long long)sx * n + t) * Rr; g.scm = (long long)n * n * Rr; g.scn = 1;
+      g.batch = Dr; g.abs = RnD; g.bbs = (long long)Rr * Dr; g.cbs = 0;
+      g.mode = GEMM_ATOMIC;
+      simt_gemm(g, s);
+    }
+}
+
 }  // namespace
 
 // ============================================================================= C ABI
@@ -2187,6 +2235,84 @@ a2_status a2_heff_destroy(a2_heff* h) {
   cudaStreamSynchronize(h->ctx->stream);
   delete h;
   return A2_OK;
+}
+
+a2_status a2_energy_gradient(a2_ctx* c, const a2_tt* t, const a2_mpo* m, long long nparam,
+                             long long nmap, const long long* map_param, const int* map_site,
+                             const long long* map_index, const double* map_factor,
+                             double* grad_out, double* E_out) {
+  if (!c || !t || !m) return c ? fail(c, A2_EINVAL, "null argument") : A2_EINVAL;
+  return guarded(c, [&] {
+    A2_REQUIRE(nparam >= 1 && nmap >= 0 && grad_out && (nmap == 0 || (map_param && map_site &&
+               map_index && map_factor)), "a2_energy_gradient: bad arguments");
+    tt_check(t);
+    A2_REQUIRE(t->ctx == c && m->L == t->L && t->phys == m->phys, "TT / MPO mismatch");
+    const int L = t->L;
+    cudaStream_t s = c->stream;
+    // map entries grouped by site, checked against the core sizes
+    std::vector<std::vector<long long>> by_site(L);
+    for (long long e = 0; e < nmap; ++e) {
+      const int j = map_site[e];
+      A2_REQUIRE(j >= 0 && j < L, "a2_energy_gradient: map site out of range");
+      const long long size = (long long)m->R[j] * m->phys[j] * m->phys[j] * m->R[j + 1];
+      A2_REQUIRE(map_index[e] >= 0 && map_index[e] < size && map_param[e] >= 0 &&
+                 map_param[e] < nparam, "a2_energy_gradient: map entry out of range");
+      by_site[j].push_back(e);
+    }
+    double nrm = 0.0;
+    const double E = energy_T<double>(c, t, m, &nrm);
+    const double n2 = nrm * nrm;
+    A2_REQUIRE(n2 > 0.0, "a2_energy_gradient: zero TT");
+    Engine<double> eng(c, m, A2_FP64);
+    // right environments of every suffix
+    std::vector<DevBuf> HR(L + 1);
+    eng.set_unit(HR[L]);
+    for (int j = L - 1; j >= 1; --j) {
+      const int Dl = t->dims[j], Dr = t->dims[j + 1];
+      HR[j].ensure(sizeof(double) * (size_t)Dl * m->R[j] * Dl, s);
+      eng.right_update(HR[j + 1].as<double>(), j, t->cores[j].as<double>(), Dl, Dr,
+                       t->cores[j].as<double>(), Dl, Dr, HR[j].as<double>());
+    }
+    DevBuf grad, HL, HLn, G, bx, bz, mp, mi, mf;
+    grad.ensure(sizeof(double) * (size_t)nparam, s);
+    fill_zero(grad.p, sizeof(double) * (size_t)nparam, s);
+    eng.set_unit(HL);
+    for (int j = 0; j < L; ++j) {
+      const int Dl = t->dims[j], n = t->phys[j], Dr = t->dims[j + 1];
+      const int Rl = m->R[j], Rr = m->R[j + 1];
+      if (!by_site[j].empty()) {
+        G.ensure(sizeof(double) * (size_t)Rl * n * n * Rr, s);
+        core_gradient(c, HL.as<double>(), Dl, Rl, t->cores[j].as<double>(), n, Dr,
+                      HR[j + 1].as<double>(), Rr, G.as<double>(), bx, bz);
+        const auto& es = by_site[j];
+        const size_t ne = es.size();
+        std::vector<long long> hp(ne), hi(ne);
+        std::vector<double> hf(ne);
+        for (size_t q = 0; q < ne; ++q) {
+          hp[q] = map_param[es[q]];
+          hi[q] = map_index[es[q]];
+          hf[q] = map_factor[es[q]] / n2;
+        }
+        upload(mp, hp.data(), sizeof(long long) * ne, s);
+        upload(mi, hi.data(), sizeof(long long) * ne, s);
+        upload(mf, hf.data(), sizeof(double) * ne, s);
+        gather_axpy_atomic(G.as<double>(), mi.as<long long>(), mp.as<long long>(),
+                           mf.as<double>(), (long long)ne, grad.as<double>(), s);
+        A2_CUDA(cudaStreamSynchronize(s));     // the host staging vectors go out of scope
+      }
+      if (j + 1 < L) {
+        HLn.ensure(sizeof(double) * (size_t)Dr * m->R[j + 1] * Dr, s);
+        eng.left_update(HL.as<double>(), j, t->cores[j].as<double>(), Dl, Dr,
+                        t->cores[j].as<double>(), Dl, Dr, HLn.as<double>());
+        std::swap(HL, HLn);
+        HR[j + 1].release();
+      }
+    }
+    A2_CUDA(cudaMemcpyAsync(grad_out, grad.p, sizeof(double) * (size_t)nparam,
+                            cudaMemcpyDeviceToHost, s));
+    A2_CUDA(cudaStreamSynchronize(s));
+    if (E_out) *E_out = E;
+  });
 }
 
 a2_status a2_heff_apply(a2_ctx* c, const a2_mpo* m, int k, a2_precision prec, int Dl, int Dr,

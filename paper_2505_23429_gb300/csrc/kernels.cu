@@ -1062,8 +1062,9 @@ void coarse_solve_dev(const double* A, const double* S, int m, double eps, doubl
 
 // ----------------------------------------------------------------------------- tridiagonal
 // Lowest eigenpair of the symmetric tridiagonal T (diag a[0..k-1], off-diag b[0..k-2]):
-// bisection on the Sturm count of T - x I (Golub & Van Loan, Sec. 8.4), then inverse
-// iteration with a partially pivoted tridiagonal solve.  One thread; k <= 64.
+// bisection on the Sturm count of T - x I (Golub & Van Loan, Sec. 8.4; here 32-way
+// multisection by one warp), then inverse iteration with a partially pivoted tridiagonal
+// solve (one thread, shared-memory arrays).  k <= 64.
 __device__ int sturm_below(const double* a, const double* b, int k, double x) {
   int cnt = 0;
   double d = a[0] - x;
@@ -1077,7 +1078,9 @@ __device__ int sturm_below(const double* a, const double* b, int k, double x) {
 }
 
 __global__ void tridiag_lowest_kernel(TridiagIn in, double* out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  // multisection: the 32 lanes evaluate the Sturm count at 32 interior points of the
+  // bracket at once, so that every round shrinks it 33-fold
+  const int lane = threadIdx.x & 31;
   const int k = in.k;
   const double* a = in.a;
   const double* b = in.b;
@@ -1088,19 +1091,24 @@ __global__ void tridiag_lowest_kernel(TridiagIn in, double* out) {
     hi = fmax(hi, a[i] + r);
     scale = fmax(scale, fabs(a[i]) + r);
   }
-  for (int it = 0; it < 200 && hi - lo > 4e-16 * fmax(scale, 1e-300); ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (sturm_below(a, b, k, mid) >= 1) hi = mid; else lo = mid;
+  for (int it = 0; it < 40 && hi - lo > 4e-16 * fmax(scale, 1e-300); ++it) {
+    const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+    const bool above = sturm_below(a, b, k, x) >= 1;     // lowest eigenvalue <= x
+    const unsigned m = __ballot_sync(0xffffffffu, above);
+    const int j = m ? __ffs(m) - 1 : 32;                 // first point above the eigenvalue
+    const double nlo = j == 0 ? lo : lo + (hi - lo) * (double)j / 33.0;
+    const double nhi = j == 32 ? hi : lo + (hi - lo) * (double)(j + 1) / 33.0;
+    if (!(nlo >= lo && nhi <= hi && nlo < nhi)) break;  // no further progress in FP64
+    lo = nlo;
+    hi = nhi;
   }
   const double theta = 0.5 * (lo + hi);
-  // inverse iteration: (T - theta I) y = v
-  double y[64], v[64];
+  if (lane != 0) return;
+  // inverse iteration: (T - theta I) y = v, partially pivoted tridiagonal elimination
+  __shared__ double y[64], v[64], dl[64], d[64], du[64], du2[64], rhs[64];
   for (int i = 0; i < k; ++i) v[i] = 1.0 / sqrt((double)k) * (1.0 + 0.01 * i);
   const double eps = 1e-14 * fmax(scale, 1e-300);
   for (int rep = 0; rep < 3; ++rep) {
-    // Gaussian elimination with partial pivoting on the tridiagonal (dl, d, du, du2)
-    double dl[64], d[64], du[64], du2[64], rhs[64];
     for (int i = 0; i < k; ++i) {
       d[i] = a[i] - theta;
       du[i] = (i + 1 < k) ? b[i] : 0.0;
@@ -1137,8 +1145,8 @@ __global__ void tridiag_lowest_kernel(TridiagIn in, double* out) {
     for (int i = k - 3; i >= 0; --i) y[i] = (rhs[i] - du[i] * y[i + 1] - du2[i] * y[i + 2]) / d[i];
     double nrm = 0.0;
     for (int i = 0; i < k; ++i) nrm += y[i] * y[i];
-    nrm = sqrt(nrm);
-    for (int i = 0; i < k; ++i) v[i] = y[i] / nrm;
+    const double inv = 1.0 / sqrt(nrm);
+    for (int i = 0; i < k; ++i) v[i] = y[i] * inv;
   }
   out[0] = theta;
   for (int i = 0; i < k; ++i) out[1 + i] = v[i];
@@ -1229,6 +1237,22 @@ void cols_rev_to_rows(const double* G, long long ld, int rows, int col_first, in
   dim3 grid(cdiv(rows, 32), cdiv(r, 32));
   A2_REQUIRE(grid.y < 65536, "cols_rev_to_rows: grid too large");
   cols_rev_to_rows_kernel<<<grid, dim3(32, 8), 0, s>>>(G, ld, rows, col_first, r, P);
+  A2_CHECK_LAUNCH();
+}
+
+__global__ void gather_axpy_atomic_kernel(const double* __restrict__ G,
+                                          const long long* __restrict__ index,
+                                          const long long* __restrict__ param,
+                                          const double* __restrict__ factor, long long n,
+                                          double* grad) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    atomicAdd(grad + param[e], factor[e] * G[index[e]]);
+}
+void gather_axpy_atomic(const double* G, const long long* index, const long long* param,
+                        const double* factor, long long n, double* grad, cudaStream_t s) {
+  if (n <= 0) return;
+  gather_axpy_atomic_kernel<<<grid_for(n), 256, 0, s>>>(G, index, param, factor, n, grad);
   A2_CHECK_LAUNCH();
 }
 

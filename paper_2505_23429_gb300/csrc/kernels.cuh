@@ -136,6 +136,9 @@ void precondition(const double* r, const double* diag, const double* theta, doub
 void cols_rev_to_rows(const double* G, long long ld, int rows, int col_first, int r, double* P,
                       cudaStream_t s);
 void fill_zero(void* p, size_t bytes, cudaStream_t s);
+// grad[param[e]] += factor[e] * G[index[e]] for e < n (FP64 atomics)
+void gather_axpy_atomic(const double* G, const long long* index, const long long* param,
+                        const double* factor, long long n, double* grad, cudaStream_t s);
 void sign_fix_qr(double* Q, int ldq, int rows, double* R, int ldr, int k, cudaStream_t s);
 void scale_rows(double* M, int rows, int cols, const double* svals, cudaStream_t s); // M[r,:]*=s[r]
 // TT-sum block copy: dst[(r0 + i)*ld_dst_r + ... ] = alpha * src

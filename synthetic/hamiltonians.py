@@ -193,19 +193,27 @@ def _place_term(coef, ops, L, split_site, table):
     return sites, local, nops, sign * coef, tau
 
 
-def chemistry_mpo(h, eri, split_site=None, tol=0.0):
+def chemistry_mpo(h, eri, split_site=None, tol=0.0, coeff_map=False):
     """Exact MPO (list of (R_l, 4, 4, R_r) cores) of the spin-orbital
     Hamiltonian built from spatial integrals h (L,L) and eri (L,L,L,L).
 
     Terms whose coefficient magnitude is <= tol are skipped (tol=0 keeps every
     nonzero term).  split_site (default L//2) is the site where two-operator
     prefixes hand over to two-operator suffixes.
+
+    coeff_map=True also returns the linear map from the parameters to the cores:
+    every core entry is an affine function of the parameters theta = (h.ravel(),
+    eri.ravel()) (parameter p = i*L + j for h[i, j], L*L + ((i*L + j)*L + k)*L + l for
+    eri[i, j, k, l]), W(theta) = W(0) + sum_p theta_p M_p.  The map lists the nonzero
+    entries of every M_p as arrays param, site, index (flat index into the core),
+    factor.  Parameters skipped by tol have no entries.
     """
     L = h.shape[0]
     if split_site is None:
         split_site = L // 2
     table = {}
     placed = []
+    params = []      # (parameter index, d coefficient / d parameter) per placed term
     for i, j in itertools.product(range(L), repeat=2):
         if abs(h[i, j]) <= tol:
             continue
@@ -214,6 +222,7 @@ def chemistry_mpo(h, eri, split_site=None, tol=0.0):
                             split_site, table)
             if r is not None:
                 placed.append(r)
+                params.append((i * L + j, r[3] / h[i, j]))
     for i, j, k, l in itertools.product(range(L), repeat=4):
         v = eri[i, j, k, l]
         if abs(v) <= tol:
@@ -223,11 +232,12 @@ def chemistry_mpo(h, eri, split_site=None, tol=0.0):
             r = _place_term(0.5 * v, ops, L, split_site, table)
             if r is not None:
                 placed.append(r)
+                params.append((L * L + ((i * L + j) * L + k) * L + l, r[3] / v))
     mats = [m for _, m in sorted(table.values(), key=lambda t: t[0])]
-    return _assemble(placed, L, mats, 4)
+    return _assemble(placed, L, mats, 4, params if coeff_map else None)
 
 
-def _assemble(placed, L, mats, n):
+def _assemble(placed, L, mats, n, params=None):
     """Build MPO cores from placed terms (sites, local keys, nops, coef, tau)."""
     # state identity at cut c (between site c-1 and site c):
     #   ('I',)  nothing placed; ('F',) term complete;
@@ -248,7 +258,8 @@ def _assemble(placed, L, mats, n):
         sid(c, ("F",))
     trans = [dict() for _ in range(L)]   # site -> {(a, b): matrix}
 
-    for sites, local, nops, coef, tau in placed:
+    cmap = []        # (param, site, a, b, op, factor) of the coefficient-bearing blocks
+    for ti, (sites, local, nops, coef, tau) in enumerate(placed):
         items = [(k, local[k], nops[k]) for k in sites]
         # cuts left of both the first operator and tau stay on the shared identity
         # channel I -> I, cuts right of both on F -> F: only [k0, k1] gets transitions
@@ -274,6 +285,8 @@ def _assemble(placed, L, mats, n):
                     t[(ia, ib)] = t[(ia, ib)] + coef * op
                 else:
                     t[(ia, ib)] = coef * op
+                if params is not None:
+                    cmap.append((params[ti][0], k, ia, ib, op, params[ti][1]))
             else:
                 trans[k][(ia, ib)] = op
     cores = []
@@ -288,6 +301,27 @@ def _assemble(placed, L, mats, n):
             W[ia, :, :, ib] += m
         cores.append(W)
     # boundary: keep only the I state on the left and the F state on the right
-    cores[0] = cores[0][states[0][("I",)]:states[0][("I",)] + 1]
-    cores[-1] = cores[-1][..., states[L][("F",)]:states[L][("F",)] + 1]
-    return [np.ascontiguousarray(c) for c in cores]
+    i0, fL = states[0][("I",)], states[L][("F",)]
+    cores[0] = cores[0][i0:i0 + 1]
+    cores[-1] = cores[-1][..., fL:fL + 1]
+    cores = [np.ascontiguousarray(c) for c in cores]
+    if params is None:
+        return cores
+    ps, st, ix, fa = [], [], [], []
+    for p, k, ia, ib, op, d in cmap:
+        if k == 0:
+            assert ia == i0
+            ia = 0
+        if k == L - 1:
+            assert ib == fL
+            ib = 0
+        Rr = cores[k].shape[3]
+        for s_, t_ in zip(*np.nonzero(op)):
+            ps.append(p)
+            st.append(k)
+            ix.append(((ia * n + s_) * n + t_) * Rr + ib)
+            fa.append(d * op[s_, t_])
+    cm = dict(param=np.array(ps, dtype=np.int64), site=np.array(st, dtype=np.int32),
+              index=np.array(ix, dtype=np.int64), factor=np.array(fa, dtype=np.float64),
+              nparam=L * L + L ** 4)
+    return cores, cm
