@@ -80,6 +80,7 @@ def lib():
                            _P, ctypes.POINTER(_P)],
         "a2_heff_apply_op": [_P, _P, _P],
         "a2_heff_destroy": [_P],
+        "a2_set_autotune": [ctypes.c_int],
         "a2_energy_gradient": [_P, _P, _P, ctypes.c_longlong, ctypes.c_longlong,
                                ctypes.POINTER(ctypes.c_longlong), _I,
                                ctypes.POINTER(ctypes.c_longlong), _D, _D, _D],
@@ -121,7 +122,7 @@ def exported_symbols():
             "a2_heff_apply", "a2_env_update", "a2_svd_split", "a2_gemm_bf16",
             "a2_device_error", "a2_profile", "a2_heff_apply_noalloc", "a2_mpo_fold_split",
             "a2_mpo_fold_info", "a2_mpo_set_fold", "a2_heff_create", "a2_heff_apply_op",
-            "a2_heff_destroy", "a2_energy_gradient"]
+            "a2_heff_destroy", "a2_energy_gradient", "a2_set_autotune"]
 
 
 def _dp(a):
@@ -479,3 +480,8 @@ def energy_autograd(h, eri, ctx, tt, mpo, cmap):
             return gE * gh, gE * geri
 
     return _Energy.apply(h, eri)
+
+
+def set_autotune(enable):
+    """Enable / disable the tcgen05 GEMM autotuner (library-wide)."""
+    lib().a2_set_autotune(1 if enable else 0)

@@ -2043,6 +2043,11 @@ a2_status a2_mpo_nnz(const a2_mpo* m, int site, long long* nnz) {
   return A2_OK;
 }
 
+a2_status a2_set_autotune(int enable) {
+  tc_autotune(enable != 0);
+  return A2_OK;
+}
+
 a2_status a2_mpo_fold_split(const double* W, int Rl, int n, int Rr, double* G_out,
                             long long* nnz_g, int* foldable) {
   if (!W || !nnz_g || !foldable || Rl < 1 || n < 1 || Rr < 1) return A2_EINVAL;

@@ -393,13 +393,19 @@ sparse_rows_split3_kernel(SparseRows<V> sp, SparseGeom g, const TI* __restrict__
       for (int i = 0; i < NV; ++i) acc[i] += add[ob + ro + i];
     }
     __nv_bfloat16* o = out + ob + ro;
+    // NV consecutive values per plane in one vector store (8 or 16 bytes)
+    __align__(16) __nv_bfloat16 h[NV], m[NV], lo[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      __nv_bfloat16 h, m, lo;
-      split3<Acc>(acc[i], h, m, lo);
-      o[i] = h;
-      o[plane + i] = m;
-      o[2 * plane + i] = lo;
+    for (int i = 0; i < NV; ++i) split3<Acc>(acc[i], h[i], m[i], lo[i]);
+    if constexpr (NV == 8) {
+      *reinterpret_cast<uint4*>(o) = *reinterpret_cast<const uint4*>(h);
+      *reinterpret_cast<uint4*>(o + plane) = *reinterpret_cast<const uint4*>(m);
+      *reinterpret_cast<uint4*>(o + 2 * plane) = *reinterpret_cast<const uint4*>(lo);
+    } else {
+      static_assert(NV == 4, "split3 stores: 4 or 8 values per lane");
+      *reinterpret_cast<uint2*>(o) = *reinterpret_cast<const uint2*>(h);
+      *reinterpret_cast<uint2*>(o + plane) = *reinterpret_cast<const uint2*>(m);
+      *reinterpret_cast<uint2*>(o + 2 * plane) = *reinterpret_cast<const uint2*>(lo);
     }
   }
 }
@@ -443,7 +449,9 @@ void sparse_rows_apply_split3(const SparseRows<V>& sp, const SparseGeom& g, cons
   if constexpr (sizeof(TI) != 2) A2_REQUIRE(in_plane == 0, "input planes need BF16 input");
   auto al = [](long long x) { return x % NV == 0; };
   if (!(al(g.veclen) && al(g.in_sw) && al(g.in_st) && al(g.in_b1) && al(g.in_b2) &&
-        al(in_plane) && reinterpret_cast<uintptr_t>(in) % 16 == 0)) {
+        al(in_plane) && reinterpret_cast<uintptr_t>(in) % 16 == 0 && al(g.out_sw) &&
+        al(g.out_ss) && al(g.out_b1) && al(g.out_b2) && al(plane) &&
+        reinterpret_cast<uintptr_t>(out) % (2 * NV) == 0)) {
     const int rows = std::min(64, std::max(1, 2048 / g.veclen));
     dim3 grid(cdiv(sp.nrows, rows), g.B1 * g.B2);
     A2_REQUIRE(grid.y < 65536, "sparse grid too large");

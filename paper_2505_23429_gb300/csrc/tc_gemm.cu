@@ -13,7 +13,10 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <map>
 #include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "tc_gemm.cuh"
 
@@ -746,6 +749,55 @@ void tc_gemm_bf16(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B,
   tc_gemm_bf16_pairs(Ap, lda, Bp, ldb, M, N, K, 1, p0, p0, C, ldc, out_kind, splitk, s);
 }
 
+namespace {
+
+// One GEMM configuration: the kernel variant (0: BN = 128 / 6 stages, 1: BN = 256 /
+// 4 stages, 2: promoted split products) and the number of K splits.
+struct TcConfig {
+  int variant = 1, splitk = 1;
+};
+
+void run_config(const TcConfig& cfg, const __nv_bfloat16* const* A, long long lda,
+                const __nv_bfloat16* const* B, long long ldb, int M, int N, int K, int npairs,
+                const int* pa, const int* pb, void* C, long long ldc, int out_kind,
+                cudaStream_t s, const TcSeg2* seg) {
+  if (cfg.variant == 2)
+    tc::launch<256, 4, true>(A, lda, B, ldb, M, N, K, npairs, pa, pb, seg, C, ldc, out_kind,
+                             cfg.splitk, s);
+  else if (cfg.variant == 0)
+    tc::launch<128, 6, false>(A, lda, B, ldb, M, N, K, npairs, pa, pb, seg, C, ldc, out_kind,
+                              cfg.splitk, s);
+  else
+    tc::launch<256, 4, false>(A, lda, B, ldb, M, N, K, npairs, pa, pb, seg, C, ldc, out_kind,
+                              cfg.splitk, s);
+}
+
+// Autotuner: the first call of a GEMM shape class (tile counts of M and N, K in steps of
+// 512, operand pairs, output kind, second segment) times the candidate configurations
+// with CUDA events on the caller's stream and keeps the fastest for every later call of
+// that class.  Candidates: the kernel
+// variants that apply (BN = 128 / 256; the promoted kernel for split products) and, for
+// accumulated outputs, the caller's K-split count, half and twice it.  Trials with an
+// accumulated output re-zero C first; the winner then runs on a zeroed C.
+struct TuneKey {
+  int M, N, K, npairs, out_kind, seg_rows;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(M, N, K, npairs, out_kind, seg_rows) <
+           std::tie(o.M, o.N, o.K, o.npairs, o.out_kind, o.seg_rows);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TcConfig> g_tune;
+bool g_tune_on = true;
+
+}  // namespace
+
+void tc_autotune(bool on) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune_on = on;
+  if (!on) g_tune.clear();
+}
+
 void tc_gemm_bf16_pairs(const __nv_bfloat16* const* A, long long lda,
                         const __nv_bfloat16* const* B, long long ldb, int M, int N, int K,
                         int npairs, const int* pa, const int* pb, void* C, long long ldc,
@@ -754,15 +806,62 @@ void tc_gemm_bf16_pairs(const __nv_bfloat16* const* A, long long lda,
   A2_REQUIRE(K >= 1 && npairs >= 1 && npairs <= 6, "tc GEMM: K >= 1, 1..6 operand pairs");
   if (splitk > 1)
     A2_REQUIRE(out_kind == tc::OUT_F32_ATOMIC, "split-K needs atomic FP32 output");
-  if (npairs > 1 && out_kind != tc::OUT_BF16)   // split-precision products: promoted sums
-    tc::launch<256, 4, true>(A, lda, B, ldb, M, N, K, npairs, pa, pb, seg, C, ldc, out_kind,
-                             splitk, s);
-  else if (N <= 128)
-    tc::launch<128, 6, false>(A, lda, B, ldb, M, N, K, npairs, pa, pb, seg, C, ldc, out_kind,
-                              splitk, s);
-  else
-    tc::launch<256, 4, false>(A, lda, B, ldb, M, N, K, npairs, pa, pb, seg, C, ldc, out_kind,
-                              splitk, s);
+  const bool promote = npairs > 1 && out_kind != tc::OUT_BF16;  // split products: promoted sums
+  TcConfig def;
+  def.variant = promote ? 2 : (N <= 128 ? 0 : 1);
+  def.splitk = splitk;
+  // shapes with the same tile counts (and K within 512) share one decision
+  const TuneKey key{(M + 127) / 128, (N + 127) / 128, (K + 511) / 512, npairs, out_kind,
+                    seg ? (seg->R1 * seg->Dr + 511) / 512 : 0};
+  bool tune = false;
+  TcConfig best = def;
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    if (g_tune_on) {
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) best = it->second;
+      else tune = true;
+    }
+  }
+  if (!tune) {
+    run_config(best, A, lda, B, ldb, M, N, K, npairs, pa, pb, C, ldc, out_kind, s, seg);
+    return;
+  }
+  std::vector<TcConfig> cand;
+  std::vector<int> variants = promote ? std::vector<int>{2} : std::vector<int>{0, 1};
+  std::vector<int> splits{splitk};
+  if (out_kind == tc::OUT_F32_ATOMIC) {
+    splits.push_back(splitk * 2);
+    if (splitk > 1) splits.push_back(std::max(1, splitk / 2));
+  }
+  for (int v : variants)
+    for (int k : splits) cand.push_back(TcConfig{v, k});
+  const size_t cbytes = (size_t)M * ldc * (out_kind == tc::OUT_BF16 ? 2 : 4);
+  cudaEvent_t e0, e1;
+  A2_CUDA(cudaEventCreate(&e0));
+  A2_CUDA(cudaEventCreate(&e1));
+  float best_ms = 1e30f;
+  for (const TcConfig& cf : cand) {
+    if (out_kind == tc::OUT_F32_ATOMIC) fill_zero(C, cbytes, s);
+    A2_CUDA(cudaEventRecord(e0, s));
+    run_config(cf, A, lda, B, ldb, M, N, K, npairs, pa, pb, C, ldc, out_kind, s, seg);
+    A2_CUDA(cudaEventRecord(e1, s));
+    A2_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    A2_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = cf;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune[key] = best;
+  }
+  if (out_kind == tc::OUT_F32_ATOMIC) fill_zero(C, cbytes, s);
+  run_config(best, A, lda, B, ldb, M, N, K, npairs, pa, pb, C, ldc, out_kind, s, seg);
 }
 
 // -------------------------------------------------------------- BF16 H_eff chain

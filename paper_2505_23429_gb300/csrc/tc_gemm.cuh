@@ -13,7 +13,8 @@ int tc_error_flag(bool reset);
 // C[m][n] (=|+=atomic) sum_k A[m][k] B[n][k]; A: M x K (row stride lda), B: N x K
 // (row stride ldb), both BF16 with 16-byte aligned bases and row strides that are
 // multiples of 8 elements.  out_kind: 0 = BF16 store, 1 = FP32 store, 2 = FP32 atomic
-// add (required when splitk > 1; C must be zeroed by the caller).
+// add (required when splitk > 1; C must be zeroed by the caller — the autotuner
+// re-zeroes it between its trials).  splitk is a hint the autotuner may change.
 void tc_gemm_bf16(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B, long long ldb,
                   int M, int N, int K, void* C, long long ldc, int out_kind, int splitk,
                   cudaStream_t s);
@@ -63,6 +64,9 @@ void tc_heff_f32emu(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int 
                     const __nv_bfloat16* Rp, long long ldr, long long rplane, const double* x,
                     float* y, const SparseRows<float>& W1, const SparseRows<float>& W2,
                     const HeffFold& F, DevBuf& t1, DevBuf& t2, DevBuf& xa, DevBuf& tf);
+
+// Enable (default) or disable the GEMM autotuner (disabling also forgets its choices).
+void tc_autotune(bool on);
 
 inline long long pad8(long long x) { return (x + 7) / 8 * 8; }
 
