@@ -21,9 +21,9 @@ The energy of the new iterate is its Rayleigh quotient (eq. energy_eig).
 import numpy as np
 
 from .coarse import coarse_solve
-from .env import env_left_update, heff_apply, left_envs, right_envs, sandwich
+from .env import env_left_update, heff1_apply, heff_apply, left_envs, right_envs, sandwich
 from .lanczos import lanczos_lowest
-from .tt import lq_pos, svd_split, tt_add, tt_inner, tt_round, tt_scale
+from .tt import lq_pos, qr_pos, svd_split, tt_add, tt_inner, tt_round, tt_scale
 
 
 def bond_groups(L, sizes):
@@ -98,6 +98,74 @@ def global_iteration(U, mpo, sizes, D_max, svd_tol=1e-10, eig_tol=1e-10,
     report = dict(energy=E_new, lambda_coarse=lam, coeffs=c, coarse_rank=p,
                   S_hat=S, A_hat=A, local_energies=local_e, krylov=kry,
                   max_discarded=disc_max, compression_discarded=disc_c,
+                  local_rayleigh=[A[g, g] / S[g, g] for g in range(1, m)],
+                  basis=basis)
+    return Unew, report
+
+
+def core_groups(L, sizes):
+    assert sum(sizes) == L, (sizes, L)
+    out, k = [], 0
+    for s in sizes:
+        out.append((k, k + s - 1))
+        k += s
+    return out
+
+
+def global_iteration_onesite(U, mpo, sizes, D_max, svd_tol=1e-10, eig_tol=1e-10,
+                             coarse_eps=1e-10, max_krylov=40):
+    """One-site A2DMRG global iteration (Alg. 2, one-site case) with P groups of cores.
+
+    The cores 0..L-1 are split into P contiguous groups; inside a group the one-site
+    micro-steps run left to right as in Alg. 1 (one-site): the j-th step takes the
+    lowest eigenvector of the one-site H_eff of the current j-orthogonal TT, and unless
+    it is the group's last core it is orthogonalised (QR, diag R >= 0) and R is moved
+    into the next core (Alg. 1, step 2, one-site).  Ranks do not change.  P = L is
+    exactly Alg. 2 in the one-site case (coarse dimension L + 1), P = 1 a classical
+    one-site half-sweep.  Coarse problem and compression as in the two-site case.
+    """
+    L = len(U)
+    groups = core_groups(L, sizes)
+    V, C = orthogonal_copies(U)
+    HL = left_envs(U, mpo)
+    HR = right_envs(V, mpo, downto=1)
+    updated, local_e, kry = [], [], [0] * L
+    for kg, mg in groups:
+        Hl = HL[kg]
+        centre = C[kg]
+        new = {}
+        th = None
+        for j in range(kg, mg + 1):
+            mv = lambda v, Hl=Hl, j=j: heff1_apply(Hl, mpo[j], HR[j + 1], v)
+            th, x, nmv, _ = lanczos_lowest(mv, centre, tol=eig_tol, max_krylov=max_krylov)
+            kry[j] = nmv
+            if j < mg:
+                Dl, n, Dr = x.shape
+                Q, R = qr_pos(x.reshape(Dl * n, Dr))
+                new[j] = Q.reshape(Dl, n, -1)
+                Hl = env_left_update(Hl, new[j], mpo[j], new[j])
+                centre = np.tensordot(R, V[j + 1], axes=(1, 0))
+            else:
+                new[j] = x
+        Ug = list(U[:kg]) + [new[j] for j in range(kg, mg + 1)] + list(V[mg + 1:])
+        updated.append(Ug)
+        local_e.append(th)
+    basis = [list(U)] + updated
+    m = len(basis)
+    S = np.zeros((m, m))
+    A = np.zeros((m, m))
+    for i in range(m):
+        for j in range(i, m):
+            S[i, j] = S[j, i] = tt_inner(basis[i], basis[j])
+            A[i, j] = A[j, i] = sandwich(basis[i], mpo, basis[j])
+    c, lam, p = coarse_solve(A, S, coarse_eps)
+    X = tt_add(basis, c)
+    Unew, disc_c = tt_round(X, D_max, svd_tol)
+    Unew = tt_scale(Unew, 1.0 / np.sqrt(tt_inner(Unew, Unew)))
+    E_new = energy(Unew, mpo)
+    report = dict(energy=E_new, lambda_coarse=lam, coeffs=c, coarse_rank=p,
+                  S_hat=S, A_hat=A, local_energies=local_e, krylov=kry,
+                  compression_discarded=disc_c,
                   local_rayleigh=[A[g, g] / S[g, g] for g in range(1, m)],
                   basis=basis)
     return Unew, report

@@ -54,6 +54,15 @@ def heff_apply(HL, W1, W2, HR, x):
     return T
 
 
+def heff1_apply(HL, W, HR, x):
+    """One-site H_eff of the j-th one-site micro-iteration (Def. of the micro-iterations,
+    one-site case): y[a,s,b] = sum HL[a,w,a'] W[w,s,t,w'] HR[b,w',b'] x[a',t,b']."""
+    T = np.tensordot(HL, x, axes=(2, 0))                  # a w t b'
+    T = np.tensordot(T, W, axes=([1, 2], [0, 2]))         # a b' s w'
+    T = np.tensordot(T, HR, axes=([1, 3], [2, 1]))        # a s b
+    return T
+
+
 def heff_apply_entry(HL, W1, W2, HR, x, a, b):
     """The slice y[a, :, :, b] of heff_apply, contracted for that one pair of outer bond
     indices only (the same sum as above with a and b fixed), so that single outputs of a
