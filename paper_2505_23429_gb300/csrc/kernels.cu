@@ -268,6 +268,10 @@ __global__ void sparse_rows_kernel(SparseRows<V> sp, SparseGeom g, const TI* __r
   }
 }
 
+// Output rows per CTA of the vectorised kernels: the CTAs resident at one time then span
+// few batches, so the input rows they gather from stay in L2 between their uses.
+constexpr int kSparseRowsPerCta = 16;
+
 // Vectorised variant: each lane owns VEC consecutive vector elements (16-byte loads),
 // `lpr` lanes cover one row chunk of lpr*VEC elements, a warp serves 32/lpr rows at a
 // time.  Grid: x = row blocks, y = vector chunks, z = batch; consecutive CTAs share the
@@ -462,13 +466,13 @@ void sparse_rows_apply_split3(const SparseRows<V>& sp, const SparseGeom& g, cons
   }
   int lpr = 1;
   while (lpr < 32 && lpr * NV < g.veclen) lpr *= 2;
-  dim3 grid(cdiv(sp.nrows, 64), cdiv(g.veclen, lpr * NV), g.B1 * g.B2);
+  dim3 grid(cdiv(sp.nrows, kSparseRowsPerCta), cdiv(g.veclen, lpr * NV), g.B1 * g.B2);
   A2_REQUIRE(grid.y < 65536 && grid.z < 65536, "sparse grid too large");
   auto kern = in_plane ? (add ? sparse_rows_split3_kernel<TI, V, true, true>
                                : sparse_rows_split3_kernel<TI, V, true, false>)
                       : (add ? sparse_rows_split3_kernel<TI, V, false, true>
                              : sparse_rows_split3_kernel<TI, V, false, false>);
-  kern<<<grid, 256, 0, s>>>(sp, g, in, in_plane, add, out, plane, lpr, 64);
+  kern<<<grid, 256, 0, s>>>(sp, g, in, in_plane, add, out, plane, lpr, kSparseRowsPerCta);
   A2_CHECK_LAUNCH();
 }
 template void sparse_rows_apply_split3<float, float>(const SparseRows<float>&, const SparseGeom&,
@@ -558,7 +562,7 @@ void sparse_rows_apply(const SparseRows<V>& sp, const SparseGeom& g, const TI* i
     int lpr = 1;
     while (lpr < 32 && lpr * NV < g.veclen) lpr *= 2;
     const int chunks = cdiv(g.veclen, lpr * NV);
-    const int rows = 64;
+    const int rows = kSparseRowsPerCta;
     dim3 grid(cdiv(sp.nrows, rows), chunks, g.B1 * g.B2);
     A2_REQUIRE(grid.y < 65536 && grid.z < 65536, "sparse grid too large");
     if (g.accumulate)
