@@ -26,6 +26,31 @@ from .lanczos import lanczos_lowest
 from .tt import lq_pos, qr_pos, svd_split, tt_add, tt_inner, tt_round, tt_scale
 
 
+def lowest_eigvecs(matvec, x0, K):
+    """The K lowest eigenpairs of the symmetric local operator `matvec` (Extension One
+    of the extension remark after Alg. 2: keep the K lowest eigenvectors of the local
+    problem instead of one).  Plain definition: the dense matrix of the operator (column
+    i = the operator applied to the i-th unit tensor) and its full eigendecomposition,
+    ascending.  Sign: <x_k, x0> >= 0, as for the Lanczos solution.  K is capped at the
+    local dimension."""
+    shape = x0.shape
+    N = x0.size
+    K = min(K, N)
+    H = np.empty((N, N))
+    for i in range(N):
+        e = np.zeros(N)
+        e[i] = 1.0
+        H[:, i] = matvec(e.reshape(shape)).ravel()
+    w, X = np.linalg.eigh(0.5 * (H + H.T))
+    xs = []
+    for k in range(K):
+        x = X[:, k]
+        if x @ x0.ravel() < 0:
+            x = -x
+        xs.append(x.reshape(shape))
+    return list(w[:K]), xs
+
+
 def bond_groups(L, sizes):
     assert sum(sizes) == L - 1, (sizes, L)
     out, k = [], 0
@@ -55,7 +80,11 @@ def energy(U, mpo):
 
 
 def global_iteration(U, mpo, sizes, D_max, svd_tol=1e-10, eig_tol=1e-10,
-                     coarse_eps=1e-10, max_krylov=40):
+                     coarse_eps=1e-10, max_krylov=40, n_eig=1):
+    """n_eig = K > 1: Extension One.  The last micro-step of every group keeps its K
+    lowest eigenvectors; each gives one updated TT (its own truncated SVD), so the coarse
+    space has K*P + 1 vectors, ordered [iterate, group 0 (lowest first), group 1, ...];
+    local_energies then lists the K eigenvalues of every group in the same order."""
     L = len(U)
     groups = bond_groups(L, sizes)
     V, C = orthogonal_copies(U)
@@ -67,10 +96,21 @@ def global_iteration(U, mpo, sizes, D_max, svd_tol=1e-10, eig_tol=1e-10,
         centre = C[kg]
         new = {}
         th = None
+        extra = []
         for k in range(kg, mg + 1):
             x0 = np.tensordot(centre, V[k + 1], axes=(2, 0))
             mv = lambda v, Hl=Hl, k=k: heff_apply(Hl, mpo[k], mpo[k + 1], HR[k + 2], v)
-            th, x, nmv, _ = lanczos_lowest(mv, x0, tol=eig_tol, max_krylov=max_krylov)
+            if n_eig > 1 and k == mg:
+                ths, xs = lowest_eigvecs(mv, x0, n_eig)
+                th, x, nmv = ths[0], xs[0], x0.size
+                for th_e, x_e in zip(ths[1:], xs[1:]):
+                    Dl, n1, n2, Dr = x_e.shape
+                    P, s, Q, disc = svd_split(x_e.reshape(Dl * n1, n2 * Dr), D_max, svd_tol)
+                    disc_max = max(disc_max, disc)
+                    extra.append((th_e, [P.reshape(Dl, n1, -1),
+                                         (s[:, None] * Q).reshape(-1, n2, Dr)]))
+            else:
+                th, x, nmv, _ = lanczos_lowest(mv, x0, tol=eig_tol, max_krylov=max_krylov)
             kry[k] = nmv
             Dl, n1, n2, Dr = x.shape
             P, s, Q, disc = svd_split(x.reshape(Dl * n1, n2 * Dr), D_max, svd_tol)
@@ -82,6 +122,10 @@ def global_iteration(U, mpo, sizes, D_max, svd_tol=1e-10, eig_tol=1e-10,
         Ug = list(U[:kg]) + [new[k] for k in range(kg, mg + 2)] + list(V[mg + 2:])
         updated.append(Ug)
         local_e.append(th)
+        for th_e, tail in extra:
+            updated.append(list(U[:kg]) + [new[k] for k in range(kg, mg)] + tail
+                           + list(V[mg + 2:]))
+            local_e.append(th_e)
     basis = [list(U)] + updated
     m = len(basis)
     S = np.zeros((m, m))
@@ -113,7 +157,7 @@ def core_groups(L, sizes):
 
 
 def global_iteration_onesite(U, mpo, sizes, D_max, svd_tol=1e-10, eig_tol=1e-10,
-                             coarse_eps=1e-10, max_krylov=40):
+                             coarse_eps=1e-10, max_krylov=40, n_eig=1):
     """One-site A2DMRG global iteration (Alg. 2, one-site case) with P groups of cores.
 
     The cores 0..L-1 are split into P contiguous groups; inside a group the one-site
@@ -123,6 +167,8 @@ def global_iteration_onesite(U, mpo, sizes, D_max, svd_tol=1e-10, eig_tol=1e-10,
     into the next core (Alg. 1, step 2, one-site).  Ranks do not change.  P = L is
     exactly Alg. 2 in the one-site case (coarse dimension L + 1), P = 1 a classical
     one-site half-sweep.  Coarse problem and compression as in the two-site case.
+    n_eig = K > 1: Extension One, the K lowest eigenvectors of every group's last core
+    each replace that core (coarse dimension K*P + 1, ordered as in global_iteration).
     """
     L = len(U)
     groups = core_groups(L, sizes)
@@ -135,9 +181,15 @@ def global_iteration_onesite(U, mpo, sizes, D_max, svd_tol=1e-10, eig_tol=1e-10,
         centre = C[kg]
         new = {}
         th = None
+        extra = []
         for j in range(kg, mg + 1):
             mv = lambda v, Hl=Hl, j=j: heff1_apply(Hl, mpo[j], HR[j + 1], v)
-            th, x, nmv, _ = lanczos_lowest(mv, centre, tol=eig_tol, max_krylov=max_krylov)
+            if n_eig > 1 and j == mg:
+                ths, xs = lowest_eigvecs(mv, centre, n_eig)
+                th, x, nmv = ths[0], xs[0], centre.size
+                extra = list(zip(ths[1:], xs[1:]))
+            else:
+                th, x, nmv, _ = lanczos_lowest(mv, centre, tol=eig_tol, max_krylov=max_krylov)
             kry[j] = nmv
             if j < mg:
                 Dl, n, Dr = x.shape
@@ -150,6 +202,10 @@ def global_iteration_onesite(U, mpo, sizes, D_max, svd_tol=1e-10, eig_tol=1e-10,
         Ug = list(U[:kg]) + [new[j] for j in range(kg, mg + 1)] + list(V[mg + 1:])
         updated.append(Ug)
         local_e.append(th)
+        for th_e, x_e in extra:
+            updated.append(list(U[:kg]) + [new[j] for j in range(kg, mg)] + [x_e]
+                           + list(V[mg + 1:]))
+            local_e.append(th_e)
     basis = [list(U)] + updated
     m = len(basis)
     S = np.zeros((m, m))
