@@ -427,8 +427,8 @@ def main():
 
 
 def matvec_compare(a2, ctx, mpo, cores, cfg, torch, stream):
-    """H_eff applications at full bond dimension: the tensor-core chains (BF16 and
-    FP32-accurate split products), the FP64 SIMT chain, and a plain torch.tensordot
+    """H_eff applications at full bond dimension: the tensor-core chains (BF16,
+    FP32-accurate split products, FP64 emulation), the FP64 SIMT chain, and a plain torch.tensordot
     chain of the same contraction in BF16 with the dense MPO cores (cuBLAS), at the
     hand-over bond of the operator automaton and at a typical middle bond."""
     L, D, n = cfg["L"], cfg["D"], cfg["n"]
@@ -459,12 +459,17 @@ def matvec_compare(a2, ctx, mpo, cores, cfg, torch, stream):
 
         res = dict(bond=k, D=D, R=[int(W1.shape[0]), int(W1.shape[3]), int(W2.shape[3])],
                    nnz=[int(np.count_nonzero(W1)), int(np.count_nonzero(W2))], alg_flops=flops)
-        for prec, reps in (("bf16", 10), ("f32emu", 10), ("fp64", 1)):
+        ys = {}
+        for prec, reps in (("bf16", 10), ("f32emu", 10), ("f64emu", 3), ("fp64", 1)):
             op = a2.HeffOp(ctx, mpo, k, HL, HR, prec=prec)
             ms = timeit(lambda: op.apply(x, y), reps)
             op.close()
+            ys[prec] = y.clone()
             res[f"{prec}_ms"] = ms
             res[f"{prec}_tflops"] = flops / (ms * 1e-3) / 1e12
+        ref = ys["fp64"]
+        for prec in ("bf16", "f32emu", "f64emu"):   # accuracy against the FP64 SIMT chain
+            res[f"{prec}_rel_err"] = float((ys[prec] - ref).norm() / ref.norm())
         with torch.cuda.stream(stream):
             Lb, Rb, xb = HL.bfloat16(), HR.bfloat16(), x.bfloat16()
             W1b = torch.from_numpy(W1).cuda().bfloat16()

@@ -52,8 +52,12 @@ typedef enum {
                   coarse eigensolve in FP64 */
   A2_TF32 = 2, /* reserved */
   A2_FP32 = 3, /* every contraction in FP32 (SIMT), vectors / SVD / coarse in FP64 */
-  A2_F32EMU = 4 /* H_eff on tcgen05 with FP32-accurate products: operands split into
+  A2_F32EMU = 4, /* H_eff on tcgen05 with FP32-accurate products: operands split into
                    three BF16 slices, six slice pairs accumulated in FP32 */
+  A2_F64EMU = 5  /* H_eff to FP64 accuracy on tcgen05 (Ozaki scheme): FP64 operands split
+                   row-wise into eight 7-bit BF16 slices, the 36 slice pairs of level
+                   <= 9 accumulated exactly in FP32 per level and K chunk, levels summed
+                   in FP64; sparse MPO stages, environments, vectors in FP64 */
 } a2_precision;
 
 typedef struct a2_ctx a2_ctx;
@@ -132,21 +136,49 @@ typedef struct {
                                   preconditioner (same stopping rule, fewer matvecs) */
   int group_streams;           /* 0 = the P groups run concurrently (one host thread and
                                   CUDA stream each), 1 = one after another */
+  int one_site;                /* 0 = two-site A2DMRG (groups of bonds, partition sums to
+                                  L-1); 1 = the one-site case of Alg. 2: P groups of cores
+                                  (partition sums to L), one-site micro-steps with QR between
+                                  the cores of a group, no rank change in the local steps,
+                                  compression of the rank-2r structured sum; the local
+                                  contractions run on the SIMT path (FP64, or FP32 for the
+                                  mixed precisions); krylov_iters then has L entries */
+  int n_eig;                   /* K: 0 or 1 = one eigenvector per local problem; K > 1 =
+                                  Extension One (extension remark after Alg. 2): the last
+                                  local problem of every group keeps its K lowest
+                                  eigenvectors (the lowest by the usual solve, the others by
+                                  Lanczos on the operator deflated by those found), each
+                                  giving one updated TT (two-site: its own truncated SVD),
+                                  so the coarse space has up to K*P + 1 <= 63 vectors and
+                                  the compression rounds their block-diagonal sum.  Not
+                                  allowed in a2_classical_sweep. */
+  int env_mode;                /* 0 = every environment built once per iteration and kept
+                                  (storage O(d r^2 R)); 1 = memory-limited mode (the
+                                  paper's cost discussion of the micro-iterations): no
+                                  environment is kept, each local problem and each coarse
+                                  entry rebuilds the two it needs from the chain ends
+                                  (storage O(r^2 R), O(d) more environment updates);
+                                  results agree to the rounding of the precision */
 } a2_sweep_opts;
 
 typedef struct {
   double energy_in;            /* Rayleigh quotient of the input iterate (A_hat_00/S_hat_00) */
   double lambda_coarse;        /* lowest eigenvalue of the coarse problem */
-  double* energy_local;        /* [P] caller-owned or NULL: last Ritz value of each group */
-  double* coeffs;              /* [P+1] caller-owned or NULL: coarse coefficients c */
-  double* S_hat;               /* [(P+1)^2] caller-owned or NULL */
-  double* A_hat;               /* [(P+1)^2] caller-owned or NULL */
+  double* energy_local;        /* [m-1] caller-owned or NULL: last Ritz value of each group
+                                  (with n_eig > 1: the group's eigenvalues, ascending, group
+                                  after group) */
+  double* coeffs;              /* [m] caller-owned or NULL: coarse coefficients c */
+  double* S_hat;               /* [m*m] caller-owned or NULL */
+  double* A_hat;               /* [m*m] caller-owned or NULL; m = P + 1, or up to
+                                  n_eig*P + 1 with n_eig > 1 (size the arrays for that) */
   int coarse_rank;             /* p, numerical rank of S_hat */
-  int* krylov_iters;           /* [L-1] caller-owned or NULL: matvecs per bond */
+  int* krylov_iters;           /* [L-1] ([L] one-site) caller-owned or NULL: matvecs per
+                                  bond (per core) */
   double max_discarded_weight; /* largest discarded 2-norm over the SVD steps */
   double seconds;              /* wall time of the call */
   double alg_flops;            /* algorithmic flops of the contractions performed */
   long long matvecs;           /* H_eff applications in the call */
+  int coarse_dim;              /* m, the number of coarse basis vectors used */
 } a2_sweep_report;
 
 /* One global iteration of two-site A2DMRG (Alg. 2, with P groups of adjoining
@@ -259,7 +291,8 @@ a2_status a2_device_error(a2_ctx* ctx, int reset, int* code_out);
  * 1 = enable, 2 = reset totals, 3 = read the totals of `kind` (0 tcgen05 S1,
  * 1 sparse S2, 2 sparse S3, 3 tcgen05 S4, 4 SIMT H_eff, 5 environment update,
  * 6 Lanczos vector work, 7 truncated SVD, 8 LQ/QR, 9-12 the four stages of the
- * FP32-accurate split-product H_eff) into the host outputs
+ * FP32-accurate split-product H_eff, 13-16 the FP64-emulated H_eff: S1, the sparse
+ * stages, S4, the operand slicing) into the host outputs
  * (launches, milliseconds, algorithmic flops, algorithmic bytes; any may be NULL).
  * op 4 returns in *launches the number of kernel launches this library has made
  * since the process started (all of its own kernels, library calls excluded). */

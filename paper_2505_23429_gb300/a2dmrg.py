@@ -14,7 +14,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liba2dmrg.so")
 
-PRECISION = {"fp64": 0, "bf16": 1, "tf32": 2, "fp32": 3, "f32emu": 4}
+PRECISION = {"fp64": 0, "bf16": 1, "tf32": 2, "fp32": 3, "f32emu": 4, "f64emu": 5}
 STATUS = {0: "A2_OK", -1: "A2_EINVAL", -2: "A2_ENOMEM", -3: "A2_ECUDA", -4: "A2_ENOCONV",
           -5: "A2_ENUMERIC", -6: "A2_ETIMEOUT", -7: "A2_EUNSUPPORTED"}
 
@@ -31,7 +31,8 @@ class SweepOpts(ctypes.Structure):
                 ("eig_tol", ctypes.c_double), ("coarse_eps", ctypes.c_double),
                 ("max_krylov", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("prec", ctypes.c_int), ("refine_f64", ctypes.c_int), ("solver", ctypes.c_int),
-                ("group_streams", ctypes.c_int)]
+                ("group_streams", ctypes.c_int), ("one_site", ctypes.c_int),
+                ("n_eig", ctypes.c_int), ("env_mode", ctypes.c_int)]
 
 
 class SweepReport(ctypes.Structure):
@@ -43,7 +44,8 @@ class SweepReport(ctypes.Structure):
                 ("coarse_rank", ctypes.c_int),
                 ("krylov_iters", ctypes.POINTER(ctypes.c_int)),
                 ("max_discarded_weight", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("alg_flops", ctypes.c_double), ("matvecs", ctypes.c_longlong)]
+                ("alg_flops", ctypes.c_double), ("matvecs", ctypes.c_longlong),
+                ("coarse_dim", ctypes.c_int)]
 
 
 _lib = None
@@ -269,7 +271,8 @@ class MPO:
 
 
 def _opts(L, P, partition, D_max, svd_tol, eig_tol, coarse_eps, max_krylov, max_restarts, prec,
-          refine, solver="lanczos", sequential=False):
+          refine, solver="lanczos", sequential=False, one_site=False, n_eig=1,
+          low_memory=False):
     o = SweepOpts()
     o.P = P
     part = None
@@ -282,19 +285,27 @@ def _opts(L, P, partition, D_max, svd_tol, eig_tol, coarse_eps, max_krylov, max_
     o.refine_f64 = refine
     o.solver = {"lanczos": 0, "davidson": 1}[solver]
     o.group_streams = 1 if sequential else 0
+    o.one_site = 1 if one_site else 0
+    o.n_eig = n_eig
+    o.env_mode = 1 if low_memory else 0
     return o, part
 
 
 def _sweep(fn, ctx, tt, mpo, P, partition=None, D_max=64, svd_tol=1e-10, eig_tol=1e-10,
            coarse_eps=1e-10, max_krylov=40, max_restarts=200, prec="fp64", refine=2,
-           solver="lanczos", sequential=False):
+           solver="lanczos", sequential=False, one_site=False, n_eig=1, low_memory=False):
+    """one_site=True: the one-site case of Alg. 2 (partition over the L cores);
+    n_eig = K > 1: Extension One (K eigenvectors of each group's last local problem);
+    low_memory=True: the memory-limited environment mode (environments rebuilt on
+    demand, none kept)."""
     L = len(tt.phys)
     o, part = _opts(L, P, partition, D_max, svd_tol, eig_tol, coarse_eps, max_krylov,
-                    max_restarts, prec, refine, solver, sequential)
-    m = P + 1
-    bufs = dict(energy_local=np.zeros(P), coeffs=np.zeros(m), S_hat=np.zeros(m * m),
+                    max_restarts, prec, refine, solver, sequential, one_site, n_eig,
+                    low_memory)
+    m = P * max(1, n_eig) + 1
+    bufs = dict(energy_local=np.zeros(m - 1), coeffs=np.zeros(m), S_hat=np.zeros(m * m),
                 A_hat=np.zeros(m * m))
-    kry = np.zeros(L - 1, dtype=np.int32)
+    kry = np.zeros(L if one_site else L - 1, dtype=np.int32)
     r = SweepReport()
     for k, v in bufs.items():
         setattr(r, k, _dp(v))
@@ -303,10 +314,12 @@ def _sweep(fn, ctx, tt, mpo, P, partition=None, D_max=64, svd_tol=1e-10, eig_tol
     out = dict(energy_in=r.energy_in, lambda_coarse=r.lambda_coarse, coarse_rank=r.coarse_rank,
                max_discarded=r.max_discarded_weight, seconds=r.seconds, alg_flops=r.alg_flops,
                matvecs=r.matvecs, krylov=kry.tolist())
-    out["energy_local"] = bufs["energy_local"]
-    out["coeffs"] = bufs["coeffs"]
-    out["S_hat"] = bufs["S_hat"].reshape(m, m)
-    out["A_hat"] = bufs["A_hat"].reshape(m, m)
+    m = r.coarse_dim
+    out["coarse_dim"] = m
+    out["energy_local"] = bufs["energy_local"][:m - 1]
+    out["coeffs"] = bufs["coeffs"][:m]
+    out["S_hat"] = bufs["S_hat"][:m * m].reshape(m, m)
+    out["A_hat"] = bufs["A_hat"][:m * m].reshape(m, m)
     return out
 
 
@@ -402,7 +415,8 @@ def device_error(ctx, reset=True):
 
 
 PROFILE_KINDS = ["tc_s1", "sparse_s2", "sparse_s3", "tc_s4", "heff_simt", "env", "lanczos",
-                 "svd", "lq", "emu_s1", "emu_s2", "emu_s3", "emu_s4"]
+                 "svd", "lq", "emu_s1", "emu_s2", "emu_s3", "emu_s4", "f64e_s1", "f64e_sparse",
+                 "f64e_s4", "f64e_split"]
 
 
 def profile(ctx, op, kind=0):

@@ -552,6 +552,53 @@ void heff_T(a2_ctx* c, const SiteOps& A1, const SiteOps& A2, const T* HL, const 
   }
 }
 
+// y = H_eff x for the one-site micro-step at core j (one-site case of Alg. 1 / Alg. 2):
+//   y[a,s,b] = sum HL[a,w,a'] A_j[w,s,t,w'] HR[b,w',b'] x[a',t,b']
+// as T1 = HL x (GEMM over a'), the MPO core on the rows (sparse), and the contraction
+// with HR over (w', b') (GEMM); compute type T.
+template <typename T>
+void heff1_T(a2_ctx* c, const SiteOps& so, const T* HL, const T* HR, int Dl, int Dr, const T* x,
+             T* y) {
+  const int n = so.n, Rl = so.Rl, Rr = so.Rr;
+  cudaStream_t s = c->stream;
+  ProfScope ps(PK_HEFF_SIMT, s, env_flops(so, Dl, Dr),
+               sizeof(T) * ((double)Dl * Rl * Dl + (double)Dr * Rr * Dr +
+                            2.0 * Dl * Rl * n * Dr + 2.0 * Dl * n * Rr * Dr));
+  c->t1.ensure(sizeof(T) * (size_t)Dl * Rl * n * Dr, s);
+  c->t2.ensure(sizeof(T) * (size_t)Dl * n * Rr * Dr, s);
+  T* T1 = c->t1.as<T>();
+  T* T2 = c->t2.as<T>();
+  {  // T1[(a w)][(t b')] = sum_a' HL[(a w)][a'] x[a'][(t b')]
+    SimtGemm<T, T> g;
+    g.M = Dl * Rl; g.N = n * Dr; g.K = Dl;
+    g.A = HL; g.sam = Dl; g.sak = 1;
+    g.B = x; g.sbn = 1; g.sbk = (long long)n * Dr;
+    g.C = T1; g.scm = (long long)n * Dr; g.scn = 1;
+    simt_gemm(g, s);
+  }
+  {  // T2[(a s)][(w' b')] = sum_{w,t} A[w,s,t,w'] T1[(a w)][(t b')]
+    SparseGeom gm;
+    gm.veclen = Dr;
+    gm.in_sw = (long long)n * Dr; gm.in_st = Dr;
+    gm.out_sw = Dr; gm.out_ss = (long long)Rr * Dr;
+    gm.B1 = Dl; gm.in_b1 = (long long)Rl * n * Dr; gm.out_b1 = (long long)n * Rr * Dr;
+    sparse_rows_apply<T, T, T>(so.lr.rows<T>(), gm, T1, T2, s);
+  }
+  {  // y[(a s)][b] = sum_{(w' b')} T2[(a s)][(w' b')] HR[b][(w' b')]
+    SimtGemm<T, T> g;
+    g.M = Dl * n; g.N = Dr; g.K = Rr * Dr;
+    g.A = T2; g.sam = g.K; g.sak = 1;
+    g.B = HR; g.sbn = g.K; g.sbk = 1;
+    g.C = y; g.scm = Dr; g.scn = 1;
+    g.splitk = pick_splitk(g.M, g.N, g.K, sizeof(T) == 8 ? 64 : 128);
+    if (g.splitk > 1) {
+      g.mode = GEMM_ATOMIC;
+      fill_zero(y, sizeof(T) * (size_t)g.M * g.N, s);
+    }
+    simt_gemm(g, s);
+  }
+}
+
 double heff_flops(const SiteOps& A1, const SiteOps& A2, int Dl, int Dr) {
   const double n1 = A1.n, n2 = A2.n;
   return 2.0 * n1 * n2 * Dl * Dr * (A1.Rl * (double)Dl + A2.Rr * (double)Dr) +
@@ -669,6 +716,100 @@ void heff_emu(a2_ctx* c, const SiteOps& A1, const SiteOps& A2, const Bf16Envs& E
   convert<float, double>(c->ya.as<float>(), y, N, c->stream);
 }
 
+// FP64 environments as Ozaki slices (kOzSlices BF16 planes each) for the FP64-emulated
+// H_eff: L [(a w)][a'] (rows Dl*Rl, K = Dl), R [b][(w2 b')] (rows Dr, K = Rr*Dr).
+struct OzEnvs {
+  DevBuf buf;
+  const __nv_bfloat16* L = nullptr;
+  const __nv_bfloat16* R = nullptr;
+  long long ldl = 0, ldr = 0, lplane = 0, rplane = 0;
+  void set(a2_ctx* c, const double* Lf, int Dl, int Rl, const double* Rf, int Dr, int Rr) {
+    cudaStream_t s = c->stream;
+    ProfScope ps(PK_F64E_SPLIT, s, 0.0,
+                 10.0 * ((double)Dl * Rl * Dl + (double)Dr * Rr * Dr) * 2.0);
+    ldl = pad8(Dl);
+    ldr = pad8((long long)Rr * Dr);
+    lplane = ((long long)Dl * Rl * ldl + 63) / 64 * 64;
+    rplane = ((long long)Dr * ldr + 63) / 64 * 64;
+    buf.ensure(sizeof(__nv_bfloat16) * (size_t)(kOzSlices * (lplane + rplane)), s);
+    __nv_bfloat16* lb = buf.as<__nv_bfloat16>();
+    __nv_bfloat16* rb = lb + kOzSlices * lplane;
+    ozaki_split(Lf, Dl, 1, Dl * Rl, Dl, lb, ldl, lplane, s);
+    ozaki_split(Rf, (long long)Rr * Dr, 1, Dr, Rr * Dr, rb, ldr, rplane, s);
+    L = lb;
+    R = rb;
+  }
+};
+
+// y = H_eff x to FP64 accuracy with the tensor-core stages S1 and S4 emulated by the
+// Ozaki scheme (tc_gemm_f64emu) and the sparse MPO stages S2, S3 in FP64; the full MPO
+// cores are used (no identity-block fold).
+void heff_f64emu(a2_ctx* c, const SiteOps& A1, const SiteOps& A2, const OzEnvs& E, int Dl,
+                 int Dr, const double* x, double* y) {
+  A2_REQUIRE(E.L && E.R, "FP64-emulation environments not set");
+  const int n1 = A1.n, n2 = A2.n, Rl = A1.Rl, R1 = A1.Rr, Rr = A2.Rr;
+  cudaStream_t s = c->stream;
+  const long long NX = (long long)n1 * n2 * Dr;
+  const long long ldx = pad8(Dl);
+  const long long xplane = (NX * ldx + 63) / 64 * 64;
+  const long long s1 = (long long)Dl * Rl * NX, s2 = (long long)Dl * R1 * NX;
+  const long long M4 = (long long)Dl * n1 * n2, K4 = (long long)Rr * Dr;
+  const long long s3 = M4 * K4;
+  const long long ld3 = pad8(K4);
+  const long long plane3 = (M4 * ld3 + 63) / 64 * 64;
+  c->xa.ensure(sizeof(__nv_bfloat16) * (size_t)(kOzSlices * xplane), s);
+  c->t1.ensure(sizeof(double) * (size_t)std::max(s1, s3), s);
+  c->t2.ensure(sizeof(double) * (size_t)s2, s);
+  c->t3.ensure(sizeof(__nv_bfloat16) * (size_t)(kOzSlices * plane3), s);
+  __nv_bfloat16* XT = c->xa.as<__nv_bfloat16>();
+  double* T1 = c->t1.as<double>();
+  double* T2 = c->t2.as<double>();
+  double* T3 = c->t1.as<double>();
+  __nv_bfloat16* T3p = c->t3.as<__nv_bfloat16>();
+  {  // slices of x^T: row n = column n of x [a'][(s1 s2 b')]
+    ProfScope ps(PK_F64E_SPLIT, s, 0.0, (8.0 + 2.0 * kOzSlices) * (double)NX * Dl);
+    ozaki_split(x, 1, NX, (int)NX, Dl, XT, ldx, xplane, s);
+  }
+  {  // S1: T1[(a w)][(s1 s2 b')] = sum_a' L[(a w)][a'] x[a'][(s1 s2 b')]
+    const double M = (double)Dl * Rl, N = (double)NX, K = Dl;
+    ProfScope ps(PK_F64E_S1, s, 2.0 * M * N * K,
+                 2.0 * kOzSlices * (M * K + N * K) + 8.0 * M * N);
+    tc_gemm_f64emu(E.L, E.ldl, E.lplane, XT, ldx, xplane, Dl * Rl, (int)NX, Dl, T1, NX, c->tf,
+                   s);
+  }
+  {  // S2 / S3 in FP64 on the full MPO cores
+    ProfScope ps(PK_F64E_SPARSE, s,
+                 2.0 * A1.lr.nnz * (double)n2 * Dr * Dl +
+                     2.0 * A2.lr.nnz * (double)Dr * Dl * n1,
+                 8.0 * (double)(s1 + 2 * s2 + s3));
+    SparseGeom g2;
+    g2.veclen = n2 * Dr;
+    g2.in_sw = NX; g2.in_st = (long long)n2 * Dr;
+    g2.out_sw = NX; g2.out_ss = (long long)n2 * Dr;
+    g2.B1 = Dl; g2.in_b1 = (long long)Rl * NX; g2.out_b1 = (long long)R1 * NX;
+    sparse_rows_apply<double, double, double>(A1.lr.rows<double>(), g2, T1, T2, s);
+    SparseGeom g3;
+    g3.veclen = Dr;
+    g3.in_sw = NX; g3.in_st = Dr;
+    g3.out_sw = Dr; g3.out_ss = K4;
+    g3.B1 = Dl; g3.B2 = n1;
+    g3.in_b1 = (long long)R1 * NX; g3.in_b2 = (long long)n2 * Dr;
+    g3.out_b1 = (long long)n1 * n2 * K4; g3.out_b2 = (long long)n2 * K4;
+    sparse_rows_apply<double, double, double>(A2.lr.rows<double>(), g3, T2, T3, s);
+  }
+  {
+    ProfScope ps(PK_F64E_SPLIT, s, 0.0, (8.0 + 2.0 * kOzSlices) * (double)s3);
+    ozaki_split(T3, K4, 1, (int)M4, (int)K4, T3p, ld3, plane3, s);
+  }
+  {  // S4: y[(a s1 s2)][b] = sum_{(w2 b')} T3[(a s1 s2)][(w2 b')] R[b][(w2 b')]
+    const double M = (double)M4, N = Dr, K = (double)K4;
+    ProfScope ps(PK_F64E_S4, s, 2.0 * M * N * K,
+                 2.0 * kOzSlices * (M * K + N * K) + 8.0 * M * N);
+    tc_gemm_f64emu(T3p, ld3, plane3, E.R, E.ldr, E.rplane, (int)M4, Dr, (int)K4, y, Dr, c->tf,
+                   s);
+  }
+}
+
 // ============================================================================= engine
 struct View {   // a TT as per-site device pointers and bond dims
   std::vector<const double*> core;
@@ -688,6 +829,7 @@ struct Engine {
   long long matvecs = 0, matvecs_bf16 = 0;
   DevBuf cvt_bra, cvt_ket;
   Bf16Envs bfe;
+  OzEnvs oze;   // FP64-emulation slices of the current local problem's environments
 
   Engine(a2_ctx* c_, const a2_mpo* m, a2_precision p) : c(c_), mpo(m), L(m->L), prec(p) {
     HL.resize(L + 1);
@@ -761,6 +903,28 @@ struct Engine {
   void matvec_emu(int k, int Dl, int Dr, const double* x, double* y) {
     heff_emu(c, mpo->site[k], mpo->site[k + 1], bfe, Dl, Dr, x, y);
     flops += heff_flops(mpo->site[k], mpo->site[k + 1], Dl, Dr);
+    ++matvecs;
+  }
+  // FP64-emulated H_eff at bond k with the environments set in oze
+  void matvec_f64e(int k, int Dl, int Dr, const double* x, double* y) {
+    heff_f64emu(c, mpo->site[k], mpo->site[k + 1], oze, Dl, Dr, x, y);
+    flops += heff_flops(mpo->site[k], mpo->site[k + 1], Dl, Dr);
+    ++matvecs;
+  }
+  // one-site H_eff at core j with FP64 vectors and envs HL_ / HR_ (T)
+  void matvec1(int j, const T* HL_, const T* HR_, int Dl, int Dr, const double* x, double* y) {
+    const SiteOps& A = mpo->site[j];
+    const long long N = (long long)Dl * A.n * Dr;
+    if constexpr (sizeof(T) == 8) {
+      heff1_T<double>(c, A, HL_, HR_, Dl, Dr, x, y);
+    } else {
+      c->xa.ensure(sizeof(float) * N, c->stream);
+      c->ya.ensure(sizeof(float) * N, c->stream);
+      convert<double, float>(x, c->xa.as<float>(), N, c->stream);
+      heff1_T<float>(c, A, HL_, HR_, Dl, Dr, c->xa.as<float>(), c->ya.as<float>());
+      convert<float, double>(c->ya.as<float>(), y, N, c->stream);
+    }
+    flops += env_flops(A, Dl, Dr);
     ++matvecs;
   }
 };
@@ -874,6 +1038,65 @@ LanczosResult lanczos(a2_ctx* c, MV&& mv, double* x, long long N, double tol, in
   const double sgn = dot_dev(c, x, x0, N, 5);
   if (sgn < 0) axpby(0.0, x, -1.0, x, N, s);
   return res;
+}
+
+// Extension One (extension remark after Alg. 2): the eigenpairs above the lowest of a
+// local operator, one at a time, by Lanczos on the deflated operator
+// (I - Q Q^T) H (I - Q Q^T) with Q the eigenvectors found so far, each started from
+// `start` with those directions removed.  On return Q (K x N, row-major) holds the
+// lowest eigenvector `x1` (normalised) in row 0 and the others below; the eigenvalues
+// of rows 1..K-1 are returned.  K is capped at N.
+template <class MV>
+std::vector<double> deflated_eigs(a2_ctx* c, MV&& mv, const double* start, const double* x1,
+                                  long long N, int K, double tol, int max_krylov,
+                                  int max_cycles, DevBuf& Q, int* matvecs) {
+  cudaStream_t s = c->stream;
+  K = (int)std::min<long long>(K, N);
+  A2_REQUIRE(K >= 1 && K <= 64, "n_eig: at most 64 eigenvectors per local problem");
+  Q.ensure(sizeof(double) * (size_t)K * N, s);
+  double* Qp = Q.as<double>();
+  DevBuf tmp;
+  tmp.ensure(sizeof(double) * (size_t)N, s);
+  double* coef = scal(c, 4200);
+  auto project = [&](double* v, int k) {   // v -= Q_k Q_k^T v, twice
+    for (int pass = 0; pass < 2; ++pass) {
+      dot_multi(Qp, N, k, v, N, c->partial.as<double>(), coef, s);
+      gemv_sub(Qp, N, k, coef, v, N, s);
+    }
+  };
+  auto normalise = [&](double* v) {
+    dot_multi(v, 0, 1, v, N, c->partial.as<double>(), scal(c, 4290), s);
+    scale_dev(v, nullptr, scal(c, 4290), N, s);
+  };
+  A2_CUDA(cudaMemcpyAsync(Qp, x1, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  normalise(Qp);
+  const double s2 = dot_dev(c, start, start, N, 6);
+  std::vector<double> th;
+  for (int e = 1; e < K; ++e) {
+    double* v = Qp + (size_t)e * N;
+    A2_CUDA(cudaMemcpyAsync(v, start, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    project(v, e);
+    if (!(dot_dev(c, v, v, N, 6) > 1e-16 * s2)) {   // start inside span(Q): a fixed vector
+      std::vector<double> h((size_t)N);
+      for (long long i = 0; i < N; ++i) h[i] = std::sin(0.7 * (double)i + 0.3 * e);
+      A2_CUDA(cudaMemcpyAsync(v, h.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
+      A2_CUDA(cudaStreamSynchronize(s));
+      project(v, e);
+    }
+    auto mvd = [&](const double* in, double* out) {
+      A2_CUDA(cudaMemcpyAsync(tmp.p, in, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+      project(tmp.as<double>(), e);
+      mv(tmp.as<double>(), out);
+      project(out, e);
+    };
+    LanczosResult lr = lanczos(c, mvd, v, N, tol, max_krylov, max_cycles);
+    check_finite(lr.theta, "local eigenvalue (deflated)");
+    project(v, e);
+    normalise(v);
+    th.push_back(lr.theta);
+    *matvecs += lr.matvecs;
+  }
+  return th;
 }
 
 // Diagonal of H_eff at bond k (FP64): diag[a,s1,s2,b] = sum_{w,w1,w2} L[a,w,a]
@@ -1083,27 +1306,35 @@ void tt_check(const a2_tt* tt) {
   A2_REQUIRE(tt->dims[0] == 1 && tt->dims[tt->L] == 1, "TT boundary bonds must be 1");
 }
 
+// Thin QR of M (rows x cols, row-major, FP64): M = Q R with Q (rows x k) orthonormal
+// columns and R (k x cols), k = min(rows, cols), computed as the LQ factorisation of M^T.
+// Q and R are allocated here; returns k.
+int qr_split_dev(a2_ctx* c, const double* M, int rows, int cols, DevBuf& Q, DevBuf& R) {
+  cudaStream_t s = c->stream;
+  const int kk = std::min(rows, cols);
+  c->tmp2.ensure(sizeof(double) * ((size_t)rows * cols * 2 + (size_t)cols * kk), s);
+  double* Mt = c->tmp2.as<double>();
+  double* Lf = Mt + (size_t)rows * cols;
+  double* Qf = Lf + (size_t)cols * kk;
+  transpose2d<double, double>(M, Mt, rows, cols, s);
+  const int k = c->solver.lq(Mt, cols, rows, Lf, Qf, s);   // Mt = Lf (cols x k) Qf (k x rows)
+  Q.ensure(sizeof(double) * (size_t)rows * k, s);
+  transpose2d<double, double>(Qf, Q.as<double>(), k, rows, s);
+  R.ensure(sizeof(double) * (size_t)k * cols, s);
+  transpose2d<double, double>(Lf, R.as<double>(), cols, k, s);
+  return k;
+}
+
 void left_orthogonalize(a2_tt* tt, double* norm_out) {
   a2_ctx* c = tt->ctx;
   cudaStream_t s = c->stream;
   for (int j = 0; j + 1 < tt->L; ++j) {
     const int Dl = tt->dims[j], n = tt->phys[j], Dr = tt->dims[j + 1];
     const int rows = Dl * n;
-    // QR of (rows x Dr) = LQ of its transpose (Dr x rows)
-    c->tmp2.ensure(sizeof(double) * (size_t)rows * Dr * 3, s);
-    double* Mt = c->tmp2.as<double>();
-    double* Lf = Mt + (size_t)rows * Dr;
-    double* Qf = Lf + (size_t)Dr * Dr;
-    transpose2d<double, double>(tt->cores[j].as<double>(), Mt, rows, Dr, s);
-    const int k = c->solver.lq(Mt, Dr, rows, Lf, Qf, s);   // Mt = Lf (Dr x k) Qf (k x rows)
-    // core j = Qf^T (rows x k);  R = Lf^T (k x Dr);  core j+1 <- R core_{j+1}
-    DevBuf nc;
-    nc.ensure(sizeof(double) * (size_t)rows * k, s);
-    transpose2d<double, double>(Qf, nc.as<double>(), k, rows, s);
+    // core j = Q (rows x k);  core j+1 <- R core_{j+1}
+    DevBuf nc, Rm;
+    const int k = qr_split_dev(c, tt->cores[j].as<double>(), rows, Dr, nc, Rm);
     const int n2 = tt->phys[j + 1], Dr2 = tt->dims[j + 2];
-    DevBuf Rm;
-    Rm.ensure(sizeof(double) * (size_t)k * Dr, s);
-    transpose2d<double, double>(Lf, Rm.as<double>(), Dr, k, s);
     DevBuf nxt;
     nxt.ensure(sizeof(double) * (size_t)k * n2 * Dr2, s);
     matmul_dev(c, Rm.as<double>(), k, Dr, tt->cores[j + 1].as<double>(), n2 * Dr2,
@@ -1141,6 +1372,43 @@ struct Sweeper {
   const T* hl(int j) { return eng.HL[j].template as<T>(); }
   const T* hr(int j) { return eng.HR[j].template as<T>(); }
 
+  // Memory-limited environment mode (storage O(r^2 R) instead of O(d r^2 R), Sec. on
+  // the cost of the micro-iterations): no environment is kept between uses; the left
+  // environment of site j is rebuilt from the left end through U_0..U_{j-1}, the right
+  // one from the right end through V_{L-1}..V_j, on the engine (stream) of the caller.
+  // In the stored mode these return the environments built once by build_envs.
+  bool lazy() const { return o.env_mode == 1; }
+  const T* hl_at(int j, Engine<T>& e, DevBuf& buf) {
+    if (!lazy()) return hl(j);
+    cudaStream_t s = e.c->stream;
+    DevBuf a, b;
+    e.set_unit(a);
+    for (int i = 0; i < j; ++i) {
+      const int Dl = tt->dims[i], Dr = tt->dims[i + 1];
+      b.ensure(sizeof(T) * (size_t)Dr * mpo->R[i + 1] * Dr, s);
+      e.left_update(a.template as<T>(), i, tt->cores[i].as<double>(), Dl, Dr,
+                    tt->cores[i].as<double>(), Dl, Dr, b.template as<T>());
+      std::swap(a, b);
+    }
+    buf = std::move(a);
+    return buf.template as<T>();
+  }
+  const T* hr_at(int j, Engine<T>& e, DevBuf& buf) {
+    if (!lazy()) return hr(j);
+    cudaStream_t s = e.c->stream;
+    DevBuf a, b;
+    e.set_unit(a);
+    for (int i = L - 1; i >= j; --i) {
+      const int Dl = kd[i], Dr = kd[i + 1];
+      b.ensure(sizeof(T) * (size_t)Dl * mpo->R[i] * Dl, s);
+      e.right_update(a.template as<T>(), i, Vc[i].as<double>(), Dl, Dr, Vc[i].as<double>(), Dl,
+                     Dr, b.template as<T>());
+      std::swap(a, b);
+    }
+    buf = std::move(a);
+    return buf.template as<T>();
+  }
+
   // Step 1 of Alg. 2: right-to-left LQ sweep, every i-orthogonal copy.
   void step1() {
     cudaStream_t s = c->stream;
@@ -1172,6 +1440,7 @@ struct Sweeper {
   // Step 2 (first part): left envs from U, right envs from V.
   void build_envs() {
     cudaStream_t s = c->stream;
+    if (lazy()) return;   // memory-limited mode: built on demand (hl_at / hr_at)
     eng.set_unit(eng.HL[0]);
     eng.HLd[0] = 1;
     for (int j = 0; j + 1 < L; ++j) {
@@ -1192,12 +1461,20 @@ struct Sweeper {
     }
   }
 
+  // the last cores of a further updated TT of a group (Extension One): they replace the
+  // group's final cores mg+2-cores.size() .. mg+1
+  struct Tail {
+    std::vector<DevBuf> cores;
+    std::vector<int> dl, dr;
+    double theta = 0.0;
+  };
   struct Group {
     int kg, mg;
     std::vector<DevBuf> cores;   // new cores kg..mg+1 (mg - kg + 2 of them)
     std::vector<int> dl, dr;     // their bond dims
     double theta = 0.0;
     double disc = 0.0;           // largest discarded weight of the group's SVD steps
+    std::vector<Tail> extra;     // eigenvectors 2..K of the last local problem
   };
 
   // Step 2 (second part): the group's left-to-right two-site micro-steps, on the lane
@@ -1215,7 +1492,8 @@ struct Sweeper {
                               cudaMemcpyDeviceToDevice, s));
     }
     int cdim = kd[G.kg + 1];           // right bond of the centre
-    const T* HLcur = hl(G.kg);
+    DevBuf HLbuf, HRbuf;
+    const T* HLcur = hl_at(G.kg, eng, HLbuf);
     for (int k = G.kg; k <= G.mg; ++k) {
       const int n1 = tt->phys[k], n2 = tt->phys[k + 1];
       const int Dr = kd[k + 2];
@@ -1224,10 +1502,26 @@ struct Sweeper {
       x.ensure(sizeof(double) * N, s);
       matmul_dev(c, centre.as<double>(), Dl * n1, cdim, Vc[k + 1].as<double>(), n2 * Dr,
                  x.as<double>());
-      const T* HRk = hr(k + 2);
+      const T* HRk = hr_at(k + 2, eng, HRbuf);
+      if constexpr (sizeof(T) == 8) {   // FP64 emulation: slice the environments once
+        if (o.prec == A2_F64EMU)
+          eng.oze.set(c, HLcur, Dl, mpo->R[k], HRk, Dr, mpo->R[k + 2]);
+      }
       auto mv = [&](const double* in, double* out) {
+        if constexpr (sizeof(T) == 8) {
+          if (o.prec == A2_F64EMU) {
+            eng.matvec_f64e(k, Dl, Dr, in, out);
+            return;
+          }
+        }
         eng.matvec(k, HLcur, HRk, Dl, Dr, in, out);
       };
+      const bool ext = o.n_eig > 1 && k == G.mg;
+      DevBuf xstart;   // Extension One: start vector of the further eigenvectors
+      if (ext) {
+        xstart.ensure(sizeof(double) * N, s);
+        A2_CUDA(cudaMemcpyAsync(xstart.p, x.p, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+      }
       int nmv = 0;
       LanczosResult lr;
       bool done = false;
@@ -1274,6 +1568,47 @@ struct Sweeper {
       kry[k] = nmv + lr.matvecs;
       G.theta = lr.theta;
       const int rows = Dl * n1, cols = n2 * Dr;
+      if (ext) {
+        // the further eigenvectors on the accurate operator (FP32-accurate tensor-core
+        // products in the mixed modes), each truncated by its own SVD
+        auto mvx = [&](const double* in, double* out) {
+          if constexpr (sizeof(T) == 4) {
+            if (o.prec == A2_BF16 || o.prec == A2_F32EMU) {
+              eng.matvec_emu(k, Dl, Dr, in, out);
+              return;
+            }
+          }
+          mv(in, out);
+        };
+        DevBuf Qx;
+        int nx = 0;
+        std::vector<double> th = deflated_eigs(c, mvx, xstart.as<double>(), x.as<double>(), N,
+                                               o.n_eig, o.eig_tol, o.max_krylov, o.max_restarts,
+                                               Qx, &nx);
+        kry[k] += nx;
+        for (size_t e = 0; e < th.size(); ++e) {
+          Tail t;
+          t.theta = th[e];
+          DevBuf Pe, SQe;
+          Pe.ensure(sizeof(double) * (size_t)rows * std::min(rows, cols), s);
+          SQe.ensure(sizeof(double) * (size_t)std::min(rows, cols) * cols, s);
+          double de = 0.0;
+          int re = 0;
+          {
+            HiScope hs(c);
+            re = svd_split_dev(c, Qx.as<double>() + (size_t)(e + 1) * N, rows, cols, o.D_max,
+                               o.svd_tol, Pe.as<double>(), SQe.as<double>(), &de);
+          }
+          G.disc = std::max(G.disc, de);
+          t.cores.push_back(std::move(Pe));
+          t.dl.push_back(Dl);
+          t.dr.push_back(re);
+          t.cores.push_back(std::move(SQe));
+          t.dl.push_back(re);
+          t.dr.push_back(Dr);
+          G.extra.push_back(std::move(t));
+        }
+      }
       const int kmax = std::min(rows, cols);
       DevBuf P, SQ;
       P.ensure(sizeof(double) * (size_t)rows * kmax, s);
@@ -1319,7 +1654,89 @@ struct Sweeper {
     }
     return v;
   }
-  View group_view(const Group& G) {
+  // Step 2, one-site case: the group's cores first..last (G.kg .. G.mg + 1) in order; each
+  // local problem is the one-site H_eff of the current orthogonal TT, warm-started from its
+  // centre core; between the cores of the group the new core is orthogonalised (thin QR,
+  // ranks unchanged) and the triangular factor moves into the next core, with the
+  // group-local left environment updated (Alg. 1, one-site, step 2).
+  void solve_group1(Group& G, a2_ctx* c, Engine<T>& eng) {
+    cudaStream_t s = c->stream;
+    const int first = G.kg, last = G.mg + 1;
+    DevBuf Hloc, centre;
+    int Dl = tt->dims[first];
+    {
+      const size_t nb = (size_t)Dl * tt->phys[first] * kd[first + 1];
+      centre.ensure(sizeof(double) * nb, s);
+      A2_CUDA(cudaMemcpyAsync(centre.p, Cc[first].p, sizeof(double) * nb,
+                              cudaMemcpyDeviceToDevice, s));
+    }
+    DevBuf HLbuf, HRbuf;
+    const T* HLcur = hl_at(first, eng, HLbuf);
+    for (int j = first; j <= last; ++j) {
+      const int n = tt->phys[j], Dr = kd[j + 1];
+      const long long N = (long long)Dl * n * Dr;
+      const T* HRj = hr_at(j + 1, eng, HRbuf);
+      auto mv = [&](const double* in, double* out) { eng.matvec1(j, HLcur, HRj, Dl, Dr, in, out); };
+      const bool ext = o.n_eig > 1 && j == last;
+      DevBuf xstart;
+      if (ext) {
+        xstart.ensure(sizeof(double) * N, s);
+        A2_CUDA(cudaMemcpyAsync(xstart.p, centre.p, sizeof(double) * N, cudaMemcpyDeviceToDevice,
+                                s));
+      }
+      LanczosResult lr = lanczos(c, mv, centre.as<double>(), N, o.eig_tol, o.max_krylov,
+                                 o.max_restarts);
+      check_finite(lr.theta, "local eigenvalue");
+      kry[j] = lr.matvecs;
+      G.theta = lr.theta;
+      if (ext) {   // Extension One: each further eigenvector replaces the last core
+        DevBuf Qx;
+        int nx = 0;
+        std::vector<double> th = deflated_eigs(c, mv, xstart.as<double>(), centre.as<double>(),
+                                               N, o.n_eig, o.eig_tol, o.max_krylov,
+                                               o.max_restarts, Qx, &nx);
+        kry[j] += nx;
+        for (size_t e = 0; e < th.size(); ++e) {
+          Tail t;
+          t.theta = th[e];
+          DevBuf xe;
+          xe.ensure(sizeof(double) * N, s);
+          A2_CUDA(cudaMemcpyAsync(xe.p, Qx.as<double>() + (size_t)(e + 1) * N,
+                                  sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+          t.cores.push_back(std::move(xe));
+          t.dl.push_back(Dl);
+          t.dr.push_back(Dr);
+          G.extra.push_back(std::move(t));
+        }
+      }
+      if (j == last) {
+        G.cores.push_back(std::move(centre));
+        G.dl.push_back(Dl);
+        G.dr.push_back(Dr);
+        break;
+      }
+      DevBuf P, SQ;   // x = P SQ: P left-orthonormal, SQ moves into the next core
+      const int r = qr_split_dev(c, centre.as<double>(), Dl * n, Dr, P, SQ);
+      DevBuf Hn;
+      Hn.ensure(sizeof(T) * (size_t)r * mpo->R[j + 1] * r, s);
+      eng.left_update(HLcur, j, P.as<double>(), Dl, r, P.as<double>(), Dl, r, Hn.template as<T>());
+      Hloc = std::move(Hn);
+      HLcur = Hloc.template as<T>();
+      G.cores.push_back(std::move(P));
+      G.dl.push_back(Dl);
+      G.dr.push_back(r);
+      // next centre: (S Q) V_{j+1}
+      const int n2 = tt->phys[j + 1], Dr2 = kd[j + 2];
+      DevBuf next;
+      next.ensure(sizeof(double) * (size_t)r * n2 * Dr2, s);
+      matmul_dev(c, SQ.as<double>(), r, Dr, Vc[j + 1].as<double>(), n2 * Dr2, next.as<double>());
+      centre = std::move(next);
+      Dl = r;
+    }
+  }
+
+  // updated TT e of group G (0: the lowest eigenvector; e >= 1: Extension One's tails)
+  View group_view(const Group& G, int e = 0) {
     View v;
     v.core.resize(L); v.Dl.resize(L); v.Dr.resize(L);
     for (int j = 0; j < L; ++j) {
@@ -1330,6 +1747,15 @@ struct Sweeper {
         v.core[j] = G.cores[q].template as<double>(); v.Dl[j] = G.dl[q]; v.Dr[j] = G.dr[q];
       } else {
         v.core[j] = Vc[j].as<double>(); v.Dl[j] = kd[j]; v.Dr[j] = kd[j + 1];
+      }
+    }
+    if (e > 0) {
+      const Tail& t = G.extra[e - 1];
+      const int first = G.mg + 2 - (int)t.cores.size();
+      for (size_t q = 0; q < t.cores.size(); ++q) {
+        v.core[first + q] = t.cores[q].template as<double>();
+        v.Dl[first + q] = t.dl[q];
+        v.Dr[first + q] = t.dr[q];
       }
     }
     return v;
@@ -1376,8 +1802,8 @@ struct Sweeper {
   // <bra, A ket> over sites lo..hi, closed by the iterate's envs HL[lo] and HR[hi+1]
   double sandwich_span(const View& bra, const View& ket, int lo, int hi) {
     cudaStream_t s = c->stream;
-    DevBuf E, En;
-    const T* Ecur = hl(lo);
+    DevBuf E, En, Hb;
+    const T* Ecur = hl_at(lo, eng, Hb);
     for (int j = lo; j <= hi; ++j) {
       En.ensure(sizeof(T) * (size_t)bra.Dr[j] * mpo->R[j + 1] * ket.Dr[j], s);
       eng.left_update(Ecur, j, bra.core[j], bra.Dl[j], bra.Dr[j], ket.core[j], ket.Dl[j],
@@ -1386,18 +1812,19 @@ struct Sweeper {
       Ecur = E.template as<T>();
     }
     const long long ne = (long long)bra.Dr[hi] * mpo->R[hi + 1] * ket.Dr[hi];
-    A2_REQUIRE(eng.HRd[hi + 1] == bra.Dr[hi] && eng.HRd[hi + 1] == ket.Dr[hi],
-               "sandwich: right env dims");
+    A2_REQUIRE(kd[hi + 1] == bra.Dr[hi] && kd[hi + 1] == ket.Dr[hi], "sandwich: right env dims");
+    DevBuf Rb;
+    const T* Rcur = hr_at(hi + 1, eng, Rb);
     // full contraction <E, HR[hi+1]> in FP64
     c->xa.ensure(sizeof(double) * ne * 2, s);
     double* e64 = c->xa.as<double>();
     double* r64 = e64 + ne;
     if constexpr (sizeof(T) == 8) {
       A2_CUDA(cudaMemcpyAsync(e64, Ecur, sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
-      A2_CUDA(cudaMemcpyAsync(r64, hr(hi + 1), sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
+      A2_CUDA(cudaMemcpyAsync(r64, Rcur, sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
     } else {
       convert<float, double>(Ecur, e64, ne, s);
-      convert<float, double>(hr(hi + 1), r64, ne, s);
+      convert<float, double>(Rcur, r64, ne, s);
     }
     return dot_dev(c, e64, r64, ne, 7);
   }
@@ -1444,29 +1871,40 @@ struct Sweeper {
     auto t0 = std::chrono::steady_clock::now();
     tt_check(tt);
     A2_REQUIRE(tt->phys == mpo->phys, "TT and MPO physical dims differ");
+    A2_REQUIRE(o.n_eig >= 0 && o.n_eig <= 64, "n_eig must be in 0..64");
+    A2_REQUIRE(o.env_mode == 0 || o.env_mode == 1, "env_mode must be 0 or 1");
+    A2_REQUIRE(!(classical && o.n_eig > 1), "n_eig > 1 (Extension One) needs the coarse step");
     std::vector<int> sizes;
+    const bool one = o.one_site != 0;
+    const int units = one ? L : L - 1;               // cores (one-site) or bonds (two-site)
     int P = classical ? 1 : o.P;
-    A2_REQUIRE(P >= 1 && P <= L - 1, "P must be in 1..L-1");
+    A2_REQUIRE(P >= 1 && P <= units, "P must be in 1..L-1 (1..L one-site)");
     if (!classical && o.bond_partition) {
       sizes.assign(o.bond_partition, o.bond_partition + P);
     } else {
-      for (int g = 0; g < P; ++g) sizes.push_back((L - 1) / P + (g < (L - 1) % P ? 1 : 0));
+      for (int g = 0; g < P; ++g) sizes.push_back(units / P + (g < units % P ? 1 : 0));
     }
-    A2_REQUIRE(std::accumulate(sizes.begin(), sizes.end(), 0) == L - 1,
-               "bond partition must sum to L-1");
+    A2_REQUIRE(std::accumulate(sizes.begin(), sizes.end(), 0) == units,
+               one ? "core partition must sum to L" : "bond partition must sum to L-1");
     for (int x : sizes) A2_REQUIRE(x >= 1, "empty group");
     A2_REQUIRE(o.D_max >= 1, "D_max >= 1");
     A2_REQUIRE(o.max_krylov >= 2 && o.max_krylov <= 63, "max_krylov in 2..63");
-    kry.assign(L - 1, 0);
+    kry.assign(units, 0);
     step1();
     build_envs();
+    // groups as blocks of modified cores [kg, mg + 1]: two-site, bonds kg..mg; one-site,
+    // cores kg..mg + 1
     std::vector<Group> groups(P);
     int k0 = 0;
     for (int g = 0; g < P; ++g) {
       groups[g].kg = k0;
-      groups[g].mg = k0 + sizes[g] - 1;
+      groups[g].mg = k0 + sizes[g] - 1 - (one ? 1 : 0);
       k0 += sizes[g];
     }
+    auto solve = [&](Group& G, a2_ctx* lc, Engine<T>& e) {
+      if (one) solve_group1(G, lc, e);
+      else solve_group(G, lc, e);
+    };
     const int nl = (P > 1 && o.group_streams != 1) ? concurrent_lanes(P) : 1;
     if (nl > 1) {
       // the groups are independent (Alg. 2 step 2): nl host threads, each with its own
@@ -1483,7 +1921,7 @@ struct Sweeper {
             A2_CUDA(cudaSetDevice(c->device));
             a2_ctx* lc = lane(c, i);
             for (int g = next.fetch_add(1); g < P; g = next.fetch_add(1))
-              solve_group(groups[g], lc, *engs[i]);
+              solve(groups[g], lc, *engs[i]);
             A2_CUDA(cudaStreamSynchronize(lc->stream));
           } catch (...) {
             errs[i] = std::current_exception();
@@ -1499,10 +1937,17 @@ struct Sweeper {
         eng.matvecs_bf16 += e->matvecs_bf16;
       }
     } else {
-      for (int g = 0; g < P; ++g) solve_group(groups[g], c, eng);
+      for (int g = 0; g < P; ++g) solve(groups[g], c, eng);
     }
     for (auto& G : groups) max_disc = std::max(max_disc, G.disc);
-    const int m = P + 1;
+    // coarse basis: the iterate, then every group's updated TTs (Extension One: the
+    // further eigenvectors follow the lowest one of their group)
+    struct Item { int g, e; };
+    std::vector<Item> items;
+    for (int g = 0; g < P; ++g)
+      for (int e = 0; e <= (int)groups[g].extra.size(); ++e) items.push_back({g, e});
+    const int m = (int)items.size() + 1;
+    A2_REQUIRE(m <= 63, "coarse dimension (P * n_eig + 1) above 63");
     std::vector<double> S((size_t)m * m, 0.0), A((size_t)m * m, 0.0);
     // iterate: its (L-1)-orthogonal form is the stored left-orthogonal TT
     {
@@ -1510,21 +1955,22 @@ struct Sweeper {
       S[0] = overlap_span(b, b, L - 1, L - 1);
       A[0] = sandwich_span(b, b, L - 1, L - 1);
     }
-    std::vector<View> gv(P);
-    for (int g = 0; g < P; ++g) gv[g] = group_view(groups[g]);
-    for (int g = 0; g < P; ++g) {
-      const int lo = groups[g].kg, hi = groups[g].mg + 1;
+    std::vector<View> gv(m - 1);
+    for (int a = 0; a + 1 < m; ++a) gv[a] = group_view(groups[items[a].g], items[a].e);
+    for (int a = 0; a + 1 < m; ++a) {
+      const Group& Ga = groups[items[a].g];
+      const int lo = Ga.kg, hi = Ga.mg + 1;
       View b = base_view(lo);
-      S[(size_t)(g + 1)] = S[(size_t)(g + 1) * m] = overlap_span(b, gv[g], lo, hi);
-      A[(size_t)(g + 1)] = A[(size_t)(g + 1) * m] = sandwich_span(b, gv[g], lo, hi);
-      S[(size_t)(g + 1) * m + g + 1] = overlap_span(gv[g], gv[g], lo, hi);
-      A[(size_t)(g + 1) * m + g + 1] = sandwich_span(gv[g], gv[g], lo, hi);
-      for (int h = g + 1; h < P; ++h) {
-        const int hi2 = groups[h].mg + 1;
-        const double sv = overlap_span(gv[g], gv[h], lo, hi2);
-        const double av = sandwich_span(gv[g], gv[h], lo, hi2);
-        S[(size_t)(g + 1) * m + h + 1] = S[(size_t)(h + 1) * m + g + 1] = sv;
-        A[(size_t)(g + 1) * m + h + 1] = A[(size_t)(h + 1) * m + g + 1] = av;
+      S[(size_t)(a + 1)] = S[(size_t)(a + 1) * m] = overlap_span(b, gv[a], lo, hi);
+      A[(size_t)(a + 1)] = A[(size_t)(a + 1) * m] = sandwich_span(b, gv[a], lo, hi);
+      S[(size_t)(a + 1) * m + a + 1] = overlap_span(gv[a], gv[a], lo, hi);
+      A[(size_t)(a + 1) * m + a + 1] = sandwich_span(gv[a], gv[a], lo, hi);
+      for (int b2 = a + 1; b2 + 1 < m; ++b2) {
+        const int hi2 = groups[items[b2].g].mg + 1;
+        const double sv = overlap_span(gv[a], gv[b2], lo, hi2);
+        const double av = sandwich_span(gv[a], gv[b2], lo, hi2);
+        S[(size_t)(a + 1) * m + b2 + 1] = S[(size_t)(b2 + 1) * m + a + 1] = sv;
+        A[(size_t)(a + 1) * m + b2 + 1] = A[(size_t)(b2 + 1) * m + a + 1] = av;
       }
     }
     for (double v : S) check_finite(v, "S_hat");
@@ -1558,7 +2004,13 @@ struct Sweeper {
     {
       std::vector<DevBuf> X;
       std::vector<int> xd;
-      structured_sum(groups, cvec, X, xd);
+      if (m == P + 1) {
+        structured_sum(groups, cvec, X, xd);
+      } else {   // Extension One: block-diagonal sum of all m terms
+        std::vector<View> terms(1, base_view(L - 1));
+        terms.insert(terms.end(), gv.begin(), gv.end());
+        plain_sum(terms, cvec, X, xd);
+      }
       round_into_tt(X, xd);
     }
     if (rep) {
@@ -1566,7 +2018,11 @@ struct Sweeper {
       rep->lambda_coarse = lam;
       rep->coarse_rank = prank;
       if (rep->energy_local)
-        for (int g = 0; g < P; ++g) rep->energy_local[g] = groups[g].theta;
+        for (int a = 0; a + 1 < m; ++a) {
+          const Group& Ga = groups[items[a].g];
+          rep->energy_local[a] = items[a].e == 0 ? Ga.theta : Ga.extra[items[a].e - 1].theta;
+        }
+      rep->coarse_dim = m;
       if (rep->coeffs) std::copy(cvec.begin(), cvec.end(), rep->coeffs);
       if (rep->S_hat) std::copy(S.begin(), S.end(), rep->S_hat);
       if (rep->A_hat) std::copy(A.begin(), A.end(), rep->A_hat);
@@ -1595,10 +2051,10 @@ struct Sweeper {
     std::vector<int> dP(L + 1, 0), dA(L + 1, 0), dS(L + 1, 0);
     xd.assign(L + 1, 1);
     for (int l = 1; l < L; ++l) {
-      A2_REQUIRE(act[l] >= 0, "structured sum: bond without an active group");
-      const Group& G = groups[act[l]];
+      // two-site blocks cover every bond; one-site blocks leave the bonds between groups
+      // without an active channel
       dP[l] = tt->dims[l];
-      dA[l] = G.dl[l - G.kg];
+      dA[l] = act[l] >= 0 ? groups[act[l]].dl[l - groups[act[l]].kg] : 0;
       dS[l] = (l > groups[0].mg + 1) ? kd[l] : 0;
       xd[l] = dP[l] + dA[l] + dS[l];
     }
@@ -1618,15 +2074,17 @@ struct Sweeper {
       // P -> P (or P -> end for the iterate, weighted by c_0)
       copy_block3(tt->cores[j].as<double>(), tt->dims[j], n, tt->dims[j + 1], dst, s0, s1, rP,
                   cP, last ? cvec[0] : 1.0, s);
-      // P -> A: a group opens at site j
+      // P -> A: a group opens at site j (P -> S for a one-core group)
       for (int g = 0; g < P; ++g)
         if (groups[g].kg == j) {
           const Group& G = groups[g];
-          copy_block3(G.cores[0].template as<double>(), G.dl[0], n, G.dr[0], dst, s0, s1, rP, cA,
-                      cvec[g + 1], s);
+          const int col = (G.mg + 1 == j && !last) ? cS : cA;
+          // at the last site this block shares rows and column with P -> end
+          copy_block3(G.cores[0].template as<double>(), G.dl[0], n, G.dr[0], dst, s0, s1, rP, col,
+                      cvec[g + 1], s, last);
         }
       // A -> A / A -> S / A -> end
-      if (j > 0) {
+      if (j > 0 && act[j] >= 0) {
         const Group& G = groups[act[j]];
         const int q = j - G.kg;
         const bool closes = (j == G.mg + 1);
@@ -2096,7 +2554,9 @@ static a2_status run_sweep(a2_ctx* c, a2_tt* t, const a2_mpo* m, const a2_sweep_
       A2_CUDA(cudaMemcpyAsync(saved[j].p, t->cores[j].p, t->cores[j].bytes,
                               cudaMemcpyDeviceToDevice, c->stream));
     }
-    if (o->prec == A2_FP64) {
+    if (o->prec == A2_FP64 || o->prec == A2_F64EMU) {
+      if (o->prec == A2_F64EMU && !tc_available())
+        throw ArgError("A2_F64EMU needs the tcgen05 path, which this build lacks");
       Sweeper<double> sw(c, t, m, *o);
       sw.run(rep, classical);
     } else if (o->prec == A2_FP32 || o->prec == A2_BF16 || o->prec == A2_F32EMU) {
@@ -2157,7 +2617,7 @@ a2_status a2_energy(a2_ctx* c, const a2_tt* t, const a2_mpo* m, a2_precision pre
   return guarded(c, [&] {
     tt_check(t);
     A2_REQUIRE(t->phys == m->phys, "TT and MPO physical dims differ");
-    if (prec == A2_FP64) *E = energy_T<double>(c, t, m, norm_out);
+    if (prec == A2_FP64 || prec == A2_F64EMU) *E = energy_T<double>(c, t, m, norm_out);
     else *E = energy_T<float>(c, t, m, norm_out);
   });
 }
@@ -2169,6 +2629,7 @@ struct a2_heff {
   a2_precision prec = A2_FP64;
   DevBuf env;          // FP64 / FP32 copies of L and R
   Bf16Envs bfe;        // BF16 / split planes (with folded blocks)
+  OzEnvs oze;          // Ozaki slices (FP64 emulation)
 };
 
 a2_status a2_heff_create(a2_ctx* c, const a2_mpo* m, int k, a2_precision prec, int Dl, int Dr,
@@ -2197,6 +2658,9 @@ a2_status a2_heff_create(a2_ctx* c, const a2_mpo* m, int k, a2_precision prec, i
     } else if (prec == A2_BF16 || prec == A2_F32EMU) {
       A2_REQUIRE(tc_available(), "this precision needs the tcgen05 path");
       h->bfe.set<double>(c, L, Dl, A1.Rl, R, Dr, A2.Rr, prec == A2_BF16 ? 1 : 3, &A1, &A2);
+    } else if (prec == A2_F64EMU) {
+      A2_REQUIRE(tc_available(), "this precision needs the tcgen05 path");
+      h->oze.set(c, L, Dl, A1.Rl, R, Dr, A2.Rr);
     } else {
       throw ArgError("unsupported precision");
     }
@@ -2229,6 +2693,8 @@ a2_status a2_heff_apply_op(a2_heff* h, const double* x, double* y) {
       convert<float, double>(c->ya.as<float>(), y, N, s);
     } else if (h->prec == A2_BF16) {
       heff_bf16(c, A1, A2, h->bfe, Dl, Dr, x, y);
+    } else if (h->prec == A2_F64EMU) {
+      heff_f64emu(c, A1, A2, h->oze, Dl, Dr, x, y);
     } else {
       heff_emu(c, A1, A2, h->bfe, Dl, Dr, x, y);
     }
@@ -2351,6 +2817,12 @@ a2_status a2_heff_apply(a2_ctx* c, const a2_mpo* m, int k, a2_precision prec, in
       if (prec == A2_BF16) heff_bf16(c, A1, A2, E, Dl, Dr, x, y);
       else heff_emu(c, A1, A2, E, Dl, Dr, x, y);
       A2_CUDA(cudaStreamSynchronize(s));
+    } else if (prec == A2_F64EMU) {
+      A2_REQUIRE(tc_available(), "this precision needs the tcgen05 path");
+      OzEnvs E;
+      E.set(c, L, Dl, A1.Rl, R, Dr, A2.Rr);
+      heff_f64emu(c, A1, A2, E, Dl, Dr, x, y);
+      A2_CUDA(cudaStreamSynchronize(s));
     } else {
       throw ArgError("unsupported precision");
     }
@@ -2367,7 +2839,7 @@ a2_status a2_env_update(a2_ctx* c, const a2_mpo* m, int j, int side, a2_precisio
     const SiteOps& so = m->site[j];
     cudaStream_t s = c->stream;
     const int n = so.n;
-    if (prec == A2_FP64) {
+    if (prec == A2_FP64 || prec == A2_F64EMU) {   // environment updates stay on FP64 SIMT
       if (side == 0) env_left<double>(c, so, in, bra, Dlb, Drb, ket, Dlk, Drk, out);
       else env_right<double>(c, so, in, bra, Dlb, Drb, ket, Dlk, Drk, out);
     } else {

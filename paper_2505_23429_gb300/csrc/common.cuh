@@ -98,6 +98,10 @@ enum ProfKind {
   PK_EMU_S2,         // sparse S2 in FP32 (accurate matvec)
   PK_EMU_S3,         // sparse S3 in FP32 with split BF16 output (accurate matvec)
   PK_EMU_S4,         // tcgen05 S4 with split products
+  PK_F64E_S1,        // FP64-emulated S1 (Ozaki level products + combine)
+  PK_F64E_SPARSE,    // FP64 sparse S2 + S3 of the emulated H_eff
+  PK_F64E_S4,        // FP64-emulated S4
+  PK_F64E_SPLIT,     // Ozaki slicing of operands
   PK_COUNT
 };
 void prof_enable(bool on);

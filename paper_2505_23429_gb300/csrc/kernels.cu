@@ -1302,22 +1302,24 @@ void scale_rows(double* M, int rows, int cols, const double* svals, cudaStream_t
 
 // dst[(o0 + i)*dst_s0 + j*dst_s1 + (o2 + k)] = alpha * src[(i*d1 + j)*d2 + k]
 __global__ void copy_block3_kernel(const double* src, int d0, int d1, int d2, double* dst,
-                                   long long s0, long long s1, int o0, int o2, double alpha) {
+                                   long long s0, long long s1, int o0, int o2, double alpha,
+                                   bool add) {
   const long long n = (long long)d0 * d1 * d2;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
     const int k = (int)(e % d2);
     const long long ij = e / d2;
     const int j = (int)(ij % d1), i = (int)(ij / d1);
-    dst[(long long)(o0 + i) * s0 + (long long)j * s1 + (o2 + k)] = alpha * src[e];
+    double* d = dst + (long long)(o0 + i) * s0 + (long long)j * s1 + (o2 + k);
+    *d = add ? *d + alpha * src[e] : alpha * src[e];
   }
 }
 void copy_block3(const double* src, int d0, int d1, int d2, double* dst, long long dst_s0,
-                 long long dst_s1, int o0, int o2, double alpha, cudaStream_t s) {
+                 long long dst_s1, int o0, int o2, double alpha, cudaStream_t s, bool add) {
   long long n = (long long)d0 * d1 * d2;
   if (!n) return;
   copy_block3_kernel<<<grid_for(n), 256, 0, s>>>(src, d0, d1, d2, dst, dst_s0, dst_s1, o0, o2,
-                                                 alpha);
+                                                 alpha, add);
   A2_CHECK_LAUNCH();
 }
 

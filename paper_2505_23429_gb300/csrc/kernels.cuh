@@ -141,8 +141,9 @@ void gather_axpy_atomic(const double* G, const long long* index, const long long
                         const double* factor, long long n, double* grad, cudaStream_t s);
 void sign_fix_qr(double* Q, int ldq, int rows, double* R, int ldr, int k, cudaStream_t s);
 void scale_rows(double* M, int rows, int cols, const double* svals, cudaStream_t s); // M[r,:]*=s[r]
-// TT-sum block copy: dst[(r0 + i)*ld_dst_r + ... ] = alpha * src
+// TT-sum block copy: dst[(o0 + i)*dst_s0 + j*dst_s1 + o2 + k] = alpha * src[i][j][k]
+// (added to dst when add is set)
 void copy_block3(const double* src, int d0, int d1, int d2, double* dst, long long dst_s0,
-                 long long dst_s1, int o0, int o2, double alpha, cudaStream_t s);
+                 long long dst_s1, int o0, int o2, double alpha, cudaStream_t s, bool add = false);
 
 }  // namespace a2

@@ -150,6 +150,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 
 enum OutKind { OUT_BF16 = 0, OUT_F32 = 1, OUT_F32_ATOMIC = 2 };
 
+constexpr int kMaxPlanes = 8;      // BF16 planes per operand (8: the FP64 level products)
+constexpr int kMaxPairs = 8;       // operand pairs accumulated into one tile
+
 struct TcArgs {
   int M, N, K;
   int nk1, nk2;            // K blocks of the plain product and of the optional second segment
@@ -160,8 +163,9 @@ struct TcArgs {
   long long ldc;
   int out_kind;
   int npairs;              // operand pairs accumulated into one tile (split precision)
-  int pa[6], pb[6];        // A / B plane of each pair
+  int pa[kMaxPairs], pb[kMaxPairs];   // A / B plane of each pair
   int tma_store;           // 1: epilogue through shared memory + TMA bulk tensor store
+  long long split_ld;      // > 0: K split sp stores its own FP32 tile at C + sp * split_ld
 };
 
 // Up to three BF16 planes per operand (a value split into high, middle and low parts).
@@ -169,8 +173,8 @@ struct TcArgs {
 // 64 x n12 x 1 x 128/n12, i.e. 128 rows (a, s12) x 64 b') and B as a 3D view
 // [b][w1][b'] (box 64 x 1 x BN); both land in shared memory exactly like the 2D boxes.
 struct TcMaps {
-  CUtensorMap a[3];
-  CUtensorMap b[3];
+  CUtensorMap a[kMaxPlanes];
+  CUtensorMap b[kMaxPlanes];
   CUtensorMap a2[3];
   CUtensorMap b2[3];
   CUtensorMap c;           // output (FP32 box 32 x 32 or BF16 box 64 x 32, 128B swizzle)
@@ -457,7 +461,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
     // plain stores of one 32 x 32 block through a 4 KB transpose buffer: row r, column c
     // lives at r * 32 + (c ^ r), so that both the row writes and the column reads below
     // touch 32 different banks
-    auto plain32 = [&](const float (&v)[32], int n0c, int row0) {
+    auto plain32 = [&](const float (&v)[32], int n0c, int row0, void* Cb) {
       float* stage = reinterpret_cast<float*>(wbuf);     // (used only without TMA stores)
 #pragma unroll
       for (int i = 0; i < 32; ++i) stage[lane * 32 + (i ^ lane)] = v[i];
@@ -467,15 +471,15 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
       if (col < args.N) {
         if (args.out_kind == OUT_BF16) {
           __nv_bfloat16* cp =
-              reinterpret_cast<__nv_bfloat16*>(args.C) + (long long)row0 * args.ldc + col;
+              reinterpret_cast<__nv_bfloat16*>(Cb) + (long long)row0 * args.ldc + col;
           for (int r = 0; r < nrow; ++r)
             cp[(long long)r * args.ldc] = __float2bfloat16_rn(stage[r * 32 + (lane ^ r)]);
         } else if (args.out_kind == OUT_F32_ATOMIC) {
-          float* cp = reinterpret_cast<float*>(args.C) + (long long)row0 * args.ldc + col;
+          float* cp = reinterpret_cast<float*>(Cb) + (long long)row0 * args.ldc + col;
           for (int r = 0; r < nrow; ++r)
             atomicAdd(cp + (long long)r * args.ldc, stage[r * 32 + (lane ^ r)]);
         } else {
-          float* cp = reinterpret_cast<float*>(args.C) + (long long)row0 * args.ldc + col;
+          float* cp = reinterpret_cast<float*>(Cb) + (long long)row0 * args.ldc + col;
           for (int r = 0; r < nrow; ++r) cp[(long long)r * args.ldc] = stage[r * 32 + (lane ^ r)];
         }
       }
@@ -514,7 +518,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
 #pragma unroll
             for (int i = 0; i < 32; ++i) v[i] = acc[c0 + i];
             if (args.tma_store) store32(v, col, row0);
-            else plain32(v, col, row0);
+            else plain32(v, col, row0, args.C);
           }
         }
       } else {
@@ -557,12 +561,15 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
             }
           }
         } else if (!args.tma_store) {
+          void* Cb = args.C;
+          if (args.split_ld > 0)
+            Cb = reinterpret_cast<float*>(args.C) + (long long)(u / (tiles_m * tiles_n)) * args.split_ld;
 #pragma unroll 1
           for (int c0 = 0; c0 < BN; c0 += 32) {
             if (n0 + c0 >= args.N) break;
             float v[32];
             tmem_ld32(tl + (uint32_t)c0, v);
-            plain32(v, n0 + c0, row0);
+            plain32(v, n0 + c0, row0, Cb);
           }
         }
         release();
@@ -629,20 +636,25 @@ CUtensorMap make_map_nd(const __nv_bfloat16* ptr, int rank, const cuuint64_t* di
   return m;
 }
 
+// Returns the number of K splits launched.  split_ld > 0: every split stores its own FP32
+// tile at C + sp * split_ld (plain stores), with at most `splitk`-derived K blocks each.
 template <int BN, int STAGES, bool PROMOTE>
-void launch(const __nv_bfloat16* const* A, long long lda, const __nv_bfloat16* const* B,
-            long long ldb, int M, int N, int K, int npairs, const int* pa, const int* pb,
-            const TcSeg2* seg, void* C, long long ldc, int out_kind, int splitk,
-            cudaStream_t s) {
+int launch(const __nv_bfloat16* const* A, long long lda, const __nv_bfloat16* const* B,
+           long long ldb, int M, int N, int K, int npairs, const int* pa, const int* pb,
+           const TcSeg2* seg, void* C, long long ldc, int out_kind, int splitk,
+           cudaStream_t s, long long split_ld = 0) {
+  A2_REQUIRE(npairs >= 1 && npairs <= kMaxPairs, "tc GEMM: 1..8 operand pairs");
   TcMaps maps;
   int na = 0, nb = 0;
   for (int p = 0; p < npairs; ++p) {
+    A2_REQUIRE(pa[p] >= 0 && pa[p] < kMaxPlanes && pb[p] >= 0 && pb[p] < kMaxPlanes,
+               "tc GEMM: plane index out of range");
     na = std::max(na, pa[p] + 1);
     nb = std::max(nb, pb[p] + 1);
   }
-  for (int i = 0; i < 3; ++i) {
-    maps.a[i] = make_map(A[i < na ? i : 0], M, K, lda, BM);
-    maps.b[i] = make_map(B[i < nb ? i : 0], N, K, ldb, BN);
+  for (int i = 0; i < kMaxPlanes; ++i) {
+    maps.a[i] = i < na || i == 0 ? make_map(A[i], M, K, lda, BM) : maps.a[0];
+    maps.b[i] = i < nb || i == 0 ? make_map(B[i], N, K, ldb, BN) : maps.b[0];
   }
   int nk2 = 0, nbc2 = 1, n12 = 1;
   if (seg) {
@@ -695,16 +707,18 @@ void launch(const __nv_bfloat16* const* A, long long lda, const __nv_bfloat16* c
   splitk = (nk_total + args.kblocks_per_split - 1) / args.kblocks_per_split;
   args.C = C; args.ldc = ldc; args.out_kind = out_kind;
   args.npairs = npairs;
-  for (int p = 0; p < 6; ++p) {
+  for (int p = 0; p < kMaxPairs; ++p) {
     args.pa[p] = p < npairs ? pa[p] : 0;
     args.pb[p] = p < npairs ? pb[p] : 0;
   }
   args.splits = splitk;
+  args.split_ld = split_ld;
+  A2_REQUIRE(split_ld == 0 || (out_kind == OUT_F32 && !PROMOTE), "split tiles: FP32 stores");
   // TMA store epilogue when C's base and row stride allow it
   {
     const size_t es = out_kind == OUT_BF16 ? 2 : 4;
     args.tma_store = ((reinterpret_cast<uintptr_t>(C) & 15) == 0 && (ldc * es) % 16 == 0 &&
-                      ldc >= N) ? 1 : 0;
+                      ldc >= N && split_ld == 0) ? 1 : 0;
     if (args.tma_store) {
       const cuuint64_t cd[2] = {(cuuint64_t)N, (cuuint64_t)M};
       const cuuint64_t cs[1] = {(cuuint64_t)(ldc * es)};
@@ -724,6 +738,7 @@ void launch(const __nv_bfloat16* const* A, long long lda, const __nv_bfloat16* c
   const int grid = (int)std::min<long long>(units, std::max(1, num_sms));
   tc_gemm_kernel<BN, STAGES, PROMOTE><<<grid, tc_threads(PROMOTE), smem, s>>>(maps, args);
   A2_CHECK_LAUNCH();
+  return splitk;
 }
 
 }  // namespace tc
@@ -1060,6 +1075,143 @@ void tc_heff_f32emu(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int 
                        tc::OUT_F32_ATOMIC, s4_splitk(M4, Dr, kb), s,
                        t2split ? &seg : nullptr);
   }
+}
+
+
+// ============================================================================ FP64 emulation
+// Ozaki scheme (Ozaki, Ogita, Oishi, Rump, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication and its applications",
+// Numer. Algorithms 59, 2012) on the BF16 tensor cores.  Every row r of an FP64 operand
+// is split into kOzSlices slices P_i[r][k] = q * 2^(e_r - kOzBits*i) with integer
+// |q| <= 2^kOzBits - 1 (truncation of the remainder; e_r = ilogb(max_k |X[r][k]|) + 1),
+// each exact in BF16.  A product of slice i of A with slice j of B is then an integer
+// multiple of the unit 2^(e_r + e_c - kOzBits*(i+j)) of magnitude below 2^(2*kOzBits);
+// all pairs of one level l = i + j share that unit, so a level's sum over at most
+// 1024 / (l - 1) K indices per pair stays an integer below 2^24 units and the tensor
+// cores' FP32 accumulation of it is exact.  The pairs with i + j <= kOzSlices + 1 are
+// kept (the rest lie below 2^-kOzBits*kOzSlices of |A||B|), every level's tile of every K
+// split is stored in FP32, and a combine kernel adds a level's tiles exactly in a pair of
+// FP32 numbers (error-free two-sum) and the levels in FP64, smallest first.
+namespace {
+
+__global__ void ozaki_split_kernel(const double* __restrict__ X, long long sr, long long sk,
+                                   int rows, int K, __nv_bfloat16* __restrict__ P, long long ldp,
+                                   long long plane) {
+  __shared__ double red[32];
+  __shared__ int e_sh;
+  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+    const double* xr = X + (long long)r * sr;
+    double mx = 0.0;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) mx = fmax(mx, fabs(xr[(long long)k * sk]));
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+      for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if (threadIdx.x == 0) e_sh = v > 0.0 ? ilogb(v) + 1 : 0;
+    }
+    __syncthreads();
+    const int e = e_sh;
+    __nv_bfloat16* pr = P + (long long)r * ldp;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      double rem = xr[(long long)k * sk];
+#pragma unroll
+      for (int i = 1; i <= kOzSlices; ++i) {
+        const int sh = e - kOzBits * i;
+        const double q = trunc(scalbn(rem, -sh));   // |q| < 2^kOzBits
+        const double pv = scalbn(q, sh);
+        rem -= pv;                                   // exact
+        pr[(long long)(i - 1) * plane + k] = __double2bfloat16(pv);   // exact
+      }
+    }
+    __syncthreads();   // red / e_sh are reused by the next row
+  }
+}
+
+// C[r][c] = sum over the level tiles: tile t of level lev[t] at T + t * MN (row-major,
+// N columns); tiles ordered by level (largest level last).
+struct LevEnd {
+  int e[kOzSlices];   // one past the last tile of each level
+};
+
+__global__ void ozaki_combine_kernel(const float* __restrict__ T, long long MN, int nt,
+                                     LevEnd lev_end, int nlev, int N, double* __restrict__ C,
+                                     long long ldc) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < MN;
+       e += (long long)gridDim.x * blockDim.x) {
+    double total = 0.0;
+    int t1 = nt;
+    for (int l = nlev - 1; l >= 0; --l) {   // smallest level first
+      const int t0 = l > 0 ? lev_end.e[l - 1] : 0;
+      float hi = 0.f, lo = 0.f;
+      for (int t = t0; t < t1; ++t) {       // error-free two-sum: hi + lo exact
+        const float v = T[(long long)t * MN + e];
+        const float s = __fadd_rn(hi, v);
+        const float bp = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(v, bp));
+        hi = s;
+        lo = __fadd_rn(lo, err);
+      }
+      total += (double)hi + (double)lo;
+      t1 = t0;
+    }
+    C[(e / N) * ldc + e % N] = total;
+  }
+}
+
+}  // namespace
+
+void ozaki_split(const double* X, long long sr, long long sk, int rows, int K, __nv_bfloat16* P,
+                 long long ldp, long long plane, cudaStream_t s) {
+  if (rows <= 0 || K <= 0) return;
+  const int grid = std::min(rows, 152 * 8);
+  ozaki_split_kernel<<<grid, 256, 0, s>>>(X, sr, sk, rows, K, P, ldp, plane);
+  A2_CHECK_LAUNCH();
+}
+
+void tc_gemm_f64emu(const __nv_bfloat16* A, long long lda, long long aplane,
+                    const __nv_bfloat16* B, long long ldb, long long bplane, int M, int N, int K,
+                    double* C, long long ldc, DevBuf& slab, cudaStream_t s) {
+  const int nk = (K + tc::BK - 1) / tc::BK;
+  const long long MN = (long long)M * N;
+  constexpr int nlev = kOzSlices;   // levels 2 .. kOzSlices + 1
+  long long ntiles = 0;
+  for (int l = 2; l <= kOzSlices + 1; ++l) {
+    const int kb = std::max(1, 16 / (l - 1));
+    ntiles += (nk + kb - 1) / kb;
+  }
+  slab.ensure(sizeof(float) * (size_t)(ntiles * MN), s);
+  float* T = slab.as<float>();
+  const __nv_bfloat16* Ap[tc::kMaxPlanes];
+  const __nv_bfloat16* Bp[tc::kMaxPlanes];
+  for (int i = 0; i < tc::kMaxPlanes; ++i) {
+    Ap[i] = A + i * aplane;
+    Bp[i] = B + i * bplane;
+  }
+  LevEnd lev_end;
+  long long t = 0;
+  for (int l = 2; l <= kOzSlices + 1; ++l) {
+    const int np = l - 1;
+    int pa[tc::kMaxPairs], pb[tc::kMaxPairs];
+    for (int i = 0; i < np; ++i) {   // slices (i + 1, l - i - 1) -> planes (i, np - 1 - i)
+      pa[i] = i;
+      pb[i] = np - 1 - i;
+    }
+    const int kb = std::max(1, 16 / np);
+    const int want = (nk + kb - 1) / kb;
+    const int got = N <= 128
+        ? tc::launch<128, 6, false>(Ap, lda, Bp, ldb, M, N, K, np, pa, pb, nullptr, T + t * MN,
+                                    N, tc::OUT_F32, want, s, MN)
+        : tc::launch<256, 4, false>(Ap, lda, Bp, ldb, M, N, K, np, pa, pb, nullptr, T + t * MN,
+                                    N, tc::OUT_F32, want, s, MN);
+    A2_REQUIRE(got >= 1 && got <= want, "FP64 emulation: unexpected K split");
+    t += got;
+    lev_end.e[l - 2] = (int)t;
+  }
+  const int grid = (int)std::min<long long>((MN + 255) / 256, 152LL * 16);
+  ozaki_combine_kernel<<<grid, 256, 0, s>>>(T, MN, (int)t, lev_end, nlev, N, C, ldc);
+  A2_CHECK_LAUNCH();
 }
 
 }  // namespace a2

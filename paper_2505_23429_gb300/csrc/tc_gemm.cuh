@@ -65,6 +65,20 @@ void tc_heff_f32emu(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int 
                     float* y, const SparseRows<float>& W1, const SparseRows<float>& W2,
                     const HeffFold& F, DevBuf& t1, DevBuf& t2, DevBuf& xa, DevBuf& tf);
 
+// FP64 emulation (Ozaki scheme with BF16 slices, see tc_gemm.cu).
+constexpr int kOzSlices = 8;   // slices per FP64 operand
+constexpr int kOzBits = 7;     // bits per slice
+// Split the FP64 matrix X (element (r, k) at X[r*sr + k*sk], rows x K) into kOzSlices BF16
+// planes P + i*plane, row r at P + i*plane + r*ldp (ldp % 8 == 0, 16-byte aligned P).
+void ozaki_split(const double* X, long long sr, long long sk, int rows, int K, __nv_bfloat16* P,
+                 long long ldp, long long plane, cudaStream_t s);
+// C (FP64, M x N, row stride ldc) = sum_k A[m][k] B[n][k] to FP64 accuracy from the split
+// planes of A (row stride lda, plane stride aplane) and B; slab is FP32 scratch for the
+// level tiles of every K split (grown as needed).
+void tc_gemm_f64emu(const __nv_bfloat16* A, long long lda, long long aplane,
+                    const __nv_bfloat16* B, long long ldb, long long bplane, int M, int N, int K,
+                    double* C, long long ldc, DevBuf& slab, cudaStream_t s);
+
 // Enable (default) or disable the GEMM autotuner (disabling also forgets its choices).
 void tc_autotune(bool on);
 
