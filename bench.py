@@ -42,7 +42,8 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--prec", default="bf16", choices=["bf16", "f32emu", "fp32", "fp64"])
+    p.add_argument("--prec", default="bf16",
+                   choices=["bf16", "f32emu", "fp32", "fp64", "f64emu"])
     p.add_argument("--solver", default="lanczos", choices=["lanczos", "davidson"])
     p.add_argument("--converge", type=int, default=45,
                    help="after the timed steps, keep iterating (up to this many iterations in "
@@ -67,6 +68,8 @@ def parse():
     p.add_argument("--bond", type=int, default=None,
                    help="bond of --profile-matvec (default: the one left of the middle)")
     p.add_argument("--reps", type=int, default=3)
+    p.add_argument("--f64emu", action="store_true",
+                   help="--profile-matvec also applies the FP64-emulated chain")
     return p.parse_args()
 
 
@@ -89,7 +92,7 @@ def sweep_kwargs(cfg, prec, solver="lanczos", coarse_eps=None):
     if coarse_eps is None:
         # the cut must sit above the relative accuracy of A_hat: FP64 entries for fp64,
         # FP32-accurate environments otherwise
-        coarse_eps = 1e-10 if prec == "fp64" else 1e-5
+        coarse_eps = 1e-10 if prec in ("fp64", "f64emu") else 1e-5
     return dict(partition=cfg["partition"], D_max=cfg["D"], svd_tol=1e-6, eig_tol=1e-6,
                 coarse_eps=coarse_eps, max_krylov=40, max_restarts=50, prec=prec,
                 solver=solver)
@@ -206,8 +209,8 @@ def est_iteration_flops(cfg, mpo, matvecs_per_bond=30):
 
 def profile_matvec(args):
     """H_eff at one bond of the L=16 chemistry MPO with random environments of bond
-    dimension --D: BF16 and FP32-accurate tensor-core chains (operator handles, the
-    environments converted once), --reps applications each."""
+    dimension --D: BF16, FP32-accurate and (with --f64emu) FP64-emulated tensor-core chains
+    (operator handles, the environments converted once), --reps applications each."""
     import torch
     import paper_2505_23429_gb300 as a2
     cfg, cores, _ = workload(args.config)
@@ -221,7 +224,7 @@ def profile_matvec(args):
     x = torch.randn(D, n, n, D, device="cuda", dtype=torch.float64, generator=g)
     y = torch.empty_like(x)
     torch.cuda.synchronize()
-    for prec in ("bf16", "f32emu"):
+    for prec in ("bf16", "f32emu") + (("f64emu",) if args.f64emu else ()):
         op = a2.HeffOp(ctx, mpo, k, HL, HR, prec=prec)
         for _ in range(args.reps):
             op.apply(x, y)
@@ -237,8 +240,12 @@ def class_roofline(name, d, peaks, prec):
     rate_b = d["bytes"] / (d["ms"] * 1e-3) / 1e9
     if name in ("tc_s1", "tc_s4", "emu_s1", "emu_s4"):
         return "tensor", "TFLOP/s", peaks["bf16_sus"], rate_f
-    if name in ("sparse_s2", "sparse_s3", "emu_s2", "emu_s3", "lanczos"):
+    if name in ("sparse_s2", "sparse_s3", "emu_s2", "emu_s3", "lanczos", "f64e_split"):
         return "hbm", "GB/s", peaks["hbm"], rate_b
+    if name in ("f64e_s1", "f64e_s4"):   # 36 BF16 products per FP64-equivalent flop
+        return "tensor", "TFLOP/s", peaks["bf16_sus"], 36.0 * rate_f
+    if name == "f64e_sparse":
+        return "alu", "TFLOP/s", FP32_SIMT_PEAK_TFLOPS, rate_f
     if name == "env" and prec in ("bf16", "f32emu"):
         return "tensor", "TFLOP/s", peaks["bf16_sus"], rate_f
     if name in ("heff_simt", "env") and prec != "fp64":

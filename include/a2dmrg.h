@@ -54,10 +54,12 @@ typedef enum {
   A2_FP32 = 3, /* every contraction in FP32 (SIMT), vectors / SVD / coarse in FP64 */
   A2_F32EMU = 4, /* H_eff on tcgen05 with FP32-accurate products: operands split into
                    three BF16 slices, six slice pairs accumulated in FP32 */
-  A2_F64EMU = 5  /* H_eff to FP64 accuracy on tcgen05 (Ozaki scheme): FP64 operands split
-                   row-wise into eight 7-bit BF16 slices, the 36 slice pairs of level
-                   <= 9 accumulated exactly in FP32 per level and K chunk, levels summed
-                   in FP64; sparse MPO stages, environments, vectors in FP64 */
+  A2_F64EMU = 5  /* H_eff to FP64-class accuracy (~2^-48) on tcgen05 (Ozaki scheme): FP64
+                   operands split row-wise into eight 7-bit BF16 slices, the 36 slice
+                   pairs of level <= 9 accumulated exactly in FP32 per level and K chunk,
+                   the partial tiles summed by error-free two-sums into FP32 pairs; the
+                   sparse MPO stages in double-float (FP32 pairs); environments, vectors,
+                   SVD and coarse problem in FP64 */
 } a2_precision;
 
 typedef struct a2_ctx a2_ctx;

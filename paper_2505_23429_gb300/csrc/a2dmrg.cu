@@ -68,7 +68,7 @@ struct SiteOps {
   long long nnz_g = 0;
   struct Part {
     int nrows = 0, nnz = 0;
-    DevBuf ptr, rw, rs, nw, nt, v64, v32;
+    DevBuf ptr, rw, rs, nw, nt, v64, v32, v32lo;
     template <typename V> SparseRows<V> rows() const {
       SparseRows<V> r;
       r.nrows = nrows;
@@ -80,6 +80,7 @@ struct SiteOps {
       r.nnz_total = nnz;
       if constexpr (sizeof(V) == 8) r.nz_val = v64.as<double>();
       else r.nz_val = v32.as<float>();
+      r.nz_lo = v32lo.as<float>();
       return r;
     }
   } lr, rl;
@@ -134,7 +135,7 @@ void build_part(SiteOps::Part& part, const std::vector<std::vector<std::array<do
   part.nrows = (int)rows.size();
   std::vector<int> ptr(rows.size() + 1, 0), rw, rs, nw, nt;
   std::vector<double> v64;
-  std::vector<float> v32;
+  std::vector<float> v32, v32lo;
   for (size_t r = 0; r < rows.size(); ++r) {
     rw.push_back(rowid[r].first);
     rs.push_back(rowid[r].second);
@@ -143,6 +144,7 @@ void build_part(SiteOps::Part& part, const std::vector<std::vector<std::array<do
       nt.push_back((int)e[1]);
       v64.push_back(e[2]);
       v32.push_back((float)e[2]);
+      v32lo.push_back((float)(e[2] - (double)(float)e[2]));
     }
     ptr[r + 1] = (int)nw.size();
   }
@@ -154,6 +156,7 @@ void build_part(SiteOps::Part& part, const std::vector<std::vector<std::array<do
   upload(part.nt, nt.data(), nt.size() * sizeof(int), s);
   upload(part.v64, v64.data(), v64.size() * sizeof(double), s);
   upload(part.v32, v32.data(), v32.size() * sizeof(float), s);
+  upload(part.v32lo, v32lo.data(), v32lo.size() * sizeof(float), s);
 }
 
 // Scan a dense core W[wl][s][t][wr] (minus `sub` = I (x) G when given) into the two
@@ -741,9 +744,10 @@ struct OzEnvs {
   }
 };
 
-// y = H_eff x to FP64 accuracy with the tensor-core stages S1 and S4 emulated by the
-// Ozaki scheme (tc_gemm_f64emu) and the sparse MPO stages S2, S3 in FP64; the full MPO
-// cores are used (no identity-block fold).
+// y = H_eff x to FP64-class accuracy: the tensor-core stages S1 and S4 emulated by the
+// Ozaki scheme (tc_gemm_f64emu), the sparse MPO stages S2, S3 in double-float arithmetic
+// (FP32 pairs, ~2^-48; the FP64 pipe of this GPU is ~60x slower than its FP32 pipe);
+// the full MPO cores are used (no identity-block fold).
 void heff_f64emu(a2_ctx* c, const SiteOps& A1, const SiteOps& A2, const OzEnvs& E, int Dl,
                  int Dr, const double* x, double* y) {
   A2_REQUIRE(E.L && E.R, "FP64-emulation environments not set");
@@ -757,13 +761,15 @@ void heff_f64emu(a2_ctx* c, const SiteOps& A1, const SiteOps& A2, const OzEnvs& 
   const long long s3 = M4 * K4;
   const long long ld3 = pad8(K4);
   const long long plane3 = (M4 * ld3 + 63) / 64 * 64;
+  // T1 and T2 as FP32 pairs (hi plane, lo plane), T3 in FP64 (the slicing input)
+  const long long p1 = (s1 + 3) / 4 * 4, p2 = (s2 + 3) / 4 * 4;
   c->xa.ensure(sizeof(__nv_bfloat16) * (size_t)(kOzSlices * xplane), s);
-  c->t1.ensure(sizeof(double) * (size_t)std::max(s1, s3), s);
-  c->t2.ensure(sizeof(double) * (size_t)s2, s);
+  c->t1.ensure(std::max(sizeof(float) * 2 * (size_t)p1, sizeof(double) * (size_t)s3), s);
+  c->t2.ensure(sizeof(float) * 2 * (size_t)p2, s);
   c->t3.ensure(sizeof(__nv_bfloat16) * (size_t)(kOzSlices * plane3), s);
   __nv_bfloat16* XT = c->xa.as<__nv_bfloat16>();
-  double* T1 = c->t1.as<double>();
-  double* T2 = c->t2.as<double>();
+  float* T1 = c->t1.as<float>();
+  float* T2 = c->t2.as<float>();
   double* T3 = c->t1.as<double>();
   __nv_bfloat16* T3p = c->t3.as<__nv_bfloat16>();
   {  // slices of x^T: row n = column n of x [a'][(s1 s2 b')]
@@ -774,10 +780,10 @@ void heff_f64emu(a2_ctx* c, const SiteOps& A1, const SiteOps& A2, const OzEnvs& 
     const double M = (double)Dl * Rl, N = (double)NX, K = Dl;
     ProfScope ps(PK_F64E_S1, s, 2.0 * M * N * K,
                  2.0 * kOzSlices * (M * K + N * K) + 8.0 * M * N);
-    tc_gemm_f64emu(E.L, E.ldl, E.lplane, XT, ldx, xplane, Dl * Rl, (int)NX, Dl, T1, NX, c->tf,
-                   s);
+    tc_gemm_f64emu(E.L, E.ldl, E.lplane, XT, ldx, xplane, Dl * Rl, (int)NX, Dl, nullptr, NX,
+                   c->tf, s, T1, p1);
   }
-  {  // S2 / S3 in FP64 on the full MPO cores
+  {  // S2 / S3 in double-float arithmetic (FP32 pairs) on the full MPO cores
     ProfScope ps(PK_F64E_SPARSE, s,
                  2.0 * A1.lr.nnz * (double)n2 * Dr * Dl +
                      2.0 * A2.lr.nnz * (double)Dr * Dl * n1,
@@ -787,7 +793,7 @@ void heff_f64emu(a2_ctx* c, const SiteOps& A1, const SiteOps& A2, const OzEnvs& 
     g2.in_sw = NX; g2.in_st = (long long)n2 * Dr;
     g2.out_sw = NX; g2.out_ss = (long long)n2 * Dr;
     g2.B1 = Dl; g2.in_b1 = (long long)Rl * NX; g2.out_b1 = (long long)R1 * NX;
-    sparse_rows_apply<double, double, double>(A1.lr.rows<double>(), g2, T1, T2, s);
+    sparse_rows_apply_df(A1.lr.rows<float>(), g2, T1, p1, T2, p2, nullptr, s);
     SparseGeom g3;
     g3.veclen = Dr;
     g3.in_sw = NX; g3.in_st = Dr;
@@ -795,7 +801,7 @@ void heff_f64emu(a2_ctx* c, const SiteOps& A1, const SiteOps& A2, const OzEnvs& 
     g3.B1 = Dl; g3.B2 = n1;
     g3.in_b1 = (long long)R1 * NX; g3.in_b2 = (long long)n2 * Dr;
     g3.out_b1 = (long long)n1 * n2 * K4; g3.out_b2 = (long long)n2 * K4;
-    sparse_rows_apply<double, double, double>(A2.lr.rows<double>(), g3, T2, T3, s);
+    sparse_rows_apply_df(A2.lr.rows<float>(), g3, T2, p2, nullptr, 0, T3, s);
   }
   {
     ProfScope ps(PK_F64E_SPLIT, s, 0.0, (8.0 + 2.0 * kOzSlices) * (double)s3);

@@ -322,7 +322,26 @@ sparse_rows_vec_kernel(SparseRows<V> sp, SparseGeom g, const TI* __restrict__ in
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] = Acc(0);
     const int e1 = __ldg(sp.row_ptr + r + 1);
-    for (int e = __ldg(sp.row_ptr + r); e < e1; ++e) {
+    int e = __ldg(sp.row_ptr + r);
+    // four nonzeros at a time: their index loads, then their row loads, are issued
+    // together (more loads in flight); the FMAs keep the nonzero order
+    for (; e + 4 <= e1; e += 4) {
+      long long ci[4];
+      Acc w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        ci[u] = __ldg(sp.nz_w + e + u) * g.in_sw + __ldg(sp.nz_t + e + u) * g.in_st;
+        w[u] = (Acc)__ldg(sp.nz_val + e + u);
+      }
+      Acc x[4][NV];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) load_vec<TI, Acc>(in + ib + ci[u], x[u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) acc[i] = fma(w[u], x[u][i], acc[i]);
+    }
+    for (; e < e1; ++e) {
       const long long ci = __ldg(sp.nz_w + e) * g.in_sw + __ldg(sp.nz_t + e) * g.in_st;
       const Acc w = (Acc)__ldg(sp.nz_val + e);
       Acc x[NV];
@@ -376,7 +395,26 @@ sparse_rows_split3_kernel(SparseRows<V> sp, SparseGeom g, const TI* __restrict__
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] = Acc(0);
     const int e1 = __ldg(sp.row_ptr + r + 1);
-    for (int e = __ldg(sp.row_ptr + r); e < e1; ++e) {
+    int e = __ldg(sp.row_ptr + r);
+    if constexpr (!PLANES) {   // four nonzeros at a time, as in sparse_rows_vec_kernel
+      for (; e + 4 <= e1; e += 4) {
+        long long ci[4];
+        Acc w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          ci[u] = __ldg(sp.nz_w + e + u) * g.in_sw + __ldg(sp.nz_t + e + u) * g.in_st;
+          w[u] = (Acc)__ldg(sp.nz_val + e + u);
+        }
+        Acc x[4][NV];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) load_vec<TI, Acc>(in + ib + ci[u], x[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int i = 0; i < NV; ++i) acc[i] = fma(w[u], x[u][i], acc[i]);
+      }
+    }
+    for (; e < e1; ++e) {
       const long long ci = __ldg(sp.nz_w + e) * g.in_sw + __ldg(sp.nz_t + e) * g.in_st;
       const Acc w = (Acc)__ldg(sp.nz_val + e);
       Acc x[NV];
@@ -577,6 +615,115 @@ void sparse_rows_apply(const SparseRows<V>& sp, const SparseGeom& g, const TI* i
   dim3 grid(cdiv(sp.nrows, rows), g.B1 * g.B2);
   A2_REQUIRE(grid.y < 65536, "sparse grid too large");
   sparse_rows_kernel<TI, TO, V><<<grid, 256, 0, s>>>(sp, g, in, out, rows);
+  A2_CHECK_LAUNCH();
+}
+
+// Double-float multiply-add (Dekker's exact product via FMA, Knuth's two-sum; the
+// product of the two low parts, below 2^-48 of the result, is dropped).
+__device__ __forceinline__ void df_fma(float& ah, float& al, float wh, float wl, float xh,
+                                       float xl) {
+  const float p = __fmul_rn(wh, xh);
+  const float pe = __fmaf_rn(wh, xh, -p);
+  const float q = __fmaf_rn(wh, xl, __fmaf_rn(wl, xh, pe));
+  const float s = __fadd_rn(ah, p);
+  const float bp = __fsub_rn(s, ah);
+  const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+  ah = s;
+  al = __fadd_rn(al, __fadd_rn(err, q));
+}
+
+// NV = 4: float4 rows (16-byte aligned); NV = 1: any alignment.
+template <bool OUT64, int NV>
+__global__ void __launch_bounds__(256)
+sparse_rows_df_kernel(SparseRows<float> sp, SparseGeom g, const float* __restrict__ ih,
+                      long long in_plane, float* __restrict__ oh, long long out_plane,
+                      double* __restrict__ o64, int lpr, int rows_per_cta) {
+  const float* il = ih + in_plane;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rpw = 32 / lpr;
+  const int slot = lane / lpr, l = lane % lpr;
+  const int v0 = blockIdx.y * (lpr * NV) + l * NV;
+  const int bz = blockIdx.z;
+  const int b1 = bz / g.B2, b2 = bz % g.B2;
+  const long long ib = b1 * g.in_b1 + b2 * g.in_b2 + v0;
+  const long long ob = b1 * g.out_b1 + b2 * g.out_b2 + v0;
+  const int r_beg = blockIdx.x * rows_per_cta;
+  const int r_end = min(sp.nrows, r_beg + rows_per_cta);
+  const int step = (blockDim.x >> 5) * rpw;
+  if (v0 >= g.veclen) return;
+  for (int r = r_beg + warp * rpw + slot; r < r_end; r += step) {
+    float ah[NV], al[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) ah[i] = al[i] = 0.f;
+    const int e1 = __ldg(sp.row_ptr + r + 1);
+    for (int e = __ldg(sp.row_ptr + r); e < e1; ++e) {
+      const long long ci = __ldg(sp.nz_w + e) * g.in_sw + __ldg(sp.nz_t + e) * g.in_st;
+      const float wh = __ldg(sp.nz_val + e), wl = __ldg(sp.nz_lo + e);
+      if constexpr (NV == 4) {
+        const float4 xh = __ldg(reinterpret_cast<const float4*>(ih + ib + ci));
+        const float4 xl = __ldg(reinterpret_cast<const float4*>(il + ib + ci));
+        df_fma(ah[0], al[0], wh, wl, xh.x, xl.x);
+        df_fma(ah[1], al[1], wh, wl, xh.y, xl.y);
+        df_fma(ah[2], al[2], wh, wl, xh.z, xl.z);
+        df_fma(ah[3], al[3], wh, wl, xh.w, xl.w);
+      } else {
+        df_fma(ah[0], al[0], wh, wl, __ldg(ih + ib + ci), __ldg(il + ib + ci));
+      }
+    }
+    const long long ro = __ldg(sp.row_w + r) * g.out_sw + __ldg(sp.row_s + r) * g.out_ss;
+    if constexpr (OUT64) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) o64[ob + ro + i] = (double)ah[i] + (double)al[i];
+    } else {
+      float h[NV], lo[NV];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {   // renormalise: |lo| <= ulp(hi) / 2
+        const float s = __fadd_rn(ah[i], al[i]);
+        h[i] = s;
+        lo[i] = __fsub_rn(al[i], __fsub_rn(s, ah[i]));
+      }
+      if constexpr (NV == 4) {
+        *reinterpret_cast<float4*>(oh + ob + ro) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4*>(oh + out_plane + ob + ro) =
+            make_float4(lo[0], lo[1], lo[2], lo[3]);
+      } else {
+        oh[ob + ro] = h[0];
+        oh[out_plane + ob + ro] = lo[0];
+      }
+    }
+  }
+}
+
+void sparse_rows_apply_df(const SparseRows<float>& sp, const SparseGeom& g, const float* in_hi,
+                          long long in_plane, float* out_hi, long long out_plane, double* out64,
+                          cudaStream_t s) {
+  if (sp.nrows == 0 || g.veclen == 0) return;
+  A2_REQUIRE(sp.nz_lo && !g.accumulate, "double-float sparse action: bad arguments");
+  auto al = [](long long x) { return x % 4 == 0; };
+  const bool vec = al(g.veclen) && al(g.in_sw) && al(g.in_st) && al(g.out_sw) &&
+                   al(g.out_ss) && al(g.in_b1) && al(g.in_b2) && al(g.out_b1) &&
+                   al(g.out_b2) && al(in_plane) && al(out_plane) &&
+                   reinterpret_cast<uintptr_t>(in_hi) % 16 == 0 &&
+                   (out64 || reinterpret_cast<uintptr_t>(out_hi) % 16 == 0);
+  const int nv = vec ? 4 : 1;
+  int lpr = 1;
+  while (lpr < 32 && lpr * nv < g.veclen) lpr *= 2;
+  const int chunks = cdiv(g.veclen, lpr * nv);
+  const int rows = kSparseRowsPerCta;
+  dim3 grid(cdiv(sp.nrows, rows), chunks, g.B1 * g.B2);
+  A2_REQUIRE(grid.y < 65536 && grid.z < 65536, "sparse grid too large");
+  if (vec && out64)
+    sparse_rows_df_kernel<true, 4><<<grid, 256, 0, s>>>(sp, g, in_hi, in_plane, nullptr, 0,
+                                                        out64, lpr, rows);
+  else if (vec)
+    sparse_rows_df_kernel<false, 4><<<grid, 256, 0, s>>>(sp, g, in_hi, in_plane, out_hi,
+                                                         out_plane, nullptr, lpr, rows);
+  else if (out64)
+    sparse_rows_df_kernel<true, 1><<<grid, 256, 0, s>>>(sp, g, in_hi, in_plane, nullptr, 0,
+                                                        out64, lpr, rows);
+  else
+    sparse_rows_df_kernel<false, 1><<<grid, 256, 0, s>>>(sp, g, in_hi, in_plane, out_hi,
+                                                         out_plane, nullptr, lpr, rows);
   A2_CHECK_LAUNCH();
 }
 

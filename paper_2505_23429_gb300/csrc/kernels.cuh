@@ -40,6 +40,7 @@ struct SparseRows {
   const int* nz_t = nullptr;        // nnz
   const V* nz_val = nullptr;        // nnz
   long long nnz_total = 0;
+  const float* nz_lo = nullptr;     // nnz: FP64 value - (float)value (double-float kernels)
 };
 
 struct SparseGeom {
@@ -136,6 +137,14 @@ void precondition(const double* r, const double* diag, const double* theta, doub
 void cols_rev_to_rows(const double* G, long long ld, int rows, int col_first, int r, double* P,
                       cudaStream_t s);
 void fill_zero(void* p, size_t bytes, cudaStream_t s);
+// FP64-class sparse action in double-float arithmetic: input and weights as FP32 pairs
+// (in_hi + in_lo, nz_val + nz_lo; in_lo = in_hi + in_plane), output as FP32 pairs
+// (out_hi, out_hi + out_plane) or, with out64 set, in FP64.  Geometry as for
+// sparse_rows_apply (float4 rows when every stride is a multiple of 4 and the bases are
+// 16-byte aligned, scalar otherwise).
+void sparse_rows_apply_df(const SparseRows<float>& sp, const SparseGeom& g, const float* in_hi,
+                          long long in_plane, float* out_hi, long long out_plane, double* out64,
+                          cudaStream_t s);
 // grad[param[e]] += factor[e] * G[index[e]] for e < n (FP64 atomics)
 void gather_axpy_atomic(const double* G, const long long* index, const long long* param,
                         const double* factor, long long n, double* grad, cudaStream_t s);

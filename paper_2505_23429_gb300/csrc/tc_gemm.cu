@@ -1090,73 +1090,87 @@ void tc_heff_f32emu(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int 
 // 1024 / (l - 1) K indices per pair stays an integer below 2^24 units and the tensor
 // cores' FP32 accumulation of it is exact.  The pairs with i + j <= kOzSlices + 1 are
 // kept (the rest lie below 2^-kOzBits*kOzSlices of |A||B|), every level's tile of every K
-// split is stored in FP32, and a combine kernel adds a level's tiles exactly in a pair of
-// FP32 numbers (error-free two-sum) and the levels in FP64, smallest first.
+// split is stored in FP32, and a combine kernel adds the tiles, smallest level first, with
+// error-free two-sums into a pair of FP32 numbers (~2^-48 relative).
 namespace {
+
+// Slicing with integer operations only (the FP64 pipe is slow on this part): for a row
+// with largest biased exponent field f_max, e = f_max - 1022 bounds |v| < 2^e; the
+// fixed-point magnitude N = floor(|v| * 2^(56 - e)) < 2^56 is the significand shifted by
+// f - e - 1019 bits, and slice i is bits [56 - 7i, 63 - 7i) of N times 2^(e - 7i) with the
+// sign of v (the same digits as truncating the remainder slice by slice).  Scales below
+// the FP32 normal range are flushed to zero.
+static_assert(kOzSlices * kOzBits == 56, "the slices cover bits 0..55 of the fixed-point value");
+
+__device__ __forceinline__ float pow2f(int k) {
+  return (k >= -126 && k <= 127) ? __int_as_float((k + 127) << 23) : 0.f;
+}
 
 __global__ void ozaki_split_kernel(const double* __restrict__ X, long long sr, long long sk,
                                    int rows, int K, __nv_bfloat16* __restrict__ P, long long ldp,
                                    long long plane) {
-  __shared__ double red[32];
-  __shared__ int e_sh;
+  __shared__ int red[32];
   for (int r = blockIdx.x; r < rows; r += gridDim.x) {
     const double* xr = X + (long long)r * sr;
-    double mx = 0.0;
-    for (int k = threadIdx.x; k < K; k += blockDim.x) mx = fmax(mx, fabs(xr[(long long)k * sk]));
-    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    int fm = 0;
+    for (int k = threadIdx.x; k < K; k += blockDim.x)
+      fm = max(fm, (int)((__double_as_longlong(xr[(long long)k * sk]) >> 52) & 0x7FF));
+    for (int o = 16; o; o >>= 1) fm = max(fm, __shfl_xor_sync(0xffffffffu, fm, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = fm;
     __syncthreads();
-    if (threadIdx.x < 32) {
-      double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-      for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-      if (threadIdx.x == 0) e_sh = v > 0.0 ? ilogb(v) + 1 : 0;
-    }
-    __syncthreads();
-    const int e = e_sh;
+    int f_max = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) f_max = max(f_max, red[w]);
+    const int e = max(f_max, 1) - 1022;
     __nv_bfloat16* pr = P + (long long)r * ldp;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-      double rem = xr[(long long)k * sk];
+      const long long bits = __double_as_longlong(xr[(long long)k * sk]);
+      int f = (int)((bits >> 52) & 0x7FF);
+      unsigned long long m = (unsigned long long)bits & ((1ull << 52) - 1);
+      if (f) m |= 1ull << 52;
+      else f = 1;                                    // subnormal: no hidden bit
+      const int sh = f - e - 1019;                   // <= 3 since |v| < 2^e
+      const unsigned long long N = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> -sh) : 0ull);
+      const float sgn = bits < 0 ? -1.f : 1.f;
 #pragma unroll
       for (int i = 1; i <= kOzSlices; ++i) {
-        const int sh = e - kOzBits * i;
-        const double q = trunc(scalbn(rem, -sh));   // |q| < 2^kOzBits
-        const double pv = scalbn(q, sh);
-        rem -= pv;                                   // exact
-        pr[(long long)(i - 1) * plane + k] = __double2bfloat16(pv);   // exact
+        const int q = (int)((N >> (56 - kOzBits * i)) & ((1u << kOzBits) - 1));
+        pr[(long long)(i - 1) * plane + k] =
+            __float2bfloat16_rn(sgn * (float)q * pow2f(e - kOzBits * i));   // exact
       }
     }
-    __syncthreads();   // red / e_sh are reused by the next row
+    __syncthreads();   // red is reused by the next row
   }
 }
 
 // C[r][c] = sum over the level tiles: tile t of level lev[t] at T + t * MN (row-major,
 // N columns); tiles ordered by level (largest level last).
-struct LevEnd {
-  int e[kOzSlices];   // one past the last tile of each level
-};
-
-__global__ void ozaki_combine_kernel(const float* __restrict__ T, long long MN, int nt,
-                                     LevEnd lev_end, int nlev, int N, double* __restrict__ C,
-                                     long long ldc) {
+// C[r][c] = sum of all level tiles (tile t at T + t * MN, row-major with N columns,
+// ordered by level, largest level last), added smallest level first in double-float
+// arithmetic: every tile value is exact, the two-sum keeps the running sum as an FP32
+// pair hi + lo (~2^-48), and the result is written as FP64 (hi + lo) or as the pair.
+template <bool DF>
+__global__ void ozaki_combine_kernel(const float* __restrict__ T, long long MN, int nt, int N,
+                                     double* __restrict__ C, float* __restrict__ Cdf,
+                                     long long df_plane, long long ldc) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < MN;
        e += (long long)gridDim.x * blockDim.x) {
-    double total = 0.0;
-    int t1 = nt;
-    for (int l = nlev - 1; l >= 0; --l) {   // smallest level first
-      const int t0 = l > 0 ? lev_end.e[l - 1] : 0;
-      float hi = 0.f, lo = 0.f;
-      for (int t = t0; t < t1; ++t) {       // error-free two-sum: hi + lo exact
-        const float v = T[(long long)t * MN + e];
-        const float s = __fadd_rn(hi, v);
-        const float bp = __fsub_rn(s, hi);
-        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(v, bp));
-        hi = s;
-        lo = __fadd_rn(lo, err);
-      }
-      total += (double)hi + (double)lo;
-      t1 = t0;
+    float hi = 0.f, lo = 0.f;
+    for (int t = nt - 1; t >= 0; --t) {
+      const float v = __ldg(T + (long long)t * MN + e);
+      const float s = __fadd_rn(hi, v);
+      const float bp = __fsub_rn(s, hi);
+      const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(v, bp));
+      hi = s;
+      lo = __fadd_rn(lo, err);
     }
-    C[(e / N) * ldc + e % N] = total;
+    const long long o = (e / N) * ldc + e % N;
+    if constexpr (DF) {   // renormalised pair
+      const float s = __fadd_rn(hi, lo);
+      Cdf[o] = s;
+      Cdf[df_plane + o] = __fsub_rn(lo, __fsub_rn(s, hi));
+    } else {
+      C[o] = (double)hi + (double)lo;
+    }
   }
 }
 
@@ -1172,10 +1186,10 @@ void ozaki_split(const double* X, long long sr, long long sk, int rows, int K, _
 
 void tc_gemm_f64emu(const __nv_bfloat16* A, long long lda, long long aplane,
                     const __nv_bfloat16* B, long long ldb, long long bplane, int M, int N, int K,
-                    double* C, long long ldc, DevBuf& slab, cudaStream_t s) {
+                    double* C, long long ldc, DevBuf& slab, cudaStream_t s, float* Cdf,
+                    long long df_plane) {
   const int nk = (K + tc::BK - 1) / tc::BK;
   const long long MN = (long long)M * N;
-  constexpr int nlev = kOzSlices;   // levels 2 .. kOzSlices + 1
   long long ntiles = 0;
   for (int l = 2; l <= kOzSlices + 1; ++l) {
     const int kb = std::max(1, 16 / (l - 1));
@@ -1189,7 +1203,6 @@ void tc_gemm_f64emu(const __nv_bfloat16* A, long long lda, long long aplane,
     Ap[i] = A + i * aplane;
     Bp[i] = B + i * bplane;
   }
-  LevEnd lev_end;
   long long t = 0;
   for (int l = 2; l <= kOzSlices + 1; ++l) {
     const int np = l - 1;
@@ -1207,10 +1220,13 @@ void tc_gemm_f64emu(const __nv_bfloat16* A, long long lda, long long aplane,
                                     N, tc::OUT_F32, want, s, MN);
     A2_REQUIRE(got >= 1 && got <= want, "FP64 emulation: unexpected K split");
     t += got;
-    lev_end.e[l - 2] = (int)t;
   }
   const int grid = (int)std::min<long long>((MN + 255) / 256, 152LL * 16);
-  ozaki_combine_kernel<<<grid, 256, 0, s>>>(T, MN, (int)t, lev_end, nlev, N, C, ldc);
+  if (Cdf)
+    ozaki_combine_kernel<true><<<grid, 256, 0, s>>>(T, MN, (int)t, N, nullptr, Cdf, df_plane,
+                                                    ldc);
+  else
+    ozaki_combine_kernel<false><<<grid, 256, 0, s>>>(T, MN, (int)t, N, C, nullptr, 0, ldc);
   A2_CHECK_LAUNCH();
 }
 

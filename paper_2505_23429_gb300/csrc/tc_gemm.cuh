@@ -74,10 +74,12 @@ void ozaki_split(const double* X, long long sr, long long sk, int rows, int K, _
                  long long ldp, long long plane, cudaStream_t s);
 // C (FP64, M x N, row stride ldc) = sum_k A[m][k] B[n][k] to FP64 accuracy from the split
 // planes of A (row stride lda, plane stride aplane) and B; slab is FP32 scratch for the
-// level tiles of every K split (grown as needed).
+// level tiles of every K split (grown as needed).  With Cdf set the result is written as
+// an FP32 pair instead (Cdf + r*ldc + c and the same at + df_plane), C unused.
 void tc_gemm_f64emu(const __nv_bfloat16* A, long long lda, long long aplane,
                     const __nv_bfloat16* B, long long ldb, long long bplane, int M, int N, int K,
-                    double* C, long long ldc, DevBuf& slab, cudaStream_t s);
+                    double* C, long long ldc, DevBuf& slab, cudaStream_t s,
+                    float* Cdf = nullptr, long long df_plane = 0);
 
 // Enable (default) or disable the GEMM autotuner (disabling also forgets its choices).
 void tc_autotune(bool on);
