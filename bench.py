@@ -224,13 +224,24 @@ def profile_matvec(args):
     x = torch.randn(D, n, n, D, device="cuda", dtype=torch.float64, generator=g)
     y = torch.empty_like(x)
     torch.cuda.synchronize()
+    classes = {}
     for prec in ("bf16", "f32emu") + (("f64emu",) if args.f64emu else ()):
         op = a2.HeffOp(ctx, mpo, k, HL, HR, prec=prec)
+        op.apply(x, y)                       # first application: autotuner, scratch growth
+        ctx.synchronize()
+        a2.profile(ctx, "reset")
+        a2.profile(ctx, "on")
         for _ in range(args.reps):
             op.apply(x, y)
         ctx.synchronize()
+        a2.profile(ctx, "off")
         op.close()
-    print(json.dumps(dict(profile_matvec=True, D=D, bond=k, error_flag=a2.device_error(ctx))))
+        for i, name in enumerate(a2.a2dmrg.PROFILE_KINDS):   # per-application class times
+            r = a2.profile(ctx, "read", i)
+            if r["launches"]:
+                classes[f"{prec}:{name}"] = round(r["ms"] / max(args.reps, 1), 3)
+    print(json.dumps(dict(profile_matvec=True, D=D, bond=k, reps=args.reps,
+                          ms_per_application=classes, error_flag=a2.device_error(ctx))))
 
 
 def class_roofline(name, d, peaks, prec):

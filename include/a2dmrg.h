@@ -143,8 +143,9 @@ typedef struct {
                                   (partition sums to L), one-site micro-steps with QR between
                                   the cores of a group, no rank change in the local steps,
                                   compression of the rank-2r structured sum; the local
-                                  contractions run on the SIMT path (FP64, or FP32 for the
-                                  mixed precisions); krylov_iters then has L entries */
+                                  contractions run on the SIMT path for A2_FP64 / A2_FP32
+                                  and on the tensor cores with FP32-accurate products for
+                                  A2_BF16 / A2_F32EMU; krylov_iters then has L entries */
   int n_eig;                   /* K: 0 or 1 = one eigenvector per local problem; K > 1 =
                                   Extension One (extension remark after Alg. 2): the last
                                   local problem of every group keeps its K lowest

@@ -917,6 +917,18 @@ struct Engine {
     flops += heff_flops(mpo->site[k], mpo->site[k + 1], Dl, Dr);
     ++matvecs;
   }
+  // one-site H_eff on the tensor cores with FP32-accurate products (environments in bfe)
+  void matvec1_emu(int j, int Dl, int Dr, const double* x, double* y) {
+    const SiteOps& A = mpo->site[j];
+    const long long N = (long long)Dl * A.n * Dr;
+    c->ya.ensure(sizeof(float) * N, c->stream);
+    tc_heff1_f32emu(c->stream, A.n, A.Rl, A.Rr, Dl, Dr, bfe.L, bfe.ldl, bfe.lplane, bfe.R,
+                    bfe.ldr, bfe.rplane, x, c->ya.as<float>(), A.lr.rows<float>(), c->t1, c->t2,
+                    c->xa);
+    convert<float, double>(c->ya.as<float>(), y, N, c->stream);
+    flops += env_flops(A, Dl, Dr);
+    ++matvecs;
+  }
   // one-site H_eff at core j with FP64 vectors and envs HL_ / HR_ (T)
   void matvec1(int j, const T* HL_, const T* HR_, int Dl, int Dr, const double* x, double* y) {
     const SiteOps& A = mpo->site[j];
@@ -1682,7 +1694,18 @@ struct Sweeper {
       const int n = tt->phys[j], Dr = kd[j + 1];
       const long long N = (long long)Dl * n * Dr;
       const T* HRj = hr_at(j + 1, eng, HRbuf);
-      auto mv = [&](const double* in, double* out) { eng.matvec1(j, HLcur, HRj, Dl, Dr, in, out); };
+      // mixed modes: FP32-accurate tensor-core products (environments split once)
+      bool tc1 = false;
+      if constexpr (sizeof(T) == 4) {
+        if (o.prec == A2_BF16 || o.prec == A2_F32EMU) {
+          eng.bfe.set(c, HLcur, Dl, mpo->R[j], HRj, Dr, mpo->R[j + 1], 3);
+          tc1 = true;
+        }
+      }
+      auto mv = [&](const double* in, double* out) {
+        if (tc1) eng.matvec1_emu(j, Dl, Dr, in, out);
+        else eng.matvec1(j, HLcur, HRj, Dl, Dr, in, out);
+      };
       const bool ext = o.n_eig > 1 && j == last;
       DevBuf xstart;
       if (ext) {

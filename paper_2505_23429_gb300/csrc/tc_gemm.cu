@@ -1078,6 +1078,58 @@ void tc_heff_f32emu(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int 
 }
 
 
+// One-site H_eff with FP32-accurate tensor-core products (the one-site case of Alg. 2):
+// T1 = L x (as S1), T2 = the MPO core on the rows in FP32 with three BF16 output planes
+// (as S3), y = T2 R^T (as S4).
+void tc_heff1_f32emu(cudaStream_t s, int n, int Rl, int Rr, int Dl, int Dr,
+                     const __nv_bfloat16* Lp, long long ldl, long long lplane,
+                     const __nv_bfloat16* Rp, long long ldr, long long rplane, const double* x,
+                     float* y, const SparseRows<float>& W, DevBuf& t1, DevBuf& t2, DevBuf& xa) {
+  static const int pa[6] = {0, 0, 1, 0, 1, 2};
+  static const int pb[6] = {0, 1, 0, 2, 1, 0};
+  const long long NX = (long long)n * Dr;
+  const long long ldx = pad8(Dl);
+  const long long xplane = (NX * ldx + 63) / 64 * 64;
+  const long long s1 = (long long)Dl * Rl * NX;
+  const long long K4 = (long long)Rr * Dr;
+  const long long ld3 = pad8(K4);
+  const long long M4 = (long long)Dl * n;
+  const long long plane3 = (M4 * ld3 + 63) / 64 * 64;
+  xa.ensure(sizeof(__nv_bfloat16) * (size_t)(3 * xplane), s);
+  t1.ensure(sizeof(float) * (size_t)s1, s);
+  t2.ensure(sizeof(__nv_bfloat16) * (size_t)(3 * plane3), s);
+  __nv_bfloat16* XT = xa.as<__nv_bfloat16>();
+  float* T1 = t1.as<float>();
+  __nv_bfloat16* T2 = t2.as<__nv_bfloat16>();
+  transpose_split3(x, Dl, (int)NX, XT, ldx, xplane, s);
+  {
+    const __nv_bfloat16* A[3] = {Lp, Lp + lplane, Lp + 2 * lplane};
+    const __nv_bfloat16* B[3] = {XT, XT + xplane, XT + 2 * xplane};
+    const double M = (double)Dl * Rl, N = (double)NX, K = Dl;
+    ProfScope ps(PK_EMU_S1, s, 6.0 * 2.0 * M * N * K, 6.0 * (M * K + N * K) + 4.0 * M * N);
+    tc_gemm_bf16_pairs(A, ldl, B, ldx, Dl * Rl, (int)NX, Dl, 6, pa, pb, T1, NX, tc::OUT_F32, 1, s);
+  }
+  {
+    ProfScope ps(PK_EMU_S3, s, 2.0 * W.nnz_total * (double)Dr * Dl,
+                 4.0 * (double)s1 + 6.0 * (double)M4 * K4);
+    SparseGeom gm;
+    gm.veclen = Dr;
+    gm.in_sw = NX; gm.in_st = Dr;
+    gm.out_sw = Dr; gm.out_ss = ld3;
+    gm.B1 = Dl; gm.in_b1 = (long long)Rl * NX; gm.out_b1 = (long long)n * ld3;
+    sparse_rows_apply_split3<float, float>(W, gm, T1, 0, nullptr, T2, plane3, s);
+  }
+  {
+    const __nv_bfloat16* A[3] = {T2, T2 + plane3, T2 + 2 * plane3};
+    const __nv_bfloat16* B[3] = {Rp, Rp + rplane, Rp + 2 * rplane};
+    const double M = (double)M4, N = Dr, K = (double)K4;
+    ProfScope ps(PK_EMU_S4, s, 6.0 * 2.0 * M * N * K, 6.0 * (M * K + N * K) + 4.0 * M * N);
+    fill_zero(y, sizeof(float) * (size_t)M4 * Dr, s);
+    tc_gemm_bf16_pairs(A, ld3, B, ldr, (int)M4, Dr, (int)K4, 6, pa, pb, y, Dr,
+                       tc::OUT_F32_ATOMIC, s4_splitk(M4, Dr, (K4 + 63) / 64), s);
+  }
+}
+
 // ============================================================================ FP64 emulation
 // Ozaki scheme (Ozaki, Ogita, Oishi, Rump, "Error-free transformations of matrix
 // multiplication by using fast routines of matrix multiplication and its applications",

@@ -65,6 +65,14 @@ void tc_heff_f32emu(cudaStream_t s, int n1, int n2, int Rl, int R1, int Rr, int 
                     float* y, const SparseRows<float>& W1, const SparseRows<float>& W2,
                     const HeffFold& F, DevBuf& t1, DevBuf& t2, DevBuf& xa, DevBuf& tf);
 
+// One-site H_eff y[a,s,b] = sum L[a,w,a'] W[w,s,t,w'] R[b,w',b'] x[a',t,b'] with
+// FP32-accurate tensor-core products; L / R as three BF16 planes (layouts as for the
+// two-site chain), W the left-to-right rows of the core, FP64 x in, FP32 y out.
+void tc_heff1_f32emu(cudaStream_t s, int n, int Rl, int Rr, int Dl, int Dr,
+                     const __nv_bfloat16* Lp, long long ldl, long long lplane,
+                     const __nv_bfloat16* Rp, long long ldr, long long rplane, const double* x,
+                     float* y, const SparseRows<float>& W, DevBuf& t1, DevBuf& t2, DevBuf& xa);
+
 // FP64 emulation (Ozaki scheme with BF16 slices, see tc_gemm.cu).
 constexpr int kOzSlices = 8;   // slices per FP64 operand
 constexpr int kOzBits = 7;     // bits per slice

@@ -44,8 +44,8 @@ def _scaled_err(got, ref, scale):
     return float(np.abs(np.asarray(got) - np.asarray(ref)).max() / scale)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", TOL32), ("f32emu", TOL32),
-                                      ("bf16", 3e-2)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("f64emu", 1e-12), ("fp32", TOL32),
+                                      ("f32emu", TOL32), ("bf16", 3e-2)])
 @pytest.mark.parametrize("k", [5, 7, 8])
 def test_heff_full_size_sampled(ctx, chem16, prec, tol, k):
     """Bond 5: a typical middle bond; 7 / 8: the hand-over core on the right / left
