@@ -227,10 +227,12 @@ a2_status a2_energy_gradient(a2_ctx* ctx, const a2_tt* tt, const a2_mpo* mpo, lo
                              const long long* map_index, const double* map_factor,
                              double* grad_out, double* E_out);
 
-/* Library-wide: enable (1, default) or disable (0) the autotuner of the tcgen05 GEMMs.
- * When enabled, the first GEMM of every shape times the candidate kernel variants /
- * K splits on the caller's stream (synchronising it once) and keeps the fastest;
- * disabling forgets the choices and uses the built-in heuristics.  Always A2_OK. */
+/* Library-wide: enable (1, default) or disable (0) the autotuners of the tcgen05 GEMMs
+ * and of the sparse MPO stages.  When enabled, the first GEMM of every shape times the
+ * candidate kernel variants / K splits, and the first sparse launch of every shape the
+ * candidate rows per thread block, on the caller's stream (synchronising it once), and
+ * keeps the fastest; disabling forgets the choices and uses the built-in heuristics.
+ * Always A2_OK. */
 a2_status a2_set_autotune(int enable);
 
 /* ---- kernel-level entry points (device pointers, FP64 in/out) ------------- */

@@ -497,5 +497,6 @@ def energy_autograd(h, eri, ctx, tt, mpo, cmap):
 
 
 def set_autotune(enable):
-    """Enable / disable the tcgen05 GEMM autotuner (library-wide)."""
+    """Enable / disable the autotuners of the tcgen05 GEMMs and the sparse stages
+    (library-wide)."""
     lib().a2_set_autotune(1 if enable else 0)

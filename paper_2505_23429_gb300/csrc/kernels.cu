@@ -1,6 +1,7 @@
 // SIMT GEMM, sparse MPO action, vector and small dense kernels (sm_103a).
 #include <algorithm>
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -272,6 +273,57 @@ __global__ void sparse_rows_kernel(SparseRows<V> sp, SparseGeom g, const TI* __r
 // few batches, so the input rows they gather from stay in L2 between their uses.
 constexpr int kSparseRowsPerCta = 16;
 
+// Autotuner of the rows per CTA of the vectorised sparse launches: the first launch of a
+// shape class (kernel variant, rows, vector length, batches, nonzeros) times 4, 8, 16 and
+// 32 rows per CTA with CUDA events on the caller's stream and keeps the fastest.  Only
+// launches whose output does not depend on its previous contents are tuned (re-running
+// them is harmless); the others use kSparseRowsPerCta.
+struct SparseTuneKey {
+  int kid, nrows, veclen, batches;
+  long long nnz;
+  bool operator<(const SparseTuneKey& o) const {
+    if (kid != o.kid) return kid < o.kid;
+    if (nrows != o.nrows) return nrows < o.nrows;
+    if (veclen != o.veclen) return veclen < o.veclen;
+    if (batches != o.batches) return batches < o.batches;
+    return nnz < o.nnz;
+  }
+};
+std::mutex g_sp_mu;
+std::map<SparseTuneKey, int> g_sp_tune;
+std::atomic<bool> g_sp_on{true};
+
+template <class Launch>
+int sparse_rows_tuned(const SparseTuneKey& key, bool tunable, Launch&& launch, cudaStream_t s) {
+  if (!tunable || !g_sp_on.load()) return kSparseRowsPerCta;
+  {
+    std::lock_guard<std::mutex> g(g_sp_mu);
+    auto it = g_sp_tune.find(key);
+    if (it != g_sp_tune.end()) return it->second;
+  }
+  static const int cand[4] = {4, 8, 16, 32};
+  cudaEvent_t e0, e1;
+  A2_CUDA(cudaEventCreate(&e0));
+  A2_CUDA(cudaEventCreate(&e1));
+  int best = kSparseRowsPerCta;
+  float best_ms = 1e30f;
+  for (int c : cand) {
+    launch(c);                         // warm-up of this configuration
+    A2_CUDA(cudaEventRecord(e0, s));
+    launch(c);
+    A2_CUDA(cudaEventRecord(e1, s));
+    A2_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    A2_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) { best_ms = ms; best = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> g(g_sp_mu);
+  g_sp_tune[key] = best;
+  return best;
+}
+
 // Vectorised variant: each lane owns VEC consecutive vector elements (16-byte loads),
 // `lpr` lanes cover one row chunk of lpr*VEC elements, a warp serves 32/lpr rows at a
 // time.  Grid: x = row blocks, y = vector chunks, z = batch; consecutive CTAs share the
@@ -504,14 +556,20 @@ void sparse_rows_apply_split3(const SparseRows<V>& sp, const SparseGeom& g, cons
   }
   int lpr = 1;
   while (lpr < 32 && lpr * NV < g.veclen) lpr *= 2;
-  dim3 grid(cdiv(sp.nrows, kSparseRowsPerCta), cdiv(g.veclen, lpr * NV), g.B1 * g.B2);
-  A2_REQUIRE(grid.y < 65536 && grid.z < 65536, "sparse grid too large");
+  const int chunks = cdiv(g.veclen, lpr * NV);
+  A2_REQUIRE(chunks < 65536 && g.B1 * g.B2 < 65536, "sparse grid too large");
   auto kern = in_plane ? (add ? sparse_rows_split3_kernel<TI, V, true, true>
                                : sparse_rows_split3_kernel<TI, V, true, false>)
                       : (add ? sparse_rows_split3_kernel<TI, V, false, true>
                              : sparse_rows_split3_kernel<TI, V, false, false>);
-  kern<<<grid, 256, 0, s>>>(sp, g, in, in_plane, add, out, plane, lpr, kSparseRowsPerCta);
-  A2_CHECK_LAUNCH();
+  auto launch = [&](int rows) {
+    dim3 grid(cdiv(sp.nrows, rows), chunks, g.B1 * g.B2);
+    kern<<<grid, 256, 0, s>>>(sp, g, in, in_plane, add, out, plane, lpr, rows);
+    A2_CHECK_LAUNCH();
+  };
+  const SparseTuneKey key{100 + (int)sizeof(TI) * 4 + (in_plane ? 2 : 0) + (add ? 1 : 0),
+                          sp.nrows, g.veclen, g.B1 * g.B2, sp.nnz_total};
+  launch(sparse_rows_tuned(key, true, launch, s));
 }
 template void sparse_rows_apply_split3<float, float>(const SparseRows<float>&, const SparseGeom&,
                                                      const float*, long long, const float*,
@@ -600,14 +658,19 @@ void sparse_rows_apply(const SparseRows<V>& sp, const SparseGeom& g, const TI* i
     int lpr = 1;
     while (lpr < 32 && lpr * NV < g.veclen) lpr *= 2;
     const int chunks = cdiv(g.veclen, lpr * NV);
-    const int rows = kSparseRowsPerCta;
-    dim3 grid(cdiv(sp.nrows, rows), chunks, g.B1 * g.B2);
-    A2_REQUIRE(grid.y < 65536 && grid.z < 65536, "sparse grid too large");
-    if (g.accumulate)
-      sparse_rows_vec_kernel<TI, TO, V, true><<<grid, 256, 0, s>>>(sp, g, in, out, lpr, rows);
-    else
-      sparse_rows_vec_kernel<TI, TO, V, false><<<grid, 256, 0, s>>>(sp, g, in, out, lpr, rows);
-    A2_CHECK_LAUNCH();
+    A2_REQUIRE(chunks < 65536 && g.B1 * g.B2 < 65536, "sparse grid too large");
+    auto launch = [&](int rows) {
+      dim3 grid(cdiv(sp.nrows, rows), chunks, g.B1 * g.B2);
+      if (g.accumulate)
+        sparse_rows_vec_kernel<TI, TO, V, true><<<grid, 256, 0, s>>>(sp, g, in, out, lpr, rows);
+      else
+        sparse_rows_vec_kernel<TI, TO, V, false><<<grid, 256, 0, s>>>(sp, g, in, out, lpr, rows);
+      A2_CHECK_LAUNCH();
+    };
+    const SparseTuneKey key{(int)(sizeof(TI) * 16 + sizeof(TO)), sp.nrows, g.veclen,
+                            g.B1 * g.B2, sp.nnz_total};
+    launch(sparse_rows_tuned(key, !g.accumulate && (const void*)in != (const void*)out,
+                             launch, s));
     return;
   }
   int rows = max(1, 2048 / g.veclen);
@@ -709,22 +772,26 @@ void sparse_rows_apply_df(const SparseRows<float>& sp, const SparseGeom& g, cons
   int lpr = 1;
   while (lpr < 32 && lpr * nv < g.veclen) lpr *= 2;
   const int chunks = cdiv(g.veclen, lpr * nv);
-  const int rows = kSparseRowsPerCta;
-  dim3 grid(cdiv(sp.nrows, rows), chunks, g.B1 * g.B2);
-  A2_REQUIRE(grid.y < 65536 && grid.z < 65536, "sparse grid too large");
-  if (vec && out64)
-    sparse_rows_df_kernel<true, 4><<<grid, 256, 0, s>>>(sp, g, in_hi, in_plane, nullptr, 0,
-                                                        out64, lpr, rows);
-  else if (vec)
-    sparse_rows_df_kernel<false, 4><<<grid, 256, 0, s>>>(sp, g, in_hi, in_plane, out_hi,
-                                                         out_plane, nullptr, lpr, rows);
-  else if (out64)
-    sparse_rows_df_kernel<true, 1><<<grid, 256, 0, s>>>(sp, g, in_hi, in_plane, nullptr, 0,
-                                                        out64, lpr, rows);
-  else
-    sparse_rows_df_kernel<false, 1><<<grid, 256, 0, s>>>(sp, g, in_hi, in_plane, out_hi,
-                                                         out_plane, nullptr, lpr, rows);
-  A2_CHECK_LAUNCH();
+  A2_REQUIRE(chunks < 65536 && g.B1 * g.B2 < 65536, "sparse grid too large");
+  auto launch = [&](int rows) {
+    dim3 grid(cdiv(sp.nrows, rows), chunks, g.B1 * g.B2);
+    if (vec && out64)
+      sparse_rows_df_kernel<true, 4><<<grid, 256, 0, s>>>(sp, g, in_hi, in_plane, nullptr, 0,
+                                                          out64, lpr, rows);
+    else if (vec)
+      sparse_rows_df_kernel<false, 4><<<grid, 256, 0, s>>>(sp, g, in_hi, in_plane, out_hi,
+                                                           out_plane, nullptr, lpr, rows);
+    else if (out64)
+      sparse_rows_df_kernel<true, 1><<<grid, 256, 0, s>>>(sp, g, in_hi, in_plane, nullptr, 0,
+                                                          out64, lpr, rows);
+    else
+      sparse_rows_df_kernel<false, 1><<<grid, 256, 0, s>>>(sp, g, in_hi, in_plane, out_hi,
+                                                           out_plane, nullptr, lpr, rows);
+    A2_CHECK_LAUNCH();
+  };
+  const SparseTuneKey key{200 + (vec ? 2 : 0) + (out64 ? 1 : 0), sp.nrows, g.veclen,
+                          g.B1 * g.B2, sp.nnz_total};
+  launch(sparse_rows_tuned(key, true, launch, s));
 }
 
 template void sparse_rows_apply<double, double, double>(const SparseRows<double>&,
@@ -1468,6 +1535,12 @@ void copy_block3(const double* src, int d0, int d1, int d2, double* dst, long lo
   copy_block3_kernel<<<grid_for(n), 256, 0, s>>>(src, d0, d1, d2, dst, dst_s0, dst_s1, o0, o2,
                                                  alpha, add);
   A2_CHECK_LAUNCH();
+}
+
+void sparse_autotune(bool on) {
+  std::lock_guard<std::mutex> g(g_sp_mu);
+  g_sp_on.store(on);
+  if (!on) g_sp_tune.clear();
 }
 
 }  // namespace a2

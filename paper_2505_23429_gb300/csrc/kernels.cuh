@@ -137,6 +137,9 @@ void precondition(const double* r, const double* diag, const double* theta, doub
 void cols_rev_to_rows(const double* G, long long ld, int rows, int col_first, int r, double* P,
                       cudaStream_t s);
 void fill_zero(void* p, size_t bytes, cudaStream_t s);
+// Enable (default) / disable the rows-per-CTA autotuner of the sparse stages (disabling
+// also forgets its choices).
+void sparse_autotune(bool on);
 // FP64-class sparse action in double-float arithmetic: input and weights as FP32 pairs
 // (in_hi + in_lo, nz_val + nz_lo; in_lo = in_hi + in_plane), output as FP32 pairs
 // (out_hi, out_hi + out_plane) or, with out64 set, in FP64.  Geometry as for

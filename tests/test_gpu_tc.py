@@ -206,3 +206,29 @@ def test_heff_operator_handle(ctx, chem16, prec):
         got = host(y, ctx)
         assert np.all(np.isfinite(got)) and rel(got, ref) < tol
     op.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("f32emu", 1e-6), ("f64emu", 1e-13)])
+def test_autotuners_do_not_change_results(ctx, prec, tol):
+    """The GEMM and sparse-stage autotuners only pick launch shapes: H_eff with them on
+    (after their timing trials) and off agree to the rounding of the precision (split-K
+    tiles are added with atomics, so not bitwise)."""
+    h, eri = chemistry_integrals(6, 2505)
+    m = chemistry_mpo(h, eri)
+    mpo = a2.MPO(ctx, m)
+    k, Dl, Dr = 2, 48, 40
+    rng = np.random.default_rng(77)
+    Lh = rng.standard_normal((Dl, m[k].shape[0], Dl))
+    Rh = rng.standard_normal((Dr, m[k + 1].shape[3], Dr))
+    x = rng.standard_normal((Dl, 4, 4, Dr))
+    out = []
+    try:
+        for on in (True, True, False):
+            a2.set_autotune(on)
+            y = torch.zeros(x.shape, dtype=torch.float64, device="cuda")
+            a2.heff_apply(ctx, mpo, k, dev(Lh), dev(Rh), dev(x), y, prec=prec)
+            out.append(host(y, ctx))
+    finally:
+        a2.set_autotune(True)
+    assert rel(out[1], out[2]) < tol
+    assert rel(out[0], out[1]) < tol
