@@ -274,8 +274,8 @@ __global__ void sparse_rows_kernel(SparseRows<V> sp, SparseGeom g, const TI* __r
 constexpr int kSparseRowsPerCta = 16;
 
 // Autotuner of the rows per CTA of the vectorised sparse launches: the first launch of a
-// shape class (kernel variant, rows, vector length, batches, nonzeros) times 4, 8, 16 and
-// 32 rows per CTA with CUDA events on the caller's stream and keeps the fastest.  Only
+// shape class (kernel variant, rows, vector length, batches, nonzeros) times 4, 8, 16, 32
+// and 64 rows per CTA with CUDA events on the caller's stream and keeps the fastest.  Only
 // launches whose output does not depend on its previous contents are tuned (re-running
 // them is harmless); the others use kSparseRowsPerCta.
 struct SparseTuneKey {
@@ -301,7 +301,7 @@ int sparse_rows_tuned(const SparseTuneKey& key, bool tunable, Launch&& launch, c
     auto it = g_sp_tune.find(key);
     if (it != g_sp_tune.end()) return it->second;
   }
-  static const int cand[4] = {4, 8, 16, 32};
+  static const int cand[5] = {4, 8, 16, 32, 64};
   cudaEvent_t e0, e1;
   A2_CUDA(cudaEventCreate(&e0));
   A2_CUDA(cudaEventCreate(&e1));
