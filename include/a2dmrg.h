@@ -227,12 +227,13 @@ a2_status a2_energy_gradient(a2_ctx* ctx, const a2_tt* tt, const a2_mpo* mpo, lo
                              const long long* map_index, const double* map_factor,
                              double* grad_out, double* E_out);
 
-/* Library-wide: enable (1, default) or disable (0) the autotuners of the tcgen05 GEMMs
- * and of the sparse MPO stages.  When enabled, the first GEMM of every shape times the
- * candidate kernel variants / K splits, and the first sparse launch of every shape the
- * candidate rows per thread block, on the caller's stream (synchronising it once), and
- * keeps the fastest; disabling forgets the choices and uses the built-in heuristics.
- * Always A2_OK. */
+/* Library-wide autotuners, `enable` a bit set: bit 0 (1) the tcgen05 GEMM autotuner (on
+ * by default), bit 1 (2) the sparse-stage autotuner (off by default).  When on, the first
+ * GEMM of every shape class times the candidate kernel variants / K splits, and the
+ * first sparse launch of every shape the candidate rows per thread block, on the caller's
+ * stream (synchronising it once), and keeps the fastest; switching one off forgets its
+ * choices and uses the built-in heuristics.  (The sparse classes are per bond, so their
+ * trials cost more than they gain within a few iterations.)  Always A2_OK. */
 a2_status a2_set_autotune(int enable);
 
 /* ---- kernel-level entry points (device pointers, FP64 in/out) ------------- */

@@ -496,7 +496,7 @@ def energy_autograd(h, eri, ctx, tt, mpo, cmap):
     return _Energy.apply(h, eri)
 
 
-def set_autotune(enable):
-    """Enable / disable the autotuners of the tcgen05 GEMMs and the sparse stages
-    (library-wide)."""
-    lib().a2_set_autotune(1 if enable else 0)
+def set_autotune(enable, sparse=False):
+    """Enable / disable the tcgen05 GEMM autotuner (on by default) and, with sparse=True,
+    the sparse-stage autotuner (off by default); library-wide."""
+    lib().a2_set_autotune((1 if enable else 0) | (2 if sparse else 0))

@@ -2531,7 +2531,8 @@ a2_status a2_mpo_nnz(const a2_mpo* m, int site, long long* nnz) {
 }
 
 a2_status a2_set_autotune(int enable) {
-  tc_autotune(enable != 0);
+  tc_autotune((enable & 1) != 0);
+  sparse_autotune((enable & 2) != 0);
   return A2_OK;
 }
 

@@ -273,7 +273,9 @@ __global__ void sparse_rows_kernel(SparseRows<V> sp, SparseGeom g, const TI* __r
 // few batches, so the input rows they gather from stay in L2 between their uses.
 constexpr int kSparseRowsPerCta = 16;
 
-// Autotuner of the rows per CTA of the vectorised sparse launches: the first launch of a
+// Autotuner of the rows per CTA of the vectorised sparse launches (off by default: every
+// bond of a sweep is a new shape class, and the trials cost more than the few per cent
+// they gain in a single global iteration).  The first launch of a
 // shape class (kernel variant, rows, vector length, batches, nonzeros) times 4, 8, 16, 32
 // and 64 rows per CTA with CUDA events on the caller's stream and keeps the fastest.  Only
 // launches whose output does not depend on its previous contents are tuned (re-running
@@ -291,7 +293,7 @@ struct SparseTuneKey {
 };
 std::mutex g_sp_mu;
 std::map<SparseTuneKey, int> g_sp_tune;
-std::atomic<bool> g_sp_on{true};
+std::atomic<bool> g_sp_on{false};   // opt-in (a2_set_autotune bit 1)
 
 template <class Launch>
 int sparse_rows_tuned(const SparseTuneKey& key, bool tunable, Launch&& launch, cudaStream_t s) {

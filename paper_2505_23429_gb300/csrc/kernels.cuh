@@ -137,7 +137,7 @@ void precondition(const double* r, const double* diag, const double* theta, doub
 void cols_rev_to_rows(const double* G, long long ld, int rows, int col_first, int r, double* P,
                       cudaStream_t s);
 void fill_zero(void* p, size_t bytes, cudaStream_t s);
-// Enable (default) / disable the rows-per-CTA autotuner of the sparse stages (disabling
+// Enable / disable (default) the rows-per-CTA autotuner of the sparse stages (disabling
 // also forgets its choices).
 void sparse_autotune(bool on);
 // FP64-class sparse action in double-float arithmetic: input and weights as FP32 pairs

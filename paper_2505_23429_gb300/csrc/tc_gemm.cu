@@ -808,12 +808,9 @@ bool g_tune_on = true;
 }  // namespace
 
 void tc_autotune(bool on) {
-  {
-    std::lock_guard<std::mutex> g(g_tune_mu);
-    g_tune_on = on;
-    if (!on) g_tune.clear();
-  }
-  sparse_autotune(on);
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune_on = on;
+  if (!on) g_tune.clear();
 }
 
 void tc_gemm_bf16_pairs(const __nv_bfloat16* const* A, long long lda,

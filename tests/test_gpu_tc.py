@@ -224,7 +224,7 @@ def test_autotuners_do_not_change_results(ctx, prec, tol):
     out = []
     try:
         for on in (True, True, False):
-            a2.set_autotune(on)
+            a2.set_autotune(on, sparse=on)
             y = torch.zeros(x.shape, dtype=torch.float64, device="cuda")
             a2.heff_apply(ctx, mpo, k, dev(Lh), dev(Rh), dev(x), y, prec=prec)
             out.append(host(y, ctx))
