@@ -73,6 +73,12 @@ def parse():
     p.add_argument("--bond", type=int, default=None,
                    help="bond of --profile-matvec (default: the one left of the middle)")
     p.add_argument("--reps", type=int, default=3)
+    p.add_argument("--one-site", action="store_true",
+                   help="the one-site case of Alg. 2 (P groups of the L cores)")
+    p.add_argument("--n-eig", type=int, default=1,
+                   help="Extension One: eigenvectors kept per group's last local problem")
+    p.add_argument("--low-memory", action="store_true",
+                   help="memory-limited environment mode (environments rebuilt on demand)")
     p.add_argument("--f64emu", action="store_true",
                    help="--profile-matvec also applies the FP64-emulated chain")
     return p.parse_args()
@@ -324,6 +330,14 @@ def main():
     kw = sweep_kwargs(cfg, args.prec, args.solver, args.coarse_eps)
     kw["sequential"] = args.sequential or args.groups == "sequential"
     P = cfg["P"]
+    if args.one_site:   # the one-site case of Alg. 2: P groups of the L cores
+        L = cfg["L"]
+        kw["partition"] = [L // P + (1 if g < L % P else 0) for g in range(P)]
+        kw["one_site"] = True
+    if args.n_eig > 1:
+        kw["n_eig"] = args.n_eig
+    if args.low_memory:
+        kw["low_memory"] = True
     t = a2.TT.from_cores(ctx, raw)
     t.left_orthogonalize()
 
@@ -414,7 +428,10 @@ def main():
                 dtype="bf16+f32 (f64 vectors/SVD/coarse)" if args.prec == "bf16" else args.prec,
                 data="synthetic",
                 config=dict(workload=args.config, L=cfg["L"], n=cfg["n"], D=cfg["D"], P=P,
-                            partition=cfg["partition"], eig_tol=1e-6, svd_tol=1e-6,
+                            partition=kw["partition"], eig_tol=1e-6, svd_tol=1e-6,
+                            variant=("one-site" if args.one_site else "two-site")
+                            + (f", n_eig={args.n_eig}" if args.n_eig > 1 else "")
+                            + (", memory-limited environments" if args.low_memory else ""),
                             coarse_eps=kw["coarse_eps"],
                             precision=args.prec, solver=args.solver,
                             groups="sequential" if kw["sequential"] else "concurrent streams",
@@ -536,7 +553,7 @@ def e2e_run(a2, ctx, mpo, cfg, kw, cores, steps, torch, stream, world):
     for _ in range(steps):
         tt = a2.TT.from_cores(ctx, pinned)
         h2d += sum(c.nbytes for c in pinned)
-        rep = a2.additive_sweep(ctx, tt, mpo, cfg["P"], **kw)
+        rep = a2.additive_sweep(ctx, tt, mpo, len(kw["partition"]), **kw)
         out = tt.cores()
         d2h += sum(c.nbytes for c in out) + 8
         pinned = [torch.from_numpy(c).pin_memory().numpy() for c in out]
