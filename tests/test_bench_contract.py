@@ -1,0 +1,45 @@
+"""CPU: the benchmark's reference arm (the FP64 oracle timed on the host cores) prints one
+JSON line with the contract's keys, and the bench's pure helpers (roofline class mapping,
+per-rank throughput) behave as documented.  No GPU is touched."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+@pytest.mark.timeout(600)
+def test_reference_arm_json_line():
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], cwd=ROOT, capture_output=True, text=True,
+                         timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference"
+    assert d["value"] > 0 and d["higher_is_better"] is True
+    assert d["config"]["workload"] == "chem_L16_D256"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_roofline_class_mapping():
+    import bench
+    peaks = dict(hbm=6782.1, bf16_sus=1726.0, bf16=1918.6, src="test")
+    d = dict(ms=2.0, flops=4e12, bytes=8e9, launches=1)
+    assert bench.class_roofline("emu_s1", d, peaks, "bf16")[0] == "tensor"
+    b, u, p, a = bench.class_roofline("emu_s3", d, peaks, "bf16")
+    assert (b, u, p) == ("hbm", "GB/s", 6782.1) and abs(a - 4000.0) < 1e-9
+    assert bench.class_roofline("svd", d, peaks, "bf16")[0] == "alu"
+    assert "svd" in bench.LATENCY_BOUND and "lq" in bench.LATENCY_BOUND
+    for k, r in bench.DRAM_TRAFFIC_RATIO.items():
+        assert 0.5 < r < 5.0, k
