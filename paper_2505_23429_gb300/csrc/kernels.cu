@@ -280,6 +280,7 @@ constexpr int kSparseRowsPerCta = 16;
 // and 64 rows per CTA with CUDA events on the caller's stream and keeps the fastest.  Only
 // launches whose output does not depend on its previous contents are tuned (re-running
 // them is harmless); the others use kSparseRowsPerCta.
+namespace {
 struct SparseTuneKey {
   int kid, nrows, veclen, batches;
   long long nnz;
@@ -325,6 +326,7 @@ int sparse_rows_tuned(const SparseTuneKey& key, bool tunable, Launch&& launch, c
   g_sp_tune[key] = best;
   return best;
 }
+}  // namespace
 
 // Vectorised variant: each lane owns VEC consecutive vector elements (16-byte loads),
 // `lpr` lanes cover one row chunk of lpr*VEC elements, a warp serves 32/lpr rows at a
