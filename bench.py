@@ -79,6 +79,8 @@ def parse():
                    help="Extension One: eigenvectors kept per group's last local problem")
     p.add_argument("--low-memory", action="store_true",
                    help="memory-limited environment mode (environments rebuilt on demand)")
+    p.add_argument("--graphs", action="store_true",
+                   help="replay every local operator's H_eff applications from a CUDA graph")
     p.add_argument("--f64emu", action="store_true",
                    help="--profile-matvec also applies the FP64-emulated chain")
     return p.parse_args()
@@ -338,6 +340,8 @@ def main():
         kw["n_eig"] = args.n_eig
     if args.low_memory:
         kw["low_memory"] = True
+    if args.graphs:
+        kw["graphs"] = True
     t = a2.TT.from_cores(ctx, raw)
     t.left_orthogonalize()
 
@@ -431,7 +435,8 @@ def main():
                             partition=kw["partition"], eig_tol=1e-6, svd_tol=1e-6,
                             variant=("one-site" if args.one_site else "two-site")
                             + (f", n_eig={args.n_eig}" if args.n_eig > 1 else "")
-                            + (", memory-limited environments" if args.low_memory else ""),
+                            + (", memory-limited environments" if args.low_memory else "")
+                            + (", CUDA-graph matvecs" if args.graphs else ""),
                             coarse_eps=kw["coarse_eps"],
                             precision=args.prec, solver=args.solver,
                             groups="sequential" if kw["sequential"] else "concurrent streams",

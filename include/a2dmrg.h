@@ -162,6 +162,11 @@ typedef struct {
                                   entry rebuilds the two it needs from the chain ends
                                   (storage O(r^2 R), O(d) more environment updates);
                                   results agree to the rounding of the precision */
+  int graphs;                  /* 1: every local operator's H_eff application is captured
+                                  once into a CUDA graph (after one eager application) and
+                                  replayed by the eigensolver, one launch per application;
+                                  results are those of the eager path.  The profiler then
+                                  books replayed applications as a whole (kind 17). */
 } a2_sweep_opts;
 
 typedef struct {
@@ -298,7 +303,8 @@ a2_status a2_device_error(a2_ctx* ctx, int reset, int* code_out);
  * 1 sparse S2, 2 sparse S3, 3 tcgen05 S4, 4 SIMT H_eff, 5 environment update,
  * 6 Lanczos vector work, 7 truncated SVD, 8 LQ/QR, 9-12 the four stages of the
  * FP32-accurate split-product H_eff, 13-16 the FP64-emulated H_eff: S1, the sparse
- * stages, S4, the operand slicing) into the host outputs
+ * stages, S4, the operand slicing, 17 H_eff applications replayed from CUDA graphs)
+ * into the host outputs
  * (launches, milliseconds, algorithmic flops, algorithmic bytes; any may be NULL).
  * op 4 returns in *launches the number of kernel launches this library has made
  * since the process started (all of its own kernels, library calls excluded). */

@@ -32,7 +32,8 @@ class SweepOpts(ctypes.Structure):
                 ("max_krylov", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("prec", ctypes.c_int), ("refine_f64", ctypes.c_int), ("solver", ctypes.c_int),
                 ("group_streams", ctypes.c_int), ("one_site", ctypes.c_int),
-                ("n_eig", ctypes.c_int), ("env_mode", ctypes.c_int)]
+                ("n_eig", ctypes.c_int), ("env_mode", ctypes.c_int),
+                ("graphs", ctypes.c_int)]
 
 
 class SweepReport(ctypes.Structure):
@@ -272,7 +273,7 @@ class MPO:
 
 def _opts(L, P, partition, D_max, svd_tol, eig_tol, coarse_eps, max_krylov, max_restarts, prec,
           refine, solver="lanczos", sequential=False, one_site=False, n_eig=1,
-          low_memory=False):
+          low_memory=False, graphs=False):
     o = SweepOpts()
     o.P = P
     part = None
@@ -288,20 +289,22 @@ def _opts(L, P, partition, D_max, svd_tol, eig_tol, coarse_eps, max_krylov, max_
     o.one_site = 1 if one_site else 0
     o.n_eig = n_eig
     o.env_mode = 1 if low_memory else 0
+    o.graphs = 1 if graphs else 0
     return o, part
 
 
 def _sweep(fn, ctx, tt, mpo, P, partition=None, D_max=64, svd_tol=1e-10, eig_tol=1e-10,
            coarse_eps=1e-10, max_krylov=40, max_restarts=200, prec="fp64", refine=2,
-           solver="lanczos", sequential=False, one_site=False, n_eig=1, low_memory=False):
+           solver="lanczos", sequential=False, one_site=False, n_eig=1, low_memory=False,
+           graphs=False):
     """one_site=True: the one-site case of Alg. 2 (partition over the L cores);
     n_eig = K > 1: Extension One (K eigenvectors of each group's last local problem);
     low_memory=True: the memory-limited environment mode (environments rebuilt on
-    demand, none kept)."""
+    demand, none kept); graphs=True: H_eff applications replayed from CUDA graphs."""
     L = len(tt.phys)
     o, part = _opts(L, P, partition, D_max, svd_tol, eig_tol, coarse_eps, max_krylov,
                     max_restarts, prec, refine, solver, sequential, one_site, n_eig,
-                    low_memory)
+                    low_memory, graphs)
     m = P * max(1, n_eig) + 1
     bufs = dict(energy_local=np.zeros(m - 1), coeffs=np.zeros(m), S_hat=np.zeros(m * m),
                 A_hat=np.zeros(m * m))
@@ -416,7 +419,7 @@ def device_error(ctx, reset=True):
 
 PROFILE_KINDS = ["tc_s1", "sparse_s2", "sparse_s3", "tc_s4", "heff_simt", "env", "lanczos",
                  "svd", "lq", "emu_s1", "emu_s2", "emu_s3", "emu_s4", "f64e_s1", "f64e_sparse",
-                 "f64e_s4", "f64e_split"]
+                 "f64e_s4", "f64e_split", "heff_graph"]
 
 
 def profile(ctx, op, kind=0):

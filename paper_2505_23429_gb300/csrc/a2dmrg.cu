@@ -1117,6 +1117,95 @@ std::vector<double> deflated_eigs(a2_ctx* c, MV&& mv, const double* start, const
   return th;
 }
 
+// H_eff applications of one local problem replayed from a CUDA graph (one launch per
+// application instead of one per stage kernel): the first call runs eagerly (it sizes
+// the scratch buffers and lets the autotuners settle), the second is captured on the
+// caller's stream and instantiated, later calls launch the graph.  The graph's pointers
+// are fixed, so the vectors pass through two device buffers of its own.  Whatever cannot
+// be captured (a synchronisation, an allocation) ends the capture and the applications
+// stay eager.  Replays add the eager application's launch and flop counts to the
+// counters, and their time to the profiler class PK_HEFF_GRAPH.
+struct GraphedMV {
+  a2_ctx* c;
+  long long N;
+  int state = 0;            // 0 eager next, 1 capture next, 2 replay, 3 eager for good
+  DevBuf xg, yg;
+  cudaGraphExec_t exec = nullptr;
+  long long launches = 0, mvs = 0, mvs16 = 0;
+  double flops = 0.0;
+  GraphedMV(a2_ctx* c_, long long n) : c(c_), N(n) {}
+  GraphedMV(const GraphedMV&) = delete;
+  GraphedMV& operator=(const GraphedMV&) = delete;
+  ~GraphedMV() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+  template <class MV, class Eng>
+  void operator()(MV&& mv, Eng& eng, const double* in, double* out) {
+    cudaStream_t s = c->stream;
+    if (state == 3) {
+      mv(in, out);
+      return;
+    }
+    xg.ensure(sizeof(double) * N, s);
+    yg.ensure(sizeof(double) * N, s);
+    A2_CUDA(cudaMemcpyAsync(xg.p, in, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    if (state == 0) {
+      const long long l0 = launch_count(), m0 = eng.matvecs, b0 = eng.matvecs_bf16;
+      const double f0 = eng.flops;
+      mv(xg.as<double>(), yg.as<double>());
+      launches = launch_count() - l0;
+      mvs = eng.matvecs - m0;
+      mvs16 = eng.matvecs_bf16 - b0;
+      flops = eng.flops - f0;
+      state = 1;
+    } else {
+      if (state == 1) {
+        cudaGraph_t g = nullptr;
+        const long long l0 = launch_count(), m0 = eng.matvecs, b0 = eng.matvecs_bf16;
+        const double f0 = eng.flops;
+        bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+          set_capturing(true);
+          try {
+            mv(xg.as<double>(), yg.as<double>());
+          } catch (...) {
+            ok = false;
+          }
+          set_capturing(false);
+          // captured launches did not run: take back what the capture counted
+          count_launches(l0 - launch_count());
+          eng.matvecs = m0;
+          eng.matvecs_bf16 = b0;
+          eng.flops = f0;
+          ok = (cudaStreamEndCapture(s, &g) == cudaSuccess) && ok && g;
+          if (ok) ok = cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+          if (g) cudaGraphDestroy(g);
+        }
+        if (!ok) {
+          (void)cudaGetLastError();   // capture errors are not sticky
+          if (exec) cudaGraphExecDestroy(exec);
+          exec = nullptr;
+          state = 3;
+          A2_CUDA(cudaMemcpyAsync(xg.p, in, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+          mv(xg.as<double>(), yg.as<double>());
+          A2_CUDA(cudaMemcpyAsync(out, yg.p, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+          return;
+        }
+        state = 2;
+      }
+      {
+        ProfScope ps(PK_HEFF_GRAPH, s, flops, 0.0);
+        A2_CUDA(cudaGraphLaunch(exec, s));
+      }
+      count_launches(launches);
+      eng.matvecs += mvs;
+      eng.matvecs_bf16 += mvs16;
+      eng.flops += flops;
+    }
+    A2_CUDA(cudaMemcpyAsync(out, yg.p, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  }
+};
+
 // Diagonal of H_eff at bond k (FP64): diag[a,s1,s2,b] = sum_{w,w1,w2} L[a,w,a]
 // A_k[w,s1,s1,w1] A_k+1[w1,s2,s2,w2] R[b,w2,b] (preconditioner of the Davidson solver).
 template <typename T>
@@ -1525,7 +1614,7 @@ struct Sweeper {
         if (o.prec == A2_F64EMU)
           eng.oze.set(c, HLcur, Dl, mpo->R[k], HRk, Dr, mpo->R[k + 2]);
       }
-      auto mv = [&](const double* in, double* out) {
+      auto mv_raw = [&](const double* in, double* out) {
         if constexpr (sizeof(T) == 8) {
           if (o.prec == A2_F64EMU) {
             eng.matvec_f64e(k, Dl, Dr, in, out);
@@ -1534,6 +1623,15 @@ struct Sweeper {
         }
         eng.matvec(k, HLcur, HRk, Dl, Dr, in, out);
       };
+      // with o.graphs, every operator of this local problem is replayed from a CUDA graph
+      GraphedMV g_mv(c, N), g_b(c, N), g_e(c, N);
+      auto graphed = [&](GraphedMV& g, auto& f) {
+        return [&g, &f, &eng, this](const double* in, double* out) {
+          if (o.graphs) g(f, eng, in, out);
+          else f(in, out);
+        };
+      };
+      auto mv = graphed(g_mv, mv_raw);
       const bool ext = o.n_eig > 1 && k == G.mg;
       DevBuf xstart;   // Extension One: start vector of the further eigenvectors
       if (ext) {
@@ -1552,7 +1650,10 @@ struct Sweeper {
           if (o.prec == A2_BF16 || o.prec == A2_F32EMU) {
             eng.bfe.set(c, HLcur, Dl, mpo->R[k], HRk, Dr, mpo->R[k + 2], 3, &mpo->site[k],
                          &mpo->site[k + 1]);
-            auto mve = [&](const double* in, double* out) { eng.matvec_emu(k, Dl, Dr, in, out); };
+            auto mve_raw = [&](const double* in, double* out) {
+              eng.matvec_emu(k, Dl, Dr, in, out);
+            };
+            auto mve = graphed(g_e, mve_raw);
             lr = davidson(c, mve, dg.as<double>(), x.as<double>(), N, o.eig_tol, o.max_krylov,
                           o.max_krylov * o.max_restarts);
             done = true;
@@ -1569,13 +1670,19 @@ struct Sweeper {
                          &mpo->site[k + 1]);
           if (o.prec == A2_BF16) {
             // tensor-core Lanczos on the BF16 operator to a loose tolerance ...
-            auto mvb = [&](const double* in, double* out) { eng.matvec_bf16(k, Dl, Dr, in, out); };
+            auto mvb_raw = [&](const double* in, double* out) {
+              eng.matvec_bf16(k, Dl, Dr, in, out);
+            };
+            auto mvb = graphed(g_b, mvb_raw);
             LanczosResult lb = lanczos(c, mvb, x.as<double>(), N, std::max(o.eig_tol, kBf16Tol),
                                        o.max_krylov, o.max_restarts);
             nmv += lb.matvecs;
           }
           // ... then FP32-accurate tensor-core products from that vector to eig_tol
-          auto mve = [&](const double* in, double* out) { eng.matvec_emu(k, Dl, Dr, in, out); };
+          auto mve_raw = [&](const double* in, double* out) {
+            eng.matvec_emu(k, Dl, Dr, in, out);
+          };
+          auto mve = graphed(g_e, mve_raw);
           lr = lanczos(c, mve, x.as<double>(), N, o.eig_tol, o.max_krylov, o.max_restarts);
           done = true;
         }
@@ -1702,9 +1809,14 @@ struct Sweeper {
           tc1 = true;
         }
       }
-      auto mv = [&](const double* in, double* out) {
+      auto mv_raw = [&](const double* in, double* out) {
         if (tc1) eng.matvec1_emu(j, Dl, Dr, in, out);
         else eng.matvec1(j, HLcur, HRj, Dl, Dr, in, out);
+      };
+      GraphedMV g_mv(c, N);   // with o.graphs, replayed from a CUDA graph
+      auto mv = [&](const double* in, double* out) {
+        if (o.graphs) g_mv(mv_raw, eng, in, out);
+        else mv_raw(in, out);
       };
       const bool ext = o.n_eig > 1 && j == last;
       DevBuf xstart;

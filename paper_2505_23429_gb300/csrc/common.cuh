@@ -30,6 +30,8 @@ struct NumericError : std::runtime_error {
 // Every kernel launch of this library goes through A2_CHECK_LAUNCH, which also counts it.
 void count_launch();
 long long launch_count();
+void count_launches(long long n);     // n launches replayed from a CUDA graph
+void set_capturing(bool on);          // this thread is capturing a CUDA graph
 #define A2_CHECK_LAUNCH()            \
   do {                               \
     ::a2::count_launch();            \
@@ -102,6 +104,7 @@ enum ProfKind {
   PK_F64E_SPARSE,    // FP64 sparse S2 + S3 of the emulated H_eff
   PK_F64E_S4,        // FP64-emulated S4
   PK_F64E_SPLIT,     // Ozaki slicing of operands
+  PK_HEFF_GRAPH,     // H_eff applications replayed from a CUDA graph (all stages)
   PK_COUNT
 };
 void prof_enable(bool on);

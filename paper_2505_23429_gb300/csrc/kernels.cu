@@ -38,7 +38,13 @@ namespace {
 std::atomic<long long> g_launches{0};
 }
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+// Set while this thread captures a stream into a CUDA graph: the profiler's event pairs
+// are then skipped (a replayed graph does not re-record them).
+thread_local bool t_capturing = false;
+void set_capturing(bool on) { t_capturing = on; }
 
 // ----------------------------------------------------------------------------- profiler
 namespace {
@@ -90,7 +96,7 @@ bool prof_enabled() { return P().on; }
 
 ProfScope::ProfScope(int kind, cudaStream_t stream, double flops, double bytes) : s(stream) {
   ProfState& st = P();
-  if (!st.on) return;
+  if (!st.on || t_capturing) return;
   std::lock_guard<std::mutex> g(st.mu);
   ProfRec r{kind, st.get(), st.get(), flops, bytes};
   A2_CUDA(cudaEventRecord(r.a, stream));

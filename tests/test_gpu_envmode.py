@@ -70,3 +70,29 @@ def test_low_memory_against_oracle(ctx):
     assert abs(rep["lambda_coarse"] - rep0["lambda_coarse"]) < 1e-10 * abs(rep0["lambda_coarse"])
     E, _ = a2.energy(ctx, t, mpo)
     assert abs(E - rep0["energy"]) < 1e-10 * abs(E)
+
+
+@pytest.mark.parametrize("prec,one_site", [("fp64", False), ("bf16", False), ("fp32", True),
+                                           ("f64emu", False)])
+def test_cuda_graph_matvecs_match_eager(ctx, prec, one_site):
+    """H_eff applications replayed from CUDA graphs give the eager path's iteration (to the
+    rounding of the precision; split-K tiles are added with atomics)."""
+    L = 8
+    h, eri = chemistry_integrals(L, 2505)
+    m = chemistry_mpo(h, eri)
+    raw = random_tt_cores([4] * L, 8, 77)
+    sizes = [3, 3, 2] if one_site else [3, 2, 2]
+    mpo = a2.MPO(ctx, m)
+    out = {}
+    for graphs in (False, True):
+        t = a2.TT.from_cores(ctx, raw)
+        t.left_orthogonalize()
+        reps = [a2.additive_sweep(ctx, t, mpo, len(sizes), partition=sizes, D_max=8, prec=prec,
+                                  one_site=one_site, graphs=graphs, sequential=True, **KW)
+                for _ in range(2)]
+        out[graphs] = (reps, a2.energy(ctx, t, mpo)[0])
+    tol = 1e-11 if prec in ("fp64", "f64emu") else 2e-6
+    for r0, r1 in zip(out[False][0], out[True][0]):
+        assert abs(r0["lambda_coarse"] - r1["lambda_coarse"]) < tol * abs(r0["lambda_coarse"])
+        assert r0["matvecs"] == r1["matvecs"] or prec not in ("fp64", "f64emu")
+    assert abs(out[False][1] - out[True][1]) < tol * abs(out[False][1])
