@@ -92,6 +92,19 @@ a2_status a2_tt_get_core(const a2_tt* tt, int site, int* Dl, int* n, int* Dr, do
 a2_status a2_tt_left_orthogonalize(a2_tt* tt, double* norm_out);
 a2_status a2_tt_destroy(a2_tt* tt);
 
+/* Checkpoint of the state between global iterations (Alg. 2 keeps exactly the
+ * left-orthogonal TT U^(n),d): a2_tt_save writes the TT to the file `path` (host path,
+ * replaced if it exists) as little-endian raw data: the 8 bytes "A2TTCKP1", int32 L,
+ * int32 phys[L], int32 bonds[L+1] (bonds[0] = bonds[L] = 1), then every core as FP64
+ * [Dl][n][Dr] row-major, site 0 first.  a2_tt_load reads such a file into a new TT of
+ * the context (the caller owns it; a2_tt_destroy).  Errors: A2_EINVAL (NULL arguments,
+ * unreadable / unwritable file, wrong magic, inconsistent or truncated contents, bond
+ * dims that do not chain), A2_ECUDA.  Resuming from the file repeats the iteration that
+ * follows the save, to the reproducibility of the precision (split-K tiles are added
+ * with atomics, so bitwise equality is not promised). */
+a2_status a2_tt_save(const a2_tt* tt, const char* path);
+a2_status a2_tt_load(a2_ctx* ctx, const char* path, a2_tt** out);
+
 /* ---- matrix product operator (eq. MPO) ------------------------------------ */
 
 /* Load L cores (host pointers) with MPO bond dims mpo_bonds[L+1] (first and

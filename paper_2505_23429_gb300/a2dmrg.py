@@ -72,6 +72,8 @@ def lib():
         "a2_tt_get_core": [_P, ctypes.c_int, _I, _I, _I, _D],
         "a2_tt_left_orthogonalize": [_P, _D],
         "a2_tt_destroy": [_P],
+        "a2_tt_save": [_P, ctypes.c_char_p],
+        "a2_tt_load": [_P, ctypes.c_char_p, ctypes.POINTER(_P)],
         "a2_mpo_load": [_P, ctypes.c_int, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_P)],
         "a2_mpo_nnz": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)],
         "a2_mpo_destroy": [_P],
@@ -213,6 +215,21 @@ class TT:
 
     def cores(self):
         return [self.core(j) for j in range(len(self.phys))]
+
+    def save(self, path):
+        """Checkpoint (a2_tt_save): the TT's cores and dims to the host file `path`."""
+        self.ctx.check(lib().a2_tt_save(self._h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, ctx, path):
+        """A new TT from a checkpoint written by save (a2_tt_load)."""
+        h = _P()
+        ctx.check(lib().a2_tt_load(ctx._h, os.fsencode(path), ctypes.byref(h)))
+        with open(path, "rb") as f:   # the site count and physical dims of the header
+            f.read(8)
+            L = int(np.frombuffer(f.read(4), dtype="<i4")[0])
+            phys = np.frombuffer(f.read(4 * L), dtype="<i4").tolist()
+        return cls(ctx, h, phys)
 
     def left_orthogonalize(self):
         nrm = ctypes.c_double()

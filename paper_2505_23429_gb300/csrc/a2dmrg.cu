@@ -10,6 +10,7 @@
 //   S2 T2[a,w1,s1,t2,b'] = sum_{w,t1} A_k[w,s1,t1,w1] T1[...]       sparse MPO action
 //   S3 T3[a,s1,s2,w2,b'] = sum_{w1,t2} A_k+1[w1,s2,t2,w2] T2[...]   sparse MPO action
 //   S4 y[a,s1,s2,b]      = sum_{w2,b'} T3[...] R[b,w2,b']            dense GEMM (split K)
+#include <cstdio>
 #include <algorithm>
 #include <atomic>
 #include <array>
@@ -2589,6 +2590,86 @@ a2_status a2_tt_get_core(const a2_tt* t, int site, int* Dl, int* n, int* Dr, dou
       A2_CUDA(cudaStreamSynchronize(c->stream));
     }
   });
+}
+
+a2_status a2_tt_save(const a2_tt* t, const char* path) {
+  if (!t) return A2_EINVAL;
+  a2_ctx* c = t->ctx;
+  return guarded(c, [&] {
+    A2_REQUIRE(path, "a2_tt_save: null path");
+    tt_check(t);
+    std::FILE* f = std::fopen(path, "wb");
+    A2_REQUIRE(f, "a2_tt_save: cannot open the file for writing");
+    bool ok = std::fwrite("A2TTCKP1", 1, 8, f) == 8;
+    const int32_t L = t->L;
+    ok = ok && std::fwrite(&L, sizeof(L), 1, f) == 1;
+    std::vector<int32_t> ph(t->phys.begin(), t->phys.end()), bd(t->dims.begin(), t->dims.end());
+    ok = ok && std::fwrite(ph.data(), sizeof(int32_t), ph.size(), f) == ph.size();
+    ok = ok && std::fwrite(bd.data(), sizeof(int32_t), bd.size(), f) == bd.size();
+    std::vector<double> h;
+    for (int j = 0; ok && j < t->L; ++j) {
+      const size_t nel = (size_t)t->dims[j] * t->phys[j] * t->dims[j + 1];
+      h.resize(nel);
+      A2_CUDA(cudaMemcpyAsync(h.data(), t->cores[j].p, sizeof(double) * nel,
+                              cudaMemcpyDeviceToHost, c->stream));
+      A2_CUDA(cudaStreamSynchronize(c->stream));
+      ok = std::fwrite(h.data(), sizeof(double), nel, f) == nel;
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    A2_REQUIRE(ok, "a2_tt_save: write failed");
+  });
+}
+
+a2_status a2_tt_load(a2_ctx* c, const char* path, a2_tt** out) {
+  if (!c || !out) return c ? fail(c, A2_EINVAL, "a2_tt_load: null argument") : A2_EINVAL;
+  *out = nullptr;
+  auto* t = new (std::nothrow) a2_tt();
+  if (!t) return A2_ENOMEM;
+  a2_status st = guarded(c, [&] {
+    A2_REQUIRE(path, "a2_tt_load: null path");
+    std::FILE* f = std::fopen(path, "rb");
+    A2_REQUIRE(f, "a2_tt_load: cannot open the file");
+    struct Closer {
+      std::FILE* f;
+      ~Closer() { std::fclose(f); }
+    } closer{f};
+    char magic[8];
+    A2_REQUIRE(std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "A2TTCKP1", 8) == 0,
+               "a2_tt_load: not a TT checkpoint");
+    int32_t L = 0;
+    A2_REQUIRE(std::fread(&L, sizeof(L), 1, f) == 1 && L >= 2 && L <= (1 << 20),
+               "a2_tt_load: bad site count");
+    std::vector<int32_t> ph(L), bd(L + 1);
+    A2_REQUIRE(std::fread(ph.data(), sizeof(int32_t), L, f) == (size_t)L &&
+                   std::fread(bd.data(), sizeof(int32_t), L + 1, f) == (size_t)(L + 1),
+               "a2_tt_load: truncated header");
+    A2_REQUIRE(bd[0] == 1 && bd[L] == 1, "a2_tt_load: boundary bonds must be 1");
+    for (int j = 0; j < L; ++j)
+      A2_REQUIRE(ph[j] >= 1 && bd[j] >= 1 && bd[j + 1] >= 1 &&
+                     (double)bd[j] * ph[j] * bd[j + 1] < 4e9,
+                 "a2_tt_load: bad dimensions");
+    t->ctx = c;
+    t->L = L;
+    t->phys.assign(ph.begin(), ph.end());
+    t->dims.assign(bd.begin(), bd.end());
+    t->cores.resize(L);
+    std::vector<double> h;
+    for (int j = 0; j < L; ++j) {
+      const size_t nel = (size_t)bd[j] * ph[j] * bd[j + 1];
+      h.resize(nel);
+      A2_REQUIRE(std::fread(h.data(), sizeof(double), nel, f) == nel, "a2_tt_load: truncated core");
+      upload(t->cores[j], h.data(), sizeof(double) * nel, c->stream);
+      A2_CUDA(cudaStreamSynchronize(c->stream));   // h is reused for the next core
+    }
+    char extra;
+    A2_REQUIRE(std::fread(&extra, 1, 1, f) == 0, "a2_tt_load: trailing data");
+  });
+  if (st != A2_OK) {
+    delete t;
+    return st;
+  }
+  *out = t;
+  return A2_OK;
 }
 
 a2_status a2_tt_left_orthogonalize(a2_tt* t, double* norm_out) {
