@@ -11,6 +11,7 @@
 //   S3 T3[a,s1,s2,w2,b'] = sum_{w1,t2} A_k+1[w1,s2,t2,w2] T2[...]   sparse MPO action
 //   S4 y[a,s1,s2,b]      = sum_{w2,b'} T3[...] R[b,w2,b']            dense GEMM (split K)
 #include <cstdio>
+#include <nvtx3/nvToolsExt.h>
 #include <algorithm>
 #include <atomic>
 #include <array>
@@ -58,6 +59,20 @@ struct a2_tt {
 };
 
 namespace {
+
+// NVTX range for the steps of a global iteration (visible to nsys / ncu --nvtx; free
+// when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  NvtxRange(const char* name, int i) {
+    char buf[64];
+    std::snprintf(buf, sizeof(buf), "%s %d", name, i);
+    nvtxRangePushA(buf);
+  }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct SiteOps {
   int Rl = 0, n = 0, Rr = 0;
@@ -1603,6 +1618,7 @@ struct Sweeper {
     DevBuf HLbuf, HRbuf;
     const T* HLcur = hl_at(G.kg, eng, HLbuf);
     for (int k = G.kg; k <= G.mg; ++k) {
+      NvtxRange r_local("a2: local solve at bond", k);
       const int n1 = tt->phys[k], n2 = tt->phys[k + 1];
       const int Dr = kd[k + 2];
       const long long N = (long long)Dl * n1 * n2 * Dr;
@@ -1799,6 +1815,7 @@ struct Sweeper {
     DevBuf HLbuf, HRbuf;
     const T* HLcur = hl_at(first, eng, HLbuf);
     for (int j = first; j <= last; ++j) {
+      NvtxRange r_local("a2: one-site local solve at core", j);
       const int n = tt->phys[j], Dr = kd[j + 1];
       const long long N = (long long)Dl * n * Dr;
       const T* HRj = hr_at(j + 1, eng, HRbuf);
@@ -2032,8 +2049,14 @@ struct Sweeper {
     A2_REQUIRE(o.D_max >= 1, "D_max >= 1");
     A2_REQUIRE(o.max_krylov >= 2 && o.max_krylov <= 63, "max_krylov in 2..63");
     kry.assign(units, 0);
-    step1();
-    build_envs();
+    {
+      NvtxRange r("a2: step 1 (LQ sweep)");
+      step1();
+    }
+    {
+      NvtxRange r("a2: environments");
+      build_envs();
+    }
     // groups as blocks of modified cores [kg, mg + 1]: two-site, bonds kg..mg; one-site,
     // cores kg..mg + 1
     std::vector<Group> groups(P);
@@ -2044,6 +2067,7 @@ struct Sweeper {
       k0 += sizes[g];
     }
     auto solve = [&](Group& G, a2_ctx* lc, Engine<T>& e) {
+      NvtxRange r("a2: group from site", G.kg);
       if (one) solve_group1(G, lc, e);
       else solve_group(G, lc, e);
     };
@@ -2091,6 +2115,7 @@ struct Sweeper {
     const int m = (int)items.size() + 1;
     A2_REQUIRE(m <= 63, "coarse dimension (P * n_eig + 1) above 63");
     std::vector<double> S((size_t)m * m, 0.0), A((size_t)m * m, 0.0);
+    NvtxRange r_coarse("a2: coarse problem and compression");
     // iterate: its (L-1)-orthogonal form is the stored left-orthogonal TT
     {
       View b = base_view(L - 1);
@@ -2144,6 +2169,7 @@ struct Sweeper {
     check_finite(lam, "coarse eigenvalue");
     // Step 4: compression of sum_j c_j tau(U~^j) from its three-channel TT form
     {
+      NvtxRange r("a2: compression");
       std::vector<DevBuf> X;
       std::vector<int> xd;
       if (m == P + 1) {
