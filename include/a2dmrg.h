@@ -200,6 +200,10 @@ typedef struct {
   double alg_flops;            /* algorithmic flops of the contractions performed */
   long long matvecs;           /* H_eff applications in the call */
   int coarse_dim;              /* m, the number of coarse basis vectors used */
+  int unconverged;             /* local eigensolves that stopped after max_restarts cycles
+                                  with the residual still above eig_tol: their last Ritz
+                                  pair is accepted (the coarse step and the compression use
+                                  it) and counted here */
 } a2_sweep_report;
 
 /* One global iteration of two-site A2DMRG (Alg. 2, with P groups of adjoining

@@ -46,7 +46,7 @@ class SweepReport(ctypes.Structure):
                 ("krylov_iters", ctypes.POINTER(ctypes.c_int)),
                 ("max_discarded_weight", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("alg_flops", ctypes.c_double), ("matvecs", ctypes.c_longlong),
-                ("coarse_dim", ctypes.c_int)]
+                ("coarse_dim", ctypes.c_int), ("unconverged", ctypes.c_int)]
 
 
 _lib = None
@@ -336,6 +336,7 @@ def _sweep(fn, ctx, tt, mpo, P, partition=None, D_max=64, svd_tol=1e-10, eig_tol
                matvecs=r.matvecs, krylov=kry.tolist())
     m = r.coarse_dim
     out["coarse_dim"] = m
+    out["unconverged"] = r.unconverged
     out["energy_local"] = bufs["energy_local"][:m - 1]
     out["coeffs"] = bufs["coeffs"][:m]
     out["S_hat"] = bufs["S_hat"][:m * m].reshape(m, m)

@@ -1083,7 +1083,8 @@ LanczosResult lanczos(a2_ctx* c, MV&& mv, double* x, long long N, double tol, in
 template <class MV>
 std::vector<double> deflated_eigs(a2_ctx* c, MV&& mv, const double* start, const double* x1,
                                   long long N, int K, double tol, int max_krylov,
-                                  int max_cycles, DevBuf& Q, int* matvecs) {
+                                  int max_cycles, DevBuf& Q, int* matvecs,
+                                  std::atomic<int>* unconverged = nullptr) {
   cudaStream_t s = c->stream;
   K = (int)std::min<long long>(K, N);
   A2_REQUIRE(K >= 1 && K <= 64, "n_eig: at most 64 eigenvectors per local problem");
@@ -1125,6 +1126,7 @@ std::vector<double> deflated_eigs(a2_ctx* c, MV&& mv, const double* start, const
     };
     LanczosResult lr = lanczos(c, mvd, v, N, tol, max_krylov, max_cycles);
     check_finite(lr.theta, "local eigenvalue (deflated)");
+    if (!lr.converged && unconverged) unconverged->fetch_add(1);
     project(v, e);
     normalise(v);
     th.push_back(lr.theta);
@@ -1487,6 +1489,7 @@ struct Sweeper {
   std::vector<DevBuf> Vc, Cc;         // right-orth cores V_i, centres C_i
   std::vector<int> kd;                // bond dims of the right-orthogonal part
   std::vector<int> kry;
+  std::atomic<int> unconv{0};   // local eigensolves stopped at max_restarts above eig_tol
   double max_disc = 0.0;
 
   Sweeper(a2_ctx* c_, a2_tt* t, const a2_mpo* m, const a2_sweep_opts& op)
@@ -1708,6 +1711,7 @@ struct Sweeper {
         lr = lanczos(c, mv, x.as<double>(), N, o.eig_tol, o.max_krylov, o.max_restarts);
       check_finite(lr.theta, "local eigenvalue");
       kry[k] = nmv + lr.matvecs;
+      if (!lr.converged) unconv.fetch_add(1);
       G.theta = lr.theta;
       const int rows = Dl * n1, cols = n2 * Dr;
       if (ext) {
@@ -1726,7 +1730,7 @@ struct Sweeper {
         int nx = 0;
         std::vector<double> th = deflated_eigs(c, mvx, xstart.as<double>(), x.as<double>(), N,
                                                o.n_eig, o.eig_tol, o.max_krylov, o.max_restarts,
-                                               Qx, &nx);
+                                               Qx, &nx, &unconv);
         kry[k] += nx;
         for (size_t e = 0; e < th.size(); ++e) {
           Tail t;
@@ -1847,13 +1851,14 @@ struct Sweeper {
                                  o.max_restarts);
       check_finite(lr.theta, "local eigenvalue");
       kry[j] = lr.matvecs;
+      if (!lr.converged) unconv.fetch_add(1);
       G.theta = lr.theta;
       if (ext) {   // Extension One: each further eigenvector replaces the last core
         DevBuf Qx;
         int nx = 0;
         std::vector<double> th = deflated_eigs(c, mv, xstart.as<double>(), centre.as<double>(),
                                                N, o.n_eig, o.eig_tol, o.max_krylov,
-                                               o.max_restarts, Qx, &nx);
+                                               o.max_restarts, Qx, &nx, &unconv);
         kry[j] += nx;
         for (size_t e = 0; e < th.size(); ++e) {
           Tail t;
@@ -2049,6 +2054,7 @@ struct Sweeper {
     A2_REQUIRE(o.D_max >= 1, "D_max >= 1");
     A2_REQUIRE(o.max_krylov >= 2 && o.max_krylov <= 63, "max_krylov in 2..63");
     kry.assign(units, 0);
+    unconv.store(0);
     {
       NvtxRange r("a2: step 1 (LQ sweep)");
       step1();
@@ -2198,6 +2204,7 @@ struct Sweeper {
       rep->max_discarded_weight = max_disc;
       rep->alg_flops = eng.flops;
       rep->matvecs = eng.matvecs;
+      rep->unconverged = unconv.load();
       A2_CUDA(cudaStreamSynchronize(s));
       rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }

@@ -194,3 +194,24 @@ def test_concurrent_groups_match_sequential(ctx):
     assert abs(out[True][0]["lambda_coarse"] - out[False][0]["lambda_coarse"]) < 1e-12 * 10
     x, y = out[True][1], out[False][1]
     assert abs(abs(x @ y) - 1.0) < 1e-10
+
+
+def test_forced_nonconvergence_is_reported(ctx):
+    """Host-side failure injection: one restart cycle of a two-vector Krylov space cannot
+    reach eig_tol = 1e-14, so every local solve stops early; the iteration still completes
+    (the last Ritz pairs are accepted) and reports each such solve.  A normal run reports
+    none."""
+    L = 8
+    m = heisenberg_mpo(L)
+    raw, _ = _start([2] * L, 4, 11)
+    mpo = a2.MPO(ctx, m)
+    t = _gpu_tt(ctx, raw)
+    rep = a2.additive_sweep(ctx, t, mpo, 2, partition=[4, 3], D_max=8, prec="fp64",
+                            svd_tol=1e-10, eig_tol=1e-14, coarse_eps=1e-10, max_krylov=2,
+                            max_restarts=1)
+    assert rep["unconverged"] == L - 1
+    assert np.isfinite(rep["lambda_coarse"])
+    assert abs(a2.energy(ctx, t, mpo)[1] - 1.0) < 1e-12
+    t2 = _gpu_tt(ctx, raw)
+    rep2 = a2.additive_sweep(ctx, t2, mpo, 2, partition=[4, 3], D_max=8, prec="fp64", **KW)
+    assert rep2["unconverged"] == 0
