@@ -136,8 +136,10 @@ a2_status a2_mpo_set_fold(a2_mpo* mpo, int enable);
 /* ---- one global iteration -------------------------------------------------- */
 
 typedef struct {
-  int P;                       /* number of groups of bonds (subdomains), 1..L-1 */
-  const int* bond_partition;   /* P group sizes summing to L-1 (host), or NULL = even split */
+  int P;                       /* number of groups of bonds (subdomains), 1..L-1 (groups
+                                  of cores, 1..L, with one_site) */
+  const int* bond_partition;   /* P group sizes summing to L-1 (L with one_site) (host), or
+                                  NULL = even split */
   int D_max;                   /* rank cap of the truncated SVD steps and the compression */
   double svd_tol;              /* keep smallest r with discarded 2-norm <= svd_tol*||sigma|| */
   double eig_tol;              /* Lanczos: ||H x - theta x|| <= eig_tol*max(1,|theta|) */
@@ -207,9 +209,10 @@ typedef struct {
 } a2_sweep_report;
 
 /* One global iteration of two-site A2DMRG (Alg. 2, with P groups of adjoining
- * bonds swept as in Alg. 1 inside each group).  In: left-orthogonal TT of
- * norm 1 (U^(n),d).  Out (in place): the compressed left-orthogonal TT of
- * norm 1 (U^(n+1),d).  report may be NULL. */
+ * bonds swept as in Alg. 1 inside each group; the one-site case, Extension One and the
+ * memory-limited mode through the options).  In: left-orthogonal TT of norm 1
+ * (U^(n),d).  Out (in place): the compressed left-orthogonal TT of norm 1 (U^(n+1),d);
+ * on any error the input TT is restored.  report may be NULL. */
 a2_status a2_additive_sweep(a2_ctx* ctx, a2_tt* tt, const a2_mpo* mpo, const a2_sweep_opts* opts,
                             a2_sweep_report* report);
 
