@@ -34,8 +34,8 @@ METRIC = ("additive-sweep time to |dE|<1e-6 vs FP64 oracle; "
           "H_eff matvec TFLOP/s vs plain")
 # classes reported by time share only (latency-bound FP64 factorisations)
 LATENCY_BOUND = ("svd", "lq")
-# DRAM traffic / algorithmic bytes of a kernel class, from its ncu capture at D = 128
-# (profiles/sparse_rows_kernel_heff_D128.md); the bench scales it to its own launches
+# DRAM traffic / algorithmic bytes of a kernel class, from its ncu capture at D = 128;
+# the bench scales it to its own launches
 DRAM_TRAFFIC_RATIO = {"emu_s2": 0.963, "emu_s3": 0.961}
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 FP64_PEAK_TFLOPS = 1.2   # FP64 (SIMT) rate measured on this part with a DGEMM loop

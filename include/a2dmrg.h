@@ -202,10 +202,13 @@ typedef struct {
   double alg_flops;            /* algorithmic flops of the contractions performed */
   long long matvecs;           /* H_eff applications in the call */
   int coarse_dim;              /* m, the number of coarse basis vectors used */
-  int unconverged;             /* local eigensolves that stopped after max_restarts cycles
-                                  with the residual still above eig_tol: their last Ritz
-                                  pair is accepted (the coarse step and the compression use
-                                  it) and counted here */
+  int unconverged;             /* local eigensolves that stopped with the residual still
+                                  above eig_tol -- after max_restarts cycles, or (Davidson)
+                                  when the preconditioned residual adds no new direction to
+                                  the search space: their last Ritz pair is accepted (the
+                                  coarse step and the compression use it) and counted here.
+                                  A Lanczos breakdown (invariant Krylov space: the Ritz
+                                  pair is exact) counts as converged. */
 } a2_sweep_report;
 
 /* One global iteration of two-site A2DMRG (Alg. 2, with P groups of adjoining
@@ -349,7 +352,10 @@ a2_status a2_profile(a2_ctx* ctx, int op, int kind, long long* launches, double*
  *  - Every call shares the one array and leaves its contents behind; each call
  *    overwrites everything it reads.  Calls whose work overlaps on the GPU (other
  *    streams, other contexts on the same device) race on the array: order them.
- *  - y is overwritten (zeroed first when the last stage splits its reduction). */
+ *  - y is overwritten (zeroed first when the last stage splits its reduction).
+ *  - The device address of the array is looked up once per device and kept for the life
+ *    of the library: do not reset a device (cudaDeviceReset) while the library is loaded
+ *    and still in use on it. */
 a2_status a2_heff_apply_noalloc(a2_ctx* ctx, const a2_mpo* mpo, int k, int Dl, int Dr,
                                 const double* L, const double* R, const double* x, double* y);
 

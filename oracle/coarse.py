@@ -6,7 +6,8 @@ Sec. 3.1 with the tolerance eps), form the reduced symmetric problem
     Sig+^{-1/2} V+^T A_hat V+ Sig+^{-1/2} z = lambda z      (eq. aux_eig_final_sym)
 and return lambda_min and c = V+ Sig+^{-1/2} z (so c^T S_hat c = 1).  Sign
 convention: c_0 >= 0, or if c_0 = 0 the entry of largest magnitude is positive.
-Pinned by tests/test_oracle_coarse.py against scipy.linalg.eigh(A, S).
+Pinned by tests/test_oracle_dmrg.py (the coarse-solve test against
+scipy.linalg.eigh(A, S), including a rank-deficient S).
 """
 import numpy as np
 
