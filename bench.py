@@ -59,7 +59,9 @@ def parse():
                         "concurrently on one stream per group")
     p.add_argument("--sequential", action="store_true", help="same as --groups sequential")
     p.add_argument("--coarse-eps", type=float, default=None,
-                   help="S_hat eigenvalue cut (default 1e-10 for fp64, 1e-5 otherwise)")
+                   help="S_hat eigenvalue cut (default 1e-10; 1e-5 for plain fp32)")
+    p.add_argument("--no-refine", action="store_true",
+                   help="bf16 / f32emu: skip the FP64 refinement of the local Ritz pairs")
     p.add_argument("--no-fold", action="store_true",
                    help="keep every MPO core fully sparse (no identity-block fold)")
     p.add_argument("--config", default="chem_L16_D256")
@@ -101,14 +103,13 @@ def workload(name):
     return cfg, mpo, raw
 
 
-def sweep_kwargs(cfg, prec, solver="lanczos", coarse_eps=None):
+def sweep_kwargs(cfg, prec, solver="lanczos", coarse_eps=None, refine=1):
     if coarse_eps is None:
-        # the cut must sit above the relative accuracy of A_hat: FP64 entries for fp64,
-        # FP32-accurate environments otherwise
-        coarse_eps = 1e-10 if prec in ("fp64", "f64emu") else 1e-5
+        # A_hat and S_hat are FP64-class in every precision but plain FP32
+        coarse_eps = 1e-5 if prec == "fp32" else 1e-10
     return dict(partition=cfg["partition"], D_max=cfg["D"], svd_tol=1e-6, eig_tol=1e-6,
                 coarse_eps=coarse_eps, max_krylov=40, max_restarts=50, prec=prec,
-                solver=solver)
+                solver=solver, refine=refine)
 
 
 def read_peaks():
@@ -329,7 +330,7 @@ def main():
     mpo = a2.MPO(ctx, mpo_cores)
     if args.no_fold:
         mpo.set_fold(False)
-    kw = sweep_kwargs(cfg, args.prec, args.solver, args.coarse_eps)
+    kw = sweep_kwargs(cfg, args.prec, args.solver, args.coarse_eps, 0 if args.no_refine else 1)
     kw["sequential"] = args.sequential or args.groups == "sequential"
     P = cfg["P"]
     if args.one_site:   # the one-site case of Alg. 2: P groups of the L cores

@@ -47,19 +47,23 @@ typedef enum {
 typedef enum {
   A2_FP64 = 0, /* every contraction in FP64 */
   A2_BF16 = 1, /* Lanczos on tcgen05 tensor cores with BF16 operands to a residual of
-                  3e-3, then continued with the A2_F32EMU products to eig_tol;
-                  environments and coarse matrices in FP32, vectors / SVD /
-                  coarse eigensolve in FP64 */
+                  3e-3, then continued with the A2_F32EMU products to eig_tol, then (with
+                  refine_f64) the FP64 refinement of the Ritz pair; environments FP64,
+                  computed to FP64-class accuracy on the tensor cores as in A2_F64EMU;
+                  coarse matrices, vectors, SVD and coarse eigensolve in FP64 */
   A2_TF32 = 2, /* reserved */
   A2_FP32 = 3, /* every contraction in FP32 (SIMT), vectors / SVD / coarse in FP64 */
   A2_F32EMU = 4, /* H_eff on tcgen05 with FP32-accurate products: operands split into
-                   three BF16 slices, six slice pairs accumulated in FP32 */
+                   three BF16 slices, six slice pairs accumulated in FP32; environments,
+                   refinement and coarse problem as in A2_BF16 */
   A2_F64EMU = 5  /* H_eff to FP64-class accuracy (~2^-48) on tcgen05 (Ozaki scheme): FP64
                    operands split row-wise into eight 7-bit BF16 slices, the 36 slice
                    pairs of level <= 9 accumulated exactly in FP32 per level and K chunk,
                    the partial tiles summed by error-free two-sums into FP32 pairs; the
-                   sparse MPO stages in double-float (FP32 pairs); environments, vectors,
-                   SVD and coarse problem in FP64 */
+                   sparse MPO stages in double-float (FP32 pairs); environments FP64,
+                   their updates emulated the same way (two Ozaki GEMMs and a double-float
+                   sparse stage) above a small size, plain FP64 below; vectors, SVD and
+                   coarse problem in FP64 */
 } a2_precision;
 
 typedef struct a2_ctx a2_ctx;
@@ -147,7 +151,16 @@ typedef struct {
   int max_krylov;              /* Krylov basis size before a restart (<= 64) */
   int max_restarts;            /* restart cycles per local solve */
   a2_precision prec;
-  int refine_f64;              /* reserved (refinement is part of A2_BF16) */
+  int refine_f64;              /* A2_BF16 / A2_F32EMU, two-site local problems: 1 = FP64
+                                  refinement of every local Ritz pair after the tensor-core
+                                  phases (the spec precision split): Lanczos continued
+                                  from the Ritz vector on the FP64-class (A2_F64EMU)
+                                  operator, whose first application gives the FP64 Rayleigh
+                                  quotient and residual, until that residual meets eig_tol;
+                                  the reported local energies are then FP64 Rayleigh
+                                  quotients.  0 = none.  Ignored by the other precisions,
+                                  the one-site case and Extension One's further
+                                  eigenvectors. */
   int solver;                  /* local eigensolver: 0 = restarted Lanczos (as in the
                                   paper's experiments), 1 = Davidson with the diagonal
                                   preconditioner (same stopping rule, fewer matvecs) */
@@ -209,6 +222,8 @@ typedef struct {
                                   coarse step and the compression use it) and counted here.
                                   A Lanczos breakdown (invariant Krylov space: the Ritz
                                   pair is exact) counts as converged. */
+  long long matvecs_f64;       /* of `matvecs`: the FP64-class (Ozaki-emulated) H_eff
+                                  applications, e.g. those of the refine_f64 step */
 } a2_sweep_report;
 
 /* One global iteration of two-site A2DMRG (Alg. 2, with P groups of adjoining

@@ -46,7 +46,8 @@ class SweepReport(ctypes.Structure):
                 ("krylov_iters", ctypes.POINTER(ctypes.c_int)),
                 ("max_discarded_weight", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("alg_flops", ctypes.c_double), ("matvecs", ctypes.c_longlong),
-                ("coarse_dim", ctypes.c_int), ("unconverged", ctypes.c_int)]
+                ("coarse_dim", ctypes.c_int), ("unconverged", ctypes.c_int),
+                ("matvecs_f64", ctypes.c_longlong)]
 
 
 _lib = None
@@ -311,7 +312,7 @@ def _opts(L, P, partition, D_max, svd_tol, eig_tol, coarse_eps, max_krylov, max_
 
 
 def _sweep(fn, ctx, tt, mpo, P, partition=None, D_max=64, svd_tol=1e-10, eig_tol=1e-10,
-           coarse_eps=1e-10, max_krylov=40, max_restarts=200, prec="fp64", refine=2,
+           coarse_eps=1e-10, max_krylov=40, max_restarts=200, prec="fp64", refine=1,
            solver="lanczos", sequential=False, one_site=False, n_eig=1, low_memory=False,
            graphs=False):
     """one_site=True: the one-site case of Alg. 2 (partition over the L cores);
@@ -337,6 +338,7 @@ def _sweep(fn, ctx, tt, mpo, P, partition=None, D_max=64, svd_tol=1e-10, eig_tol
     m = r.coarse_dim
     out["coarse_dim"] = m
     out["unconverged"] = r.unconverged
+    out["matvecs_f64"] = r.matvecs_f64
     out["energy_local"] = bufs["energy_local"][:m - 1]
     out["coeffs"] = bufs["coeffs"][:m]
     out["S_hat"] = bufs["S_hat"][:m * m].reshape(m, m)

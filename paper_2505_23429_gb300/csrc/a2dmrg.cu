@@ -505,6 +505,104 @@ void env_right_emu(a2_ctx* c, const SiteOps& so, const float* Hin, const double*
   }
 }
 
+// ---- environment updates to FP64-class accuracy on tcgen05 (FP64 envs): the two GEMMs
+// emulated by the Ozaki scheme (tc_gemm_f64emu), the sparse MPO stage in double-float
+// arithmetic.  Same contraction and intermediate layouts as env_left / env_right.
+void env_left_f64e(a2_ctx* c, const SiteOps& so, const double* Hin, const double* bra, int Dlb,
+                   int Drb, const double* ket, int Dlk, int Drk, double* Hout) {
+  const int n = so.n, Rl = so.Rl, Rr = so.Rr;
+  cudaStream_t s = c->stream;
+  ProfScope ps(PK_ENV, s, env_flops(so, std::max(Dlb, Dlk), std::max(Drb, Drk)),
+               8.0 * ((double)Dlb * Rl * Dlk + (double)Drb * Rr * Drk +
+                      2.0 * Dlb * Rl * n * Drk + 2.0 * Dlb * n * Rr * Drk));
+  const long long M1 = (long long)Dlb * Rl, N1 = (long long)n * Drk;
+  const long long N3 = (long long)Rr * Drk, K3 = (long long)Dlb * n;
+  const long long ldH = pad8(Dlk), pH = round64(M1 * ldH);
+  const long long ldK = pad8(Dlk), pK = round64(N1 * ldK);
+  const long long ldB = pad8(K3), pB = round64((long long)Drb * ldB);
+  const long long pT = round64(N3 * ldB);
+  const long long s1 = M1 * N1, p1 = (s1 + 3) / 4 * 4, s2 = K3 * N3;
+  c->cb.ensure(sizeof(__nv_bfloat16) * (size_t)(kOzSlices * (pH + pK + pB)), s);
+  __nv_bfloat16* Hp = c->cb.as<__nv_bfloat16>();
+  __nv_bfloat16* Kp = Hp + kOzSlices * pH;
+  __nv_bfloat16* Bp = Kp + kOzSlices * pK;
+  c->tmp1.ensure(std::max(sizeof(float) * 2 * (size_t)p1, sizeof(double) * (size_t)s2), s);
+  c->tmp2.ensure(sizeof(double) * (size_t)s2, s);
+  c->t3.ensure(sizeof(__nv_bfloat16) * (size_t)(kOzSlices * pT), s);
+  float* T1 = c->tmp1.as<float>();
+  double* T2 = c->tmp2.as<double>();
+  double* T2t = c->tmp1.as<double>();   // after E2 has consumed T1
+  __nv_bfloat16* T2p = c->t3.as<__nv_bfloat16>();
+  ozaki_split(Hin, Dlk, 1, (int)M1, Dlk, Hp, ldH, pH, s);            // rows (a w), K = a'
+  ozaki_split(ket, 1, N1, (int)N1, Dlk, Kp, ldK, pK, s);             // rows (t b'), K = a'
+  // E1: T1[(a w)][(t b')] = sum_a' Hin[(a w)][a'] ket[a'][(t b')]   (FP32 pair out)
+  tc_gemm_f64emu(Hp, ldH, pH, Kp, ldK, pK, (int)M1, (int)N1, Dlk, nullptr, N1, c->tf, s, T1, p1);
+  {  // E2: T2[(a s)][(w' b')] = sum_{w,t} A[w,s,t,w'] T1[(a w)][(t b')]   (FP64 out)
+    SparseGeom gm;
+    gm.veclen = Drk;
+    gm.in_sw = N1; gm.in_st = Drk;
+    gm.out_sw = Drk; gm.out_ss = N3;
+    gm.B1 = Dlb; gm.in_b1 = (long long)Rl * N1; gm.out_b1 = (long long)n * N3;
+    sparse_rows_apply_df(so.lr.rows<float>(), gm, T1, p1, nullptr, 0, T2, s);
+  }
+  // E3: Hout[b][(w' b')] = sum_{(a s)} bra[(a s)][b] T2[(a s)][(w' b')]
+  ozaki_split(bra, 1, Drb, Drb, (int)K3, Bp, ldB, pB, s);            // rows b, K = (a s)
+  transpose2d<double, double>(T2, T2t, (int)K3, (int)N3, s);         // [(w' b')][(a s)]
+  ozaki_split(T2t, K3, 1, (int)N3, (int)K3, T2p, ldB, pT, s);
+  tc_gemm_f64emu(Bp, ldB, pB, T2p, ldB, pT, Drb, (int)N3, (int)K3, Hout, N3, c->tf, s);
+}
+
+void env_right_f64e(a2_ctx* c, const SiteOps& so, const double* Hin, const double* bra, int Dlb,
+                    int Drb, const double* ket, int Dlk, int Drk, double* Hout) {
+  const int n = so.n, Rl = so.Rl, Rr = so.Rr;
+  cudaStream_t s = c->stream;
+  ProfScope ps(PK_ENV, s, env_flops(so, std::max(Dlb, Dlk), std::max(Drb, Drk)),
+               8.0 * ((double)Dlb * Rl * Dlk + (double)Drb * Rr * Drk +
+                      2.0 * Drb * Rr * n * Dlk + 2.0 * n * Drb * Rl * Dlk));
+  const long long M1 = (long long)Drb * Rr, N1 = (long long)n * Dlk;
+  const long long N3 = (long long)Rl * Dlk, K3 = (long long)n * Drb;
+  const long long ldH = pad8(Drk), pH = round64(M1 * ldH);
+  const long long ldV = pad8(Drk), pV = round64(N1 * ldV);
+  const long long ldB = pad8(K3), pB = round64((long long)Dlb * ldB);
+  const long long pT = round64(N3 * ldB);
+  const long long s1 = M1 * N1, p1 = (s1 + 3) / 4 * 4, s2 = K3 * N3;
+  c->cb.ensure(sizeof(__nv_bfloat16) * (size_t)(kOzSlices * (pH + pV + pB)) +
+                   sizeof(double) * (size_t)n * Dlk * Drk, s);
+  __nv_bfloat16* Hp = c->cb.as<__nv_bfloat16>();
+  __nv_bfloat16* Vp = Hp + kOzSlices * pH;
+  __nv_bfloat16* Bp = Vp + kOzSlices * pV;
+  double* Vt = reinterpret_cast<double*>(Bp + kOzSlices * pB);
+  c->tmp1.ensure(std::max(sizeof(float) * 2 * (size_t)p1, sizeof(double) * (size_t)s2), s);
+  c->tmp2.ensure(sizeof(double) * (size_t)s2, s);
+  c->t3.ensure(sizeof(__nv_bfloat16) * (size_t)(kOzSlices * pT), s);
+  float* T1 = c->tmp1.as<float>();
+  double* T2 = c->tmp2.as<double>();
+  double* T2t = c->tmp1.as<double>();
+  __nv_bfloat16* T2p = c->t3.as<__nv_bfloat16>();
+  permute_swap01<double, double>(ket, Vt, n, Dlk, Drk, s);            // Vt[t][a'][b']
+  ozaki_split(Hin, Drk, 1, (int)M1, Drk, Hp, ldH, pH, s);             // rows (b w'), K = b'
+  ozaki_split(Vt, Drk, 1, (int)N1, Drk, Vp, ldV, pV, s);              // rows (t a'), K = b'
+  // F1: T1[(b w')][(t a')] = sum_b' Hin[(b w')][b'] Vt[(t a')][b']   (FP32 pair out)
+  tc_gemm_f64emu(Hp, ldH, pH, Vp, ldV, pV, (int)M1, (int)N1, Drk, nullptr, N1, c->tf, s, T1, p1);
+  {  // F2: T2[(s b)][(w a')] = sum_{w',t} A[w,s,t,w'] T1[(b w')][(t a')]   (FP64 out)
+    SparseGeom gm;
+    gm.veclen = Dlk;
+    gm.in_sw = N1; gm.in_st = Dlk;
+    gm.out_sw = Dlk; gm.out_ss = (long long)Drb * N3;
+    gm.B1 = Drb; gm.in_b1 = (long long)Rr * N1; gm.out_b1 = N3;
+    sparse_rows_apply_df(so.rl.rows<float>(), gm, T1, p1, nullptr, 0, T2, s);
+  }
+  // F3: Hout[a][(w a')] = sum_{(s b)} bra[a][(s b)] T2[(s b)][(w a')]
+  ozaki_split(bra, K3, 1, Dlb, (int)K3, Bp, ldB, pB, s);             // rows a, K = (s b)
+  transpose2d<double, double>(T2, T2t, (int)K3, (int)N3, s);         // [(w a')][(s b)]
+  ozaki_split(T2t, K3, 1, (int)N3, (int)K3, T2p, ldB, pT, s);
+  tc_gemm_f64emu(Bp, ldB, pB, T2p, ldB, pT, Dlb, (int)N3, (int)K3, Hout, N3, c->tf, s);
+}
+
+// Environment updates this small stay on the FP64 SIMT kernels (the Ozaki path costs a
+// dozen launches and 36 tensor-core products per FP64 product).
+constexpr double kF64eEnvMinFlops = 2e8;
+
 // Split-K factor so that the skinny S4 GEMM fills the GPU.
 int pick_splitk(int M, int N, int K, int tile) {
   const long long tiles = (long long)cdiv(M, tile) * cdiv(N, tile);
@@ -848,7 +946,7 @@ struct Engine {
   std::vector<DevBuf> HL, HR;            // envs in T
   std::vector<int> HLd, HRd;             // bond dims of the stored envs
   double flops = 0.0;
-  long long matvecs = 0, matvecs_bf16 = 0;
+  long long matvecs = 0, matvecs_bf16 = 0, matvecs_f64 = 0;
   DevBuf cvt_bra, cvt_ket;
   Bf16Envs bfe;
   OzEnvs oze;   // FP64-emulation slices of the current local problem's environments
@@ -867,10 +965,24 @@ struct Engine {
     A2_CUDA(cudaStreamSynchronize(c->stream));   // `one` lives on the host stack
   }
 
+  // FP64-class environments on the tensor cores (Ozaki scheme) for the FP64-emulated and
+  // the mixed modes, once an update is large enough to pay for the slicing
+  bool f64e_env(int j, int Dl, int Dr) const {
+    return (prec == A2_F64EMU || prec == A2_BF16 || prec == A2_F32EMU) &&
+           env_flops(mpo->site[j], Dl, Dr) >= kF64eEnvMinFlops;
+  }
+
   // env update with FP64 cores converted to T
   void left_update(const T* Hin, int j, const double* bra, int Dlb, int Drb, const double* ket,
                    int Dlk, int Drk, T* Hout) {
     const int n = mpo->phys[j];
+    if constexpr (sizeof(T) == 8) {
+      if (f64e_env(j, std::max(Dlb, Dlk), std::max(Drb, Drk))) {
+        env_left_f64e(c, mpo->site[j], Hin, bra, Dlb, Drb, ket, Dlk, Drk, Hout);
+        flops += env_flops(mpo->site[j], std::max(Dlb, Dlk), std::max(Drb, Drk));
+        return;
+      }
+    }
     if constexpr (sizeof(T) == 4) {
       if (prec == A2_BF16 || prec == A2_F32EMU) {
         env_left_emu(c, mpo->site[j], Hin, bra, Dlb, Drb, ket, Dlk, Drk, Hout);
@@ -886,6 +998,13 @@ struct Engine {
   void right_update(const T* Hin, int j, const double* bra, int Dlb, int Drb,
                     const double* ket, int Dlk, int Drk, T* Hout) {
     const int n = mpo->phys[j];
+    if constexpr (sizeof(T) == 8) {
+      if (f64e_env(j, std::max(Dlb, Dlk), std::max(Drb, Drk))) {
+        env_right_f64e(c, mpo->site[j], Hin, bra, Dlb, Drb, ket, Dlk, Drk, Hout);
+        flops += env_flops(mpo->site[j], std::max(Dlb, Dlk), std::max(Drb, Drk));
+        return;
+      }
+    }
     if constexpr (sizeof(T) == 4) {
       if (prec == A2_BF16 || prec == A2_F32EMU) {
         env_right_emu(c, mpo->site[j], Hin, bra, Dlb, Drb, ket, Dlk, Drk, Hout);
@@ -932,6 +1051,7 @@ struct Engine {
     heff_f64emu(c, mpo->site[k], mpo->site[k + 1], oze, Dl, Dr, x, y);
     flops += heff_flops(mpo->site[k], mpo->site[k + 1], Dl, Dr);
     ++matvecs;
+    ++matvecs_f64;
   }
   // one-site H_eff on the tensor cores with FP32-accurate products (environments in bfe)
   void matvec1_emu(int j, int Dl, int Dr, const double* x, double* y) {
@@ -966,6 +1086,10 @@ struct Engine {
 // ============================================================================= Lanczos
 // residual tolerance of the BF16 tensor-core Lanczos phase (BF16 operator accuracy)
 constexpr double kBf16Tol = 3e-3;
+// tightest residual asked of the FP32-accurate split-product phase when the FP64
+// refinement follows (its products carry ~1e-6 relative error, and the rounding order of
+// its split-K sums varies from run to run, so tighter targets would stall)
+constexpr double kSplitTol = 1e-6;
 
 struct LanczosResult {
   double theta = 0.0;
@@ -1661,31 +1785,30 @@ struct Sweeper {
       int nmv = 0;
       LanczosResult lr;
       bool done = false;
+      const bool mixed = o.prec == A2_BF16 || o.prec == A2_F32EMU;
       if (o.solver == 1) {
         // Davidson with the diagonal preconditioner on the accurate operator
         DevBuf dg;
         dg.ensure(sizeof(double) * (size_t)N, c->stream);
         heff_diag<T>(c, mpo->site[k], mpo->site[k + 1], HLcur, HRk, Dl, Dr, dg.as<double>());
-        if constexpr (sizeof(T) == 4) {
-          if (o.prec == A2_BF16 || o.prec == A2_F32EMU) {
-            eng.bfe.set(c, HLcur, Dl, mpo->R[k], HRk, Dr, mpo->R[k + 2], 3, &mpo->site[k],
-                         &mpo->site[k + 1]);
-            auto mve_raw = [&](const double* in, double* out) {
-              eng.matvec_emu(k, Dl, Dr, in, out);
-            };
-            auto mve = graphed(g_e, mve_raw);
-            lr = davidson(c, mve, dg.as<double>(), x.as<double>(), N, o.eig_tol, o.max_krylov,
-                          o.max_krylov * o.max_restarts);
-            done = true;
-          }
+        if (mixed) {
+          eng.bfe.set(c, HLcur, Dl, mpo->R[k], HRk, Dr, mpo->R[k + 2], 3, &mpo->site[k],
+                       &mpo->site[k + 1]);
+          auto mve_raw = [&](const double* in, double* out) {
+            eng.matvec_emu(k, Dl, Dr, in, out);
+          };
+          auto mve = graphed(g_e, mve_raw);
+          lr = davidson(c, mve, dg.as<double>(), x.as<double>(), N, o.eig_tol, o.max_krylov,
+                        o.max_krylov * o.max_restarts);
+          done = true;
         }
         if (!done)
           lr = davidson(c, mv, dg.as<double>(), x.as<double>(), N, o.eig_tol, o.max_krylov,
                         o.max_krylov * o.max_restarts);
         done = true;
       }
-      if constexpr (sizeof(T) == 4) {
-        if (!done && (o.prec == A2_BF16 || o.prec == A2_F32EMU)) {
+      {
+        if (!done && mixed) {
           eng.bfe.set(c, HLcur, Dl, mpo->R[k], HRk, Dr, mpo->R[k + 2], 3, &mpo->site[k],
                          &mpo->site[k + 1]);
           if (o.prec == A2_BF16) {
@@ -1698,17 +1821,33 @@ struct Sweeper {
                                        o.max_krylov, o.max_restarts);
             nmv += lb.matvecs;
           }
-          // ... then FP32-accurate tensor-core products from that vector to eig_tol
+          // ... then FP32-accurate tensor-core products from that vector to eig_tol (or
+          // to kSplitTol when the FP64 refinement takes it further)
           auto mve_raw = [&](const double* in, double* out) {
             eng.matvec_emu(k, Dl, Dr, in, out);
           };
           auto mve = graphed(g_e, mve_raw);
-          lr = lanczos(c, mve, x.as<double>(), N, o.eig_tol, o.max_krylov, o.max_restarts);
+          const double tol_split =
+              (sizeof(T) == 8 && o.refine_f64) ? std::max(o.eig_tol, kSplitTol) : o.eig_tol;
+          lr = lanczos(c, mve, x.as<double>(), N, tol_split, o.max_krylov, o.max_restarts);
           done = true;
         }
       }
       if (!done)
         lr = lanczos(c, mv, x.as<double>(), N, o.eig_tol, o.max_krylov, o.max_restarts);
+      if constexpr (sizeof(T) == 8) {
+        if (mixed && o.refine_f64) {
+          // FP64 refinement of the Ritz pair: Lanczos continued from x on the FP64-class
+          // (Ozaki-emulated) operator.  Its first application gives the FP64 Rayleigh
+          // quotient and the FP64 residual; it stops as soon as that residual meets
+          // eig_tol, so an x the tensor-core phases left accurate enough costs one
+          // application.
+          nmv += lr.matvecs;
+          eng.oze.set(c, HLcur, Dl, mpo->R[k], HRk, Dr, mpo->R[k + 2]);
+          auto mvf = [&](const double* in, double* out) { eng.matvec_f64e(k, Dl, Dr, in, out); };
+          lr = lanczos(c, mvf, x.as<double>(), N, o.eig_tol, o.max_krylov, o.max_restarts);
+        }
+      }
       check_finite(lr.theta, "local eigenvalue");
       kry[k] = nmv + lr.matvecs;
       if (!lr.converged) unconv.fetch_add(1);
@@ -1718,11 +1857,9 @@ struct Sweeper {
         // the further eigenvectors on the accurate operator (FP32-accurate tensor-core
         // products in the mixed modes), each truncated by its own SVD
         auto mvx = [&](const double* in, double* out) {
-          if constexpr (sizeof(T) == 4) {
-            if (o.prec == A2_BF16 || o.prec == A2_F32EMU) {
-              eng.matvec_emu(k, Dl, Dr, in, out);
-              return;
-            }
+          if (mixed) {
+            eng.matvec_emu(k, Dl, Dr, in, out);
+            return;
           }
           mv(in, out);
         };
@@ -1825,11 +1962,9 @@ struct Sweeper {
       const T* HRj = hr_at(j + 1, eng, HRbuf);
       // mixed modes: FP32-accurate tensor-core products (environments split once)
       bool tc1 = false;
-      if constexpr (sizeof(T) == 4) {
-        if (o.prec == A2_BF16 || o.prec == A2_F32EMU) {
-          eng.bfe.set(c, HLcur, Dl, mpo->R[j], HRj, Dr, mpo->R[j + 1], 3);
-          tc1 = true;
-        }
+      if (o.prec == A2_BF16 || o.prec == A2_F32EMU) {
+        eng.bfe.set(c, HLcur, Dl, mpo->R[j], HRj, Dr, mpo->R[j + 1], 3);
+        tc1 = true;
       }
       auto mv_raw = [&](const double* in, double* out) {
         if (tc1) eng.matvec1_emu(j, Dl, Dr, in, out);
@@ -2010,7 +2145,7 @@ struct Sweeper {
       const double Rl = mpo->R[k], R1 = mpo->R[k + 1], Rr = mpo->R[k + 2];
       const double N = Dl * n1 * n2 * Dr;
       double heff;
-      if (sizeof(T) == 4 && o.prec != A2_FP32)      // tensor-core chains (split planes)
+      if (o.prec == A2_BF16 || o.prec == A2_F32EMU)  // tensor-core chains (split planes)
         heff = std::max(4.0 * Dl * Rl, 6.0 * Dl * Rr) * n1 * n2 * Dr + 6.0 * Dl * R1 * n1 * n2 * Dr +
                12.0 * (Dl * Rl * Dl + Dr * Rr * Dr + 2.0 * Dl * R1 * Dl);
       else                                           // SIMT chain: t1 = max(T1, T3), t2 = T2
@@ -2107,6 +2242,7 @@ struct Sweeper {
         eng.flops += e->flops;
         eng.matvecs += e->matvecs;
         eng.matvecs_bf16 += e->matvecs_bf16;
+        eng.matvecs_f64 += e->matvecs_f64;
       }
     } else {
       for (int g = 0; g < P; ++g) solve(groups[g], c, eng);
@@ -2204,6 +2340,7 @@ struct Sweeper {
       rep->max_discarded_weight = max_disc;
       rep->alg_flops = eng.flops;
       rep->matvecs = eng.matvecs;
+      rep->matvecs_f64 = eng.matvecs_f64;
       rep->unconverged = unconv.load();
       A2_CUDA(cudaStreamSynchronize(s));
       rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -2357,8 +2494,9 @@ struct Sweeper {
 };
 
 template <typename T>
-double energy_T(a2_ctx* c, const a2_tt* tt, const a2_mpo* mpo, double* norm_out) {
-  Engine<T> eng(c, mpo, A2_FP64);
+double energy_T(a2_ctx* c, const a2_tt* tt, const a2_mpo* mpo, double* norm_out,
+                a2_precision prec = A2_FP64) {
+  Engine<T> eng(c, mpo, prec);
   cudaStream_t s = c->stream;
   const int L = tt->L;
   DevBuf E, En;
@@ -2810,14 +2948,14 @@ static a2_status run_sweep(a2_ctx* c, a2_tt* t, const a2_mpo* m, const a2_sweep_
       A2_CUDA(cudaMemcpyAsync(saved[j].p, t->cores[j].p, t->cores[j].bytes,
                               cudaMemcpyDeviceToDevice, c->stream));
     }
-    if (o->prec == A2_FP64 || o->prec == A2_F64EMU) {
-      if (o->prec == A2_F64EMU && !tc_available())
-        throw ArgError("A2_F64EMU needs the tcgen05 path, which this build lacks");
+    if (o->prec == A2_FP64 || o->prec == A2_F64EMU || o->prec == A2_BF16 ||
+        o->prec == A2_F32EMU) {
+      // FP64 environments; the tensor-core modes keep them to FP64-class accuracy
+      if (o->prec != A2_FP64 && !tc_available())
+        throw ArgError("this precision needs the tcgen05 path, which this build lacks");
       Sweeper<double> sw(c, t, m, *o);
       sw.run(rep, classical);
-    } else if (o->prec == A2_FP32 || o->prec == A2_BF16 || o->prec == A2_F32EMU) {
-      if (o->prec != A2_FP32 && !tc_available())
-        throw ArgError("A2_BF16 needs the tcgen05 path, which this build lacks");
+    } else if (o->prec == A2_FP32) {
       Sweeper<float> sw(c, t, m, *o);
       sw.run(rep, classical);
     } else {
@@ -2873,7 +3011,8 @@ a2_status a2_energy(a2_ctx* c, const a2_tt* t, const a2_mpo* m, a2_precision pre
   return guarded(c, [&] {
     tt_check(t);
     A2_REQUIRE(t->phys == m->phys, "TT and MPO physical dims differ");
-    if (prec == A2_FP64 || prec == A2_F64EMU) *E = energy_T<double>(c, t, m, norm_out);
+    if (prec == A2_FP64) *E = energy_T<double>(c, t, m, norm_out);
+    else if (prec == A2_F64EMU) *E = energy_T<double>(c, t, m, norm_out, A2_F64EMU);
     else *E = energy_T<float>(c, t, m, norm_out);
   });
 }
@@ -3095,9 +3234,13 @@ a2_status a2_env_update(a2_ctx* c, const a2_mpo* m, int j, int side, a2_precisio
     const SiteOps& so = m->site[j];
     cudaStream_t s = c->stream;
     const int n = so.n;
-    if (prec == A2_FP64 || prec == A2_F64EMU) {   // environment updates stay on FP64 SIMT
+    if (prec == A2_FP64) {
       if (side == 0) env_left<double>(c, so, in, bra, Dlb, Drb, ket, Dlk, Drk, out);
       else env_right<double>(c, so, in, bra, Dlb, Drb, ket, Dlk, Drk, out);
+    } else if (prec == A2_F64EMU) {   // Ozaki-emulated GEMMs, double-float sparse stage
+      A2_REQUIRE(tc_available(), "this precision needs the tcgen05 path");
+      if (side == 0) env_left_f64e(c, so, in, bra, Dlb, Drb, ket, Dlk, Drk, out);
+      else env_right_f64e(c, so, in, bra, Dlb, Drb, ket, Dlk, Drk, out);
     } else {
       const long long nin = side == 0 ? (long long)Dlb * so.Rl * Dlk : (long long)Drb * so.Rr * Drk;
       const long long nout = side == 0 ? (long long)Drb * so.Rr * Drk : (long long)Dlb * so.Rl * Dlk;

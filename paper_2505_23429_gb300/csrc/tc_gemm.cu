@@ -148,6 +148,32 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 enum OutKind { OUT_BF16 = 0, OUT_F32 = 1, OUT_F32_ATOMIC = 2 };
 
 constexpr int kMaxPlanes = 8;      // BF16 planes per operand (8: the FP64 level products)
@@ -741,6 +767,342 @@ int launch(const __nv_bfloat16* const* A, long long lda, const __nv_bfloat16* co
   return splitk;
 }
 
+// ------------------------------------------------------------------ Ozaki GEMM, register sums
+// FP64-class product of two operands given as kOzSlices BF16 slice planes each (the
+// slicing of the FP64 emulation below).  Work unit = (128 x 128 output tile, K split).
+// For every level l = 2 .. kOzSlices + 1 the l - 1 slice pairs of that level are
+// accumulated over chunks of at most 16 / (l - 1) K blocks into a fresh TMEM buffer: a
+// chunk holds at most 1024 products per output element, each an integer multiple of the
+// level's unit below 2^14 units, so its FP32 sum is exact.  The epilogue adds every chunk
+// into a double-float register accumulator (hi + lo, Knuth's error-free two-sum), so no
+// per-level tile reaches memory.  Warp 0 lane 0: TMA producer; warp 1 lane 0: MMA issuer;
+// warps 2..9: epilogue (two per TMEM lane quarter, 64 columns each).  Every wait is
+// bounded as in tc_gemm_kernel.
+constexpr int kOzBN = 128;
+constexpr int kOzStages = 5;
+constexpr int kOzEpi = 8;
+constexpr int kOzThreads = 64 + 32 * kOzEpi;
+constexpr int kOzMaxLevel = 9;                  // slice pairs (i, j) with i + j <= 9
+
+struct OzSmem {
+  alignas(1024) __nv_bfloat16 a[kOzStages][BM * BK];
+  alignas(1024) __nv_bfloat16 b[kOzStages][kOzBN * BK];
+  alignas(1024) float stage[kOzEpi][2][32 * 32];   // epilogue transpose buffers (hi, lo)
+  alignas(8) uint64_t full[kOzStages];
+  alignas(8) uint64_t empty[kOzStages];
+  alignas(8) uint64_t acc_full[2];
+  alignas(8) uint64_t acc_empty[2];
+  alignas(8) uint64_t drain;
+  uint32_t tmem_base;
+  int abort_flag;
+};
+static_assert(sizeof(OzSmem) + 1024 <= 227 * 1024, "Ozaki ring exceeds shared memory");
+
+enum OzOut { OZ_F64 = 0, OZ_PAIR = 1, OZ_SPLIT = 2 };
+
+struct OzArgs {
+  int M, N, nk;              // rows, columns, K blocks of BK
+  int kblocks_per_split, splits;
+  int n_fast;                // 1: consecutive units walk the N tiles of one row of tiles
+  int out_mode;              // OZ_F64: C[m*ldc + n] = hi + lo (FP64)
+                             // OZ_PAIR: FP32 hi at C[m*ldc + n], lo at + df_plane
+                             // OZ_SPLIT: FP32 tiles of split sp, hi at C + 2sp*MN and lo at
+                             //           C + (2sp+1)*MN, row stride N
+  void* C;
+  long long ldc, df_plane, MN;
+};
+
+__device__ __forceinline__ int oz_chunk_blocks(int np) { return max(1, 16 / np); }
+
+// 10 warps: three of them share one SM sub-partition's 16K registers, hence at most 168
+// registers per thread.
+__global__ void __launch_bounds__(kOzThreads, 1)
+tc_oz_kernel(const __grid_constant__ TcMaps maps, OzArgs args) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uint32_t base = smem_u32(smem_raw);
+  const uint32_t pad = (1024u - (base & 1023u)) & 1023u;
+  auto& S = *reinterpret_cast<OzSmem*>(smem_raw + pad);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_m = (args.M + BM - 1) / BM;
+  const int tiles_n = (args.N + kOzBN - 1) / kOzBN;
+  const int nunits = tiles_m * tiles_n * args.splits;
+  constexpr uint32_t kStageBytes = (BM + kOzBN) * BK * 2;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kOzStages; ++s) {
+      mbar_init(&S.full[s], 1);
+      mbar_init(&S.empty[s], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&S.acc_full[i], 1);
+      mbar_init(&S.acc_empty[i], kOzEpi);
+    }
+    mbar_init(&S.drain, 1);
+    S.abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {   // two accumulators of 128 fp32 columns x 128 lanes
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&S.tmem_base)),
+                 "r"((uint32_t)(2 * kOzBN)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = S.tmem_base;
+
+  auto unit = [&](int u, int& m0, int& n0, int& kb0, int& nkb) {
+    const int t = u % (tiles_m * tiles_n), sp = u / (tiles_m * tiles_n);
+    if (args.n_fast) {
+      n0 = (t % tiles_n) * kOzBN;
+      m0 = (t / tiles_n) * BM;
+    } else {
+      m0 = (t % tiles_m) * BM;
+      n0 = (t / tiles_m) * kOzBN;
+    }
+    kb0 = sp * args.kblocks_per_split;
+    nkb = max(0, min(args.nk - kb0, args.kblocks_per_split));
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- producer: level, chunk, K block, slice pair
+      uint32_t g = 0, issued = 0;
+      bool stop = false;
+      for (int u = blockIdx.x; !stop && u < nunits && !*(volatile int*)&S.abort_flag;
+           u += gridDim.x) {
+        int m0, n0, kb0, nkb;
+        unit(u, m0, n0, kb0, nkb);
+        for (int l = 2; !stop && l <= kOzMaxLevel; ++l) {
+          const int np = l - 1, kbl = oz_chunk_blocks(np);
+          for (int c0 = 0; !stop && c0 < nkb; c0 += kbl) {
+            const int c1 = min(nkb, c0 + kbl);
+            for (int kb = c0; !stop && kb < c1; ++kb) {
+              for (int p = 0; p < np; ++p, ++g) {
+                const int s = g % kOzStages;
+                const uint32_t round = g / kOzStages;
+                if ((round > 0 &&
+                     !mbar_wait_or_abort(&S.empty[s], (round - 1) & 1, 11, &S.abort_flag)) ||
+                    *(volatile int*)&S.abort_flag) {
+                  S.abort_flag = 1;
+                  stop = true;
+                  break;
+                }
+                mbar_expect_tx(&S.full[s], kStageBytes);
+                const int kx = (kb0 + kb) * BK;
+                tma_load_2d(&maps.a[p], &S.full[s], S.a[s], kx, m0);
+                tma_load_2d(&maps.b[np - 1 - p], &S.full[s], S.b[s], kx, n0);
+                issued = g + 1;
+              }
+            }
+          }
+        }
+      }
+      if (*(volatile int*)&S.abort_flag) {   // wait (bounded) for the copies in flight
+        for (uint32_t j = issued > (uint32_t)kOzStages ? issued - kOzStages : 0; j < issued; ++j)
+          mbar_wait(&S.full[j % kOzStages], (j / kOzStages) & 1, 12);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer: one TMEM buffer per (level, chunk)
+      constexpr uint32_t idesc = idesc_bf16(BM, kOzBN);
+      uint32_t g = 0, ch = 0;
+      bool issued_any = false, ok = true;
+      for (int u = blockIdx.x; ok && u < nunits && !*(volatile int*)&S.abort_flag;
+           u += gridDim.x) {
+        int m0, n0, kb0, nkb;
+        unit(u, m0, n0, kb0, nkb);
+        for (int l = 2; ok && l <= kOzMaxLevel; ++l) {
+          const int np = l - 1, kbl = oz_chunk_blocks(np);
+          for (int c0 = 0; ok && c0 < nkb; c0 += kbl, ++ch) {
+            const int c1 = min(nkb, c0 + kbl);
+            const uint32_t buf = ch & 1, use = ch >> 1;
+            if (use > 0 &&
+                !mbar_wait_or_abort(&S.acc_empty[buf], (use - 1) & 1, 13, &S.abort_flag)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t d = tmem + buf * kOzBN;
+            bool first = true;
+            for (int kb = c0; ok && kb < c1; ++kb) {
+              for (int p = 0; p < np; ++p, ++g) {
+                const int s = g % kOzStages;
+                if (!mbar_wait_or_abort(&S.full[s], (g / kOzStages) & 1, 14, &S.abort_flag)) {
+                  ok = false;
+                  break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint64_t da = smem_desc(S.a[s]);
+                const uint64_t db = smem_desc(S.b[s]);
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk)
+                  mma_bf16(d, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+                           (first && kk == 0) ? 0u : 1u);
+                first = false;
+                issued_any = true;
+                mma_commit(&S.empty[s]);
+              }
+            }
+            if (!ok) break;
+            mma_commit(&S.acc_full[buf]);
+          }
+        }
+      }
+      if (!ok) S.abort_flag = 1;
+      if (*(volatile int*)&S.abort_flag && issued_any) {
+        mma_commit(&S.drain);
+        mbar_wait(&S.drain, 0, 15);
+      }
+    }
+  } else {
+    // ---------------- epilogue: double-float sums of the chunks, then the output
+    const int q = warp & 3;                 // TMEM lane quarter of this warp
+    const int ew = warp - 2;
+    const int colbase = (ew >> 2) * 64;     // this warp's 64 columns of the tile
+    float* sh = S.stage[ew][0];
+    float* sl = S.stage[ew][1];
+    uint32_t ch = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
+      int m0, n0, kb0, nkb;
+      unit(u, m0, n0, kb0, nkb);
+      float hi[64], lo[64];
+#pragma unroll
+      for (int i = 0; i < 64; ++i) hi[i] = lo[i] = 0.f;
+      for (int l = 2; ok && l <= kOzMaxLevel; ++l) {
+        const int kbl = oz_chunk_blocks(l - 1);
+        for (int c0 = 0; c0 < nkb; c0 += kbl, ++ch) {
+          const uint32_t buf = ch & 1, use = ch >> 1;
+          if (!mbar_wait_or_abort(&S.acc_full[buf], use & 1, 16, &S.abort_flag)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t tl = tmem + buf * kOzBN + (uint32_t)colbase + ((uint32_t)(q * 32) << 16);
+#pragma unroll
+          for (int c = 0; c < 64; c += 8) {
+            float v[8];
+            tmem_ld8(tl + (uint32_t)c, v);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {   // (hi, lo) += v exactly up to lo's rounding
+              const float sum = __fadd_rn(hi[c + i], v[i]);
+              const float bp = __fsub_rn(sum, hi[c + i]);
+              const float err =
+                  __fadd_rn(__fsub_rn(hi[c + i], __fsub_rn(sum, bp)), __fsub_rn(v[i], bp));
+              hi[c + i] = sum;
+              lo[c + i] = __fadd_rn(lo[c + i], err);
+            }
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&S.acc_empty[buf]);
+        }
+      }
+      if (!ok) break;
+      // output: 32 x 32 blocks through the transpose buffers (lane = row on the way in,
+      // lane = column on the way out), so that every store instruction is coalesced
+      const int row0 = m0 + q * 32;
+#pragma unroll
+      for (int c = 0; c < 64; c += 32) {
+        const int col0 = n0 + colbase + c;
+        if (col0 >= args.N || row0 >= args.M) continue;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          sh[lane * 32 + (i ^ lane)] = hi[c + i];
+          sl[lane * 32 + (i ^ lane)] = lo[c + i];
+        }
+        __syncwarp();
+        const int col = col0 + lane;
+        const int nrow = min(32, args.M - row0);
+        if (col < args.N) {
+          if (args.out_mode == OZ_F64) {
+            double* cp = reinterpret_cast<double*>(args.C) + (long long)row0 * args.ldc + col;
+#pragma unroll 4
+            for (int r = 0; r < nrow; ++r)
+              cp[(long long)r * args.ldc] =
+                  (double)sh[r * 32 + (lane ^ r)] + (double)sl[r * 32 + (lane ^ r)];
+          } else if (args.out_mode == OZ_PAIR) {
+            float* cp = reinterpret_cast<float*>(args.C) + (long long)row0 * args.ldc + col;
+#pragma unroll 4
+            for (int r = 0; r < nrow; ++r) {
+              const float h = sh[r * 32 + (lane ^ r)], e = sl[r * 32 + (lane ^ r)];
+              const float sum = __fadd_rn(h, e);   // renormalised pair
+              cp[(long long)r * args.ldc] = sum;
+              cp[(long long)r * args.ldc + args.df_plane] = __fsub_rn(e, __fsub_rn(sum, h));
+            }
+          } else {
+            const int sp = u / (tiles_m * tiles_n);
+            float* cp = reinterpret_cast<float*>(args.C) + 2LL * sp * args.MN +
+                        (long long)row0 * args.N + col;
+#pragma unroll 4
+            for (int r = 0; r < nrow; ++r) {
+              cp[(long long)r * args.N] = sh[r * 32 + (lane ^ r)];
+              cp[(long long)r * args.N + args.MN] = sl[r * 32 + (lane ^ r)];
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+    if (!ok) S.abort_flag = 1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)(2 * kOzBN)));
+  }
+}
+
+// Launches tc_oz_kernel over planes A[0..7] (M x K, row stride lda) and B[0..7] (N x K).
+void launch_oz(const __nv_bfloat16* const* A, long long lda, const __nv_bfloat16* const* B,
+               long long ldb, int M, int N, int K, int splits, int out_mode, void* C,
+               long long ldc, long long df_plane, cudaStream_t s) {
+  TcMaps maps;
+  for (int i = 0; i < kMaxPlanes; ++i) {
+    maps.a[i] = make_map(A[i], M, K, lda, BM);
+    maps.b[i] = make_map(B[i], N, K, ldb, kOzBN);
+  }
+  for (int i = 0; i < 3; ++i) {
+    maps.a2[i] = maps.a[i];
+    maps.b2[i] = maps.b[i];
+  }
+  maps.c = maps.a[0];
+  const size_t smem = sizeof(OzSmem) + 1024;
+  static std::once_flag once;
+  std::call_once(once, [smem] {
+    A2_CUDA(cudaFuncSetAttribute(tc_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+  });
+  static int num_sms = 0;
+  static std::once_flag sms_once;
+  std::call_once(sms_once, [] {
+    int dev = 0;
+    A2_CUDA(cudaGetDevice(&dev));
+    A2_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+  });
+  OzArgs args;
+  args.M = M; args.N = N;
+  args.nk = (K + BK - 1) / BK;
+  splits = std::max(1, std::min(splits, args.nk));
+  args.kblocks_per_split = (args.nk + splits - 1) / splits;
+  args.splits = (args.nk + args.kblocks_per_split - 1) / args.kblocks_per_split;
+  A2_REQUIRE(args.splits == 1 || out_mode == OZ_SPLIT, "Ozaki GEMM: K splits need split tiles");
+  args.n_fast = cdiv(N, kOzBN) <= 64 ? 1 : 0;
+  args.out_mode = out_mode;
+  args.C = C; args.ldc = ldc; args.df_plane = df_plane;
+  args.MN = (long long)M * N;
+  const long long units = (long long)cdiv(M, BM) * cdiv(N, kOzBN) * args.splits;
+  A2_REQUIRE(units < (1LL << 31), "Ozaki GEMM too large");
+  const int grid = (int)std::min<long long>(units, std::max(1, num_sms));
+  tc_oz_kernel<<<grid, kOzThreads, smem, s>>>(maps, args);
+  A2_CHECK_LAUNCH();
+}
+
 }  // namespace tc
 
 bool tc_available() { return true; }
@@ -1240,45 +1602,45 @@ void tc_gemm_f64emu(const __nv_bfloat16* A, long long lda, long long aplane,
                     const __nv_bfloat16* B, long long ldb, long long bplane, int M, int N, int K,
                     double* C, long long ldc, DevBuf& slab, cudaStream_t s, float* Cdf,
                     long long df_plane) {
-  const int nk = (K + tc::BK - 1) / tc::BK;
-  const long long MN = (long long)M * N;
-  long long ntiles = 0;
-  for (int l = 2; l <= kOzSlices + 1; ++l) {
-    const int kb = std::max(1, 16 / (l - 1));
-    ntiles += (nk + kb - 1) / kb;
-  }
-  slab.ensure(sizeof(float) * (size_t)(ntiles * MN), s);
-  float* T = slab.as<float>();
+  if (M <= 0 || N <= 0) return;
+  static int num_sms = 0;
+  static std::once_flag sms_once;
+  std::call_once(sms_once, [] {
+    int dev = 0;
+    A2_CUDA(cudaGetDevice(&dev));
+    A2_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+  });
   const __nv_bfloat16* Ap[tc::kMaxPlanes];
   const __nv_bfloat16* Bp[tc::kMaxPlanes];
   for (int i = 0; i < tc::kMaxPlanes; ++i) {
     Ap[i] = A + i * aplane;
     Bp[i] = B + i * bplane;
   }
-  long long t = 0;
-  for (int l = 2; l <= kOzSlices + 1; ++l) {
-    const int np = l - 1;
-    int pa[tc::kMaxPairs], pb[tc::kMaxPairs];
-    for (int i = 0; i < np; ++i) {   // slices (i + 1, l - i - 1) -> planes (i, np - 1 - i)
-      pa[i] = i;
-      pb[i] = np - 1 - i;
-    }
-    const int kb = std::max(1, 16 / np);
-    const int want = (nk + kb - 1) / kb;
-    const int got = N <= 128
-        ? tc::launch<128, 6, false>(Ap, lda, Bp, ldb, M, N, K, np, pa, pb, nullptr, T + t * MN,
-                                    N, tc::OUT_F32, want, s, MN)
-        : tc::launch<256, 4, false>(Ap, lda, Bp, ldb, M, N, K, np, pa, pb, nullptr, T + t * MN,
-                                    N, tc::OUT_F32, want, s, MN);
-    A2_REQUIRE(got >= 1 && got <= want, "FP64 emulation: unexpected K split");
-    t += got;
+  // K splits: at most kOzSplitBlocks K blocks per split (bounds the number of chunk sums
+  // per accumulator, hence the rounding of its lo part), and enough work units to fill
+  // the GPU when the output has few tiles
+  constexpr int kOzSplitBlocks = 64;
+  const int nk = (K + tc::BK - 1) / tc::BK;
+  const long long tiles = (long long)cdiv(M, tc::BM) * cdiv(N, tc::kOzBN);
+  int splits = cdiv(nk, kOzSplitBlocks);
+  if (tiles < num_sms) splits = std::max<int>(splits, (int)cdiv(2LL * num_sms, tiles));
+  splits = std::max(1, std::min(splits, nk));
+  splits = cdiv(nk, cdiv(nk, splits));   // the count launch_oz will use
+  if (splits == 1) {
+    if (Cdf) tc::launch_oz(Ap, lda, Bp, ldb, M, N, K, 1, tc::OZ_PAIR, Cdf, ldc, df_plane, s);
+    else tc::launch_oz(Ap, lda, Bp, ldb, M, N, K, 1, tc::OZ_F64, C, ldc, 0, s);
+    return;
   }
+  const long long MN = (long long)M * N;
+  slab.ensure(sizeof(float) * (size_t)(2LL * splits * MN), s);
+  float* T = slab.as<float>();
+  tc::launch_oz(Ap, lda, Bp, ldb, M, N, K, splits, tc::OZ_SPLIT, T, N, 0, s);
   const int grid = (int)std::min<long long>((MN + 255) / 256, 152LL * 16);
   if (Cdf)
-    ozaki_combine_kernel<true><<<grid, 256, 0, s>>>(T, MN, (int)t, N, nullptr, Cdf, df_plane,
-                                                    ldc);
+    ozaki_combine_kernel<true><<<grid, 256, 0, s>>>(T, MN, 2 * splits, N, nullptr, Cdf,
+                                                    df_plane, ldc);
   else
-    ozaki_combine_kernel<false><<<grid, 256, 0, s>>>(T, MN, (int)t, N, C, nullptr, 0, ldc);
+    ozaki_combine_kernel<false><<<grid, 256, 0, s>>>(T, MN, 2 * splits, N, C, nullptr, 0, ldc);
   A2_CHECK_LAUNCH();
 }
 

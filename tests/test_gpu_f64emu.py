@@ -116,3 +116,49 @@ def test_f64emu_sweep_matches_fp64(ctx, chem6):
     assert abs(r64["lambda_coarse"] - re["lambda_coarse"]) < 1e-11 * abs(r64["lambda_coarse"])
     assert np.allclose(r64["energy_local"], re["energy_local"], atol=1e-11)
     assert abs(out["fp64"][1] - out["f64emu"][1]) < 1e-11
+
+
+@pytest.mark.parametrize("j,Dlb,Drb,Dlk,Drk", [(0, 1, 9, 1, 12), (2, 11, 9, 7, 12),
+                                               (3, 40, 33, 40, 33), (5, 16, 1, 9, 1)])
+def test_env_update_f64emu_matches_oracle(ctx, chem6, j, Dlb, Drb, Dlk, Drk):
+    """Environment updates with both GEMMs Ozaki-emulated and the sparse stage in
+    double-float arithmetic (the path the mixed and FP64-emulated sweeps use for their
+    FP64 environments): bra and ket of different shapes, ragged dims."""
+    from oracle.env import env_left_update, env_right_update
+    m = chem6
+    mpo = a2.MPO(ctx, m)
+    W = m[j]
+    rng = np.random.default_rng(40 + j)
+    bra = rng.standard_normal((Dlb, 4, Drb))
+    ket = rng.standard_normal((Dlk, 4, Drk))
+    Hin = rng.standard_normal((Dlb, W.shape[0], Dlk))
+    ref = env_left_update(Hin, bra, W, ket)
+    out = torch.zeros(ref.shape, dtype=torch.float64, device="cuda")
+    a2.env_update(ctx, mpo, j, 0, dev(Hin), dev(bra), dev(ket), out, prec="f64emu")
+    assert rel(host(out, ctx), ref) < 1e-13
+    Hr = rng.standard_normal((Drb, W.shape[3], Drk))
+    ref = env_right_update(Hr, bra, W, ket)
+    out = torch.zeros(ref.shape, dtype=torch.float64, device="cuda")
+    a2.env_update(ctx, mpo, j, 1, dev(Hr), dev(bra), dev(ket), out, prec="f64emu")
+    assert rel(host(out, ctx), ref) < 1e-13
+
+
+def test_env_update_f64emu_large_and_scaled(ctx, chem16):
+    """A middle site of the L = 16 MPO (R = 562) at bond 96 with the input environment's
+    rows scaled over 2^-40 .. 2^40: sampled output slices against the oracle."""
+    from oracle.env import env_left_update_entry
+    m = chem16
+    j = 8
+    mpo = a2.MPO(ctx, m)
+    W = m[j]
+    rng = np.random.default_rng(77)
+    D = 96
+    bra = rng.standard_normal((D, 4, D))
+    Hin = rng.standard_normal((D, W.shape[0], D))
+    Hin *= np.exp2(np.linspace(-40, 40, W.shape[0]))[None, :, None]
+    out = torch.zeros((D, W.shape[3], D), dtype=torch.float64, device="cuda")
+    a2.env_update(ctx, mpo, j, 0, dev(Hin), dev(bra), dev(bra), out, prec="f64emu")
+    got = host(out, ctx)
+    for b, bp in [(0, 0), (5, 77), (95, 3), (40, 40)]:
+        ref = env_left_update_entry(Hin, bra, W, bra, b, bp)
+        assert rel(got[b, :, bp], ref) < 1e-12
