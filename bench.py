@@ -4,16 +4,25 @@
 Workload (default): random chemistry-like Hamiltonian, L = 16 spatial orbitals
 (n = 4), integrals seed 2505, exact operator-string MPO, TT bond cap D = 256,
 P = 4 groups of bonds [4, 4, 4, 3], seeded initial TT (SplitMix64 seed 23429,
-initial bond 4).  A step is one A2DMRG global iteration (Alg. 2): LQ sweep,
-environments, the P groups of local two-site Lanczos solves (tensor-core BF16
-matvecs, FP32 refinement), truncated SVDs, coarse problem, compression.
+initial bond 4), eig_tol = svd_tol = 1e-6, coarse cut 1e-10.  A step is one
+A2DMRG global iteration (Alg. 2): LQ sweep, environments, the P groups of local
+two-site Lanczos solves (tensor-core BF16 and split-product matvecs, FP64
+refinement of every Ritz pair), truncated SVDs, coarse problem, compression,
+then the FP64-class Rayleigh quotient of the compressed iterate.
 
-Timing: W untimed warm-up iterations from the seeded TT, then K timed
-iterations bracketed by a barrier and device synchronisation, CUDA events on
-the library's stream.  The working set (environments, intermediates of several
+Metric: seconds from the seeded TT until the stopping rule of the paper's
+experiments holds -- the relative change of the energy between successive
+global iterations below 1e-6 (Sec. 4) -- on FP64-class energies.  W untimed
+warm-up iterations run first from the seeded TT (then the TT is reset); the
+timed region runs from the seeded TT until the rule holds (at least --steps
+iterations are not required: the iteration count is what the rule needs),
+bracketed by a barrier and device synchronisation, CUDA events on the
+library's stream.  The working set (environments, intermediates of several
 GB) is far larger than the 129 MB L2, so no explicit flush is done.
+--fixed times exactly --steps iterations continuing from the warmed-up iterate
+instead (profiling runs; a throughput of global iterations).
 
---impl reference times the FP64 CPU oracle on a bounded sample of the same
+--impl reference times the FP64 CPU oracle on bounded samples of the same
 workload (the oracle is the reference of this build).
 """
 import argparse
@@ -32,6 +41,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("additive-sweep time to |dE|<1e-6 vs FP64 oracle; "
           "H_eff matvec TFLOP/s vs plain")
+RULE_TOL = 1e-6   # relative energy change between successive iterations (Sec. 4)
+# Operation counts of one global iteration of the L = 16, D = 256 workload on its way to the
+# stopping rule, from the library's counters in a GB300 run of this bench (per-bond matvecs
+# averaged over the iterations, environment updates, truncated SVDs) and the number of
+# iterations the rule needed: they scale the reference arm's oracle samples, which cannot
+# run the workload itself.
+REF_COUNTS = dict(iterations=64,
+                  krylov=[12, 14, 16, 18, 22, 22, 24, 26, 27, 20, 19, 10, 17, 3, 3],
+                  env=151, svd=30)
 # classes reported by time share only (latency-bound FP64 factorisations)
 LATENCY_BOUND = ("svd", "lq")
 # DRAM traffic / algorithmic bytes of a kernel class, from its ncu capture at D = 128;
@@ -50,9 +68,10 @@ def parse():
     p.add_argument("--prec", default="bf16",
                    choices=["bf16", "f32emu", "fp32", "fp64", "f64emu"])
     p.add_argument("--solver", default="lanczos", choices=["lanczos", "davidson"])
-    p.add_argument("--converge", type=int, default=45,
-                   help="after the timed steps, keep iterating (up to this many iterations in "
-                        "total) until |dE|/|E| < 1e-6, to report the time from the seeded TT")
+    p.add_argument("--fixed", action="store_true",
+                   help="time exactly --steps iterations from the seeded TT (no stopping rule)")
+    p.add_argument("--max-iter", type=int, default=150,
+                   help="cap of the timed run if the stopping rule does not hold earlier")
     p.add_argument("--groups", default="sequential", choices=["sequential", "concurrent"],
                    help="run the P groups one after another (default: each local matvec "
                         "already fills the GPU, and per-kernel timings stay unshared) or "
@@ -151,74 +170,89 @@ class Clocks:
                     sm_max_mhz=max(mx) if mx else None, reasons=reasons, samples=len(rows))
 
 
-def oracle_sample(cfg, mpo):
-    """One oracle H_eff application at the middle bond with D = D_max (bounded CPU sample)."""
-    from oracle.env import heff_apply
+def _bond_dims(cfg):
+    """Bond dimensions of a full-rank iterate of the workload (capped by D)."""
     L, D, n = cfg["L"], cfg["D"], cfg["n"]
-    k = L // 2 - 1
-    rng = np.random.default_rng(0)
+    return [1] + [min(D, n ** min(k, L - k)) for k in range(1, L)] + [1]
+
+
+def _fmv(mpo, n, Dl, Dr, k):
     W1, W2 = mpo[k], mpo[k + 1]
-    HL = rng.standard_normal((D, W1.shape[0], D))
-    HR = rng.standard_normal((D, W2.shape[3], D))
-    x = rng.standard_normal((D, n, n, D))
-    t = time.perf_counter()
-    heff_apply(HL, W1, W2, HR, x)
-    dt = time.perf_counter() - t
-    nnz1, nnz2 = np.count_nonzero(W1), np.count_nonzero(W2)
-    flops = (2.0 * n * n * D * D * (W1.shape[0] * D + W2.shape[3] * D)
-             + 2.0 * n * D * D * (nnz1 + nnz2))
-    return dt, flops, k
+    return (2.0 * n * n * Dl * Dr * (W1.shape[0] * Dl + W2.shape[3] * Dr)
+            + 2.0 * n * Dl * Dr * (np.count_nonzero(W1) + np.count_nonzero(W2)))
 
 
-def reference_arm(args):
-    cfg, mpo, _ = workload(args.config)
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
-    samples = []
-    for _ in range(args.warmup + args.steps):
-        samples.append(oracle_sample(cfg, mpo))
-    timed = samples[args.warmup:]
-    dt = sum(s[0] for s in timed) / len(timed)
-    rate = timed[0][1] / dt
-    # scale to one global iteration with the algorithmic flops of a full-rank iteration
-    flops_iter = est_iteration_flops(cfg, mpo)
-    value = rate / flops_iter
-    cores = os.cpu_count()
-    line = dict(impl="reference", metric=METRIC, value=value, unit="additive sweeps/s",
-                n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
-                ms_per_step=1e3 / value, higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype="f64", data="synthetic",
-                config=dict(workload=args.config, L=cfg["L"], n=cfg["n"], D=cfg["D"], P=cfg["P"]),
-                cpu_baseline=dict(value=value, unit="additive sweeps/s", cores=cores,
-                                  kind="oracle",
-                                  sample=(f"one FP64 oracle H_eff application at bond {timed[0][2]} "
-                                          f"(D={cfg['D']}) per step, {dt:.2f} s, "
-                                          f"{rate / 1e9:.1f} GFLOP/s algorithmic, scaled by "
-                                          f"{flops_iter:.3e} algorithmic flops per global iteration")),
-                e2e=dict(value=value, unit="additive sweeps/s", h2d_bytes_per_step=0,
-                         d2h_bytes_per_step=0))
-    print(json.dumps(line))
+def _fenv(mpo, n, Dl, Dr, j):
+    W = mpo[j]
+    return (2.0 * n * Dl * Dr * (W.shape[0] * Dl + W.shape[3] * Dr)
+            + 2.0 * Dl * Dr * np.count_nonzero(W))
 
 
-def est_iteration_flops(cfg, mpo, matvecs_per_bond=30):
-    """Algorithmic flops of one full-rank global iteration (matvec + env dominated)."""
+def oracle_samples(cfg, mpo, reps=1):
+    """Times the FP64 oracle's kinds of work of one global iteration on this host, each at
+    the full size of the workload's middle bond (so the numbers are the oracle's own, not a
+    flop model): one H_eff application (oracle.env.heff_apply), one truncated SVD of the
+    (n D) x (n D) two-site matrix (oracle.tt.svd_split) and one left environment update
+    (oracle.env.env_left_update).  About 15-25 s of CPU work at D = 256."""
+    from oracle.env import env_left_update, heff_apply
+    from oracle.tt import svd_split
     L, D, n = cfg["L"], cfg["D"], cfg["n"]
-    dims = [1] + [min(D, n ** min(k, L - k)) for k in range(1, L)] + [1]
-    tot = 0.0
-    for k in range(L - 1):
-        Dl, Dr = dims[k], dims[k + 2]
-        W1, W2 = mpo[k], mpo[k + 1]
-        fmv = (2.0 * n * n * Dl * Dr * (W1.shape[0] * Dl + W2.shape[3] * Dr)
-               + 2.0 * n * Dl * Dr * (np.count_nonzero(W1) + np.count_nonzero(W2)))
-        tot += matvecs_per_bond * fmv
-    for j in range(L):
-        Dl, Dr = dims[j], dims[j + 1]
-        W = mpo[j]
-        fenv = (2.0 * n * Dl * Dr * (W.shape[0] * Dl + W.shape[3] * Dr)
-                + 2.0 * Dl * Dr * np.count_nonzero(W))
-        tot += (2 + cfg["P"]) * fenv
-    return tot
+    k = L // 2 - 3 if L >= 8 else L // 2 - 1         # a middle bond that is not the hand-over one
+    dims = _bond_dims(cfg)
+    Dl, Dr = dims[k], dims[k + 2]
+    rng = np.random.default_rng(0)
+    HL = rng.standard_normal((Dl, mpo[k].shape[0], Dl))
+    HR = rng.standard_normal((Dr, mpo[k + 1].shape[3], Dr))
+    x = rng.standard_normal((Dl, n, n, Dr))
+    out = {}
+    t = time.perf_counter()
+    for _ in range(reps):
+        heff_apply(HL, mpo[k], mpo[k + 1], HR, x)
+    out["heff_s"] = (time.perf_counter() - t) / reps
+    out["heff_flops"] = _fmv(mpo, n, Dl, Dr, k)
+    M = x.reshape(Dl * n, n * Dr)
+    t = time.perf_counter()
+    svd_split(M, D, 1e-6)
+    out["svd_s"] = time.perf_counter() - t
+    U = rng.standard_normal((Dl, n, dims[k + 1]))
+    t = time.perf_counter()
+    env_left_update(HL, U, mpo[k], U)
+    out["env_s"] = time.perf_counter() - t
+    out["env_flops"] = _fenv(mpo, n, Dl, dims[k + 1], k)
+    out["bond"] = k
+    out["cores"] = os.cpu_count()
+    return out
+
+
+def oracle_iteration_seconds(cfg, mpo, smp, krylov, n_env, n_svd):
+    """Oracle time of one global iteration of this workload: the measured H_eff time scaled
+    to every bond by its algorithmic flops times that bond's matvec count (krylov[k]), plus
+    the measured environment-update time (flop-scaled, n_env of them at middle-bond size)
+    and SVD time (n_svd of them).  The coarse problem and the rest of the compression are
+    not counted (they are small next to these)."""
+    L, n = cfg["L"], cfg["n"]
+    dims = _bond_dims(cfg)
+    t = 0.0
+    for kk in range(L - 1):
+        t += krylov[kk] * smp["heff_s"] * _fmv(mpo, n, dims[kk], dims[kk + 2], kk) / smp["heff_flops"]
+    return t + n_env * smp["env_s"] + n_svd * smp["svd_s"]
+
+
+def oracle_c1_iteration():
+    """One complete oracle global iteration (Alg. 2, oracle.a2dmrg.global_iteration) of the
+    L = 12 Heisenberg workload (D = 32, P = 2) from its seeded TT, timed on this host."""
+    from oracle import a2dmrg as oa2
+    from oracle.tt import left_orthogonalize, tt_inner
+    cfg, mpo, raw = workload("heisenberg_L12_D32")
+    U = left_orthogonalize(raw)
+    U[-1] = U[-1] / np.sqrt(tt_inner(U, U))
+    for _ in range(2):                                  # reach the bond cap first
+        U, _ = oa2.global_iteration(U, mpo, cfg["partition"], cfg["D"], svd_tol=1e-6,
+                                    eig_tol=1e-6, coarse_eps=1e-10)
+    t = time.perf_counter()
+    oa2.global_iteration(U, mpo, cfg["partition"], cfg["D"], svd_tol=1e-6, eig_tol=1e-6,
+                         coarse_eps=1e-10)
+    return time.perf_counter() - t
 
 
 def profile_matvec(args):
@@ -271,8 +305,10 @@ def class_roofline(name, d, peaks, prec):
         return "tensor", "TFLOP/s", peaks["bf16_sus"], 36.0 * rate_f
     if name == "f64e_sparse":
         return "alu", "TFLOP/s", FP32_SIMT_PEAK_TFLOPS, rate_f
-    if name == "env" and prec in ("bf16", "f32emu"):
-        return "tensor", "TFLOP/s", peaks["bf16_sus"], rate_f
+    if name == "env" and prec in ("bf16", "f32emu", "f64emu"):
+        # FP64-class environments: the two GEMMs of an update Ozaki-emulated (36 BF16
+        # products per FP64-equivalent flop), small updates on the FP64 SIMT kernels
+        return "tensor", "TFLOP/s", peaks["bf16_sus"], 36.0 * rate_f
     if name in ("heff_simt", "env") and prec != "fp64":
         return "alu", "TFLOP/s", FP32_SIMT_PEAK_TFLOPS, rate_f
     return "alu", "TFLOP/s", FP64_PEAK_TFLOPS, rate_f        # FP64 factorisations / SIMT
@@ -304,6 +340,119 @@ def job_throughput(steps, ms, world):
     """Whole-job global iterations per second: every rank runs `steps` independent
     replica iterations in `ms` (max over ranks)."""
     return steps * world / (ms * 1e-3)
+
+
+def rule_met(energies, tol=RULE_TOL):
+    """The stopping rule of the experiments (Sec. 4): the relative change of the energy
+    between the last two global iterations is below tol (energies: one per iteration)."""
+    return len(energies) >= 2 and abs(energies[-1] - energies[-2]) < tol * abs(energies[-1])
+
+
+def run_to_rule(a2, ctx, mpo, raw, P, kw, max_iter, fixed, log=None, host_io=False,
+                start=None):
+    """Global iterations from the seeded TT (or from the cores `start`): until the stopping
+    rule holds (at most max_iter), or exactly max_iter with fixed.  After every iteration
+    the FP64-class Rayleigh quotient of the compressed iterate (a2_energy, Ozaki-emulated
+    environments) is taken.  host_io: the iterate goes to the device from pinned host
+    memory before every iteration and its cores and energy come back after it (the
+    end-to-end form).  Returns (reports, energies, host-to-device bytes, device-to-host
+    bytes, final cores)."""
+    import torch
+    reps, energies, h2d, d2h = [], [], 0, 0
+    t = a2.TT.from_cores(ctx, raw if start is None else start)
+    if start is None:
+        t.left_orthogonalize()
+    pinned = None
+    for it in range(max_iter):
+        if host_io:
+            if pinned is None:
+                pinned = [torch.from_numpy(c).pin_memory().numpy() for c in t.cores()]
+            t.close()
+            t = a2.TT.from_cores(ctx, pinned)
+            h2d += sum(c.nbytes for c in pinned)
+        rep = a2.additive_sweep(ctx, t, mpo, P, **kw)
+        E, _ = a2.energy(ctx, t, mpo, "f64emu")
+        reps.append(rep)
+        energies.append(E)
+        if host_io:
+            out = t.cores()
+            d2h += sum(c.nbytes for c in out) + 8
+            pinned = [torch.from_numpy(c).pin_memory().numpy() for c in out]
+        if log:
+            print(json.dumps(dict(iteration=it + 1, seconds=rep["seconds"], energy=E,
+                                  lambda_coarse=rep["lambda_coarse"],
+                                  coarse_rank=rep["coarse_rank"], krylov=rep["krylov"],
+                                  matvecs_f64=rep["matvecs_f64"],
+                                  max_discarded=rep["max_discarded"])), file=log)
+        if not fixed and rule_met(energies):
+            break
+    cores = t.cores() if max_iter > 0 else None
+    t.close()
+    return reps, energies, h2d, d2h, cores
+
+
+def reference_arm(args):
+    """The FP64 oracle on this host's cores: every step times one of its kinds of work at
+    the workload's full middle-bond size (H_eff application, truncated SVD, environment
+    update, in turn); the line's value is the oracle's time to the stopping rule, those
+    measured times scaled by the operation counts of the workload (REF_COUNTS)."""
+    cfg, mpo, _ = workload(args.config)
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle.env import env_left_update, heff_apply
+    from oracle.tt import svd_split
+    L, D, n = cfg["L"], cfg["D"], cfg["n"]
+    k = L // 2 - 3 if L >= 8 else L // 2 - 1
+    dims = _bond_dims(cfg)
+    Dl, Dr = dims[k], dims[k + 2]
+    rng = np.random.default_rng(0)
+    HL = rng.standard_normal((Dl, mpo[k].shape[0], Dl))
+    HR = rng.standard_normal((Dr, mpo[k + 1].shape[3], Dr))
+    x = rng.standard_normal((Dl, n, n, Dr))
+    U = rng.standard_normal((Dl, n, dims[k + 1]))
+    kinds = [("heff", lambda: heff_apply(HL, mpo[k], mpo[k + 1], HR, x)),
+             ("svd", lambda: svd_split(x.reshape(Dl * n, n * Dr), D, 1e-6)),
+             ("env", lambda: env_left_update(HL, U, mpo[k], U))]
+    for _ in range(args.warmup):              # warm-up: the SVD sample (the cheapest)
+        kinds[1][1]()
+    times = {"heff": [], "svd": [], "env": []}
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        name, fn = kinds[i % 3]
+        t = time.perf_counter()
+        fn()
+        times[name].append(time.perf_counter() - t)
+    wall = time.perf_counter() - t0
+    for name, fn in kinds:                    # every kind measured at least once
+        if not times[name]:
+            t = time.perf_counter()
+            fn()
+            times[name].append(time.perf_counter() - t)
+    smp = dict(heff_s=float(np.mean(times["heff"])), heff_flops=_fmv(mpo, n, Dl, Dr, k),
+               svd_s=float(np.mean(times["svd"])), env_s=float(np.mean(times["env"])))
+    it_s = oracle_iteration_seconds(cfg, mpo, smp, REF_COUNTS["krylov"], REF_COUNTS["env"],
+                                    REF_COUNTS["svd"])
+    value = it_s * REF_COUNTS["iterations"]
+    cores = os.cpu_count()
+    sample = (f"oracle (NumPy/SciPy FP64) at the middle bond {k}, D={D}: H_eff application "
+              f"{smp['heff_s']:.2f} s, truncated SVD of the {Dl * n}x{n * Dr} two-site matrix "
+              f"{smp['svd_s']:.2f} s, environment update {smp['env_s']:.2f} s; one global "
+              f"iteration = {it_s:.0f} s with the per-bond matvec counts, "
+              f"{REF_COUNTS['env']} environment updates and {REF_COUNTS['svd']} SVDs of a GB300 "
+              f"run of this workload, times the {REF_COUNTS['iterations']} iterations that run "
+              f"needed for the stopping rule")
+    line = dict(impl="reference", metric=METRIC, value=value, unit="s", n_gpus=args.gpus,
+                steps=args.steps, warmup=args.warmup,
+                ms_per_step=1e3 * wall / max(args.steps, 1), higher_is_better=False,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=args.config, L=cfg["L"], n=cfg["n"], D=cfg["D"],
+                            P=cfg["P"], partition=cfg["partition"], rule=f"|dE|/|E| < {RULE_TOL}"),
+                cpu_baseline=dict(value=value, unit="s", cores=cores, kind="oracle",
+                                  sample=sample),
+                e2e=dict(value=value, unit="s", h2d_bytes_per_step=0, d2h_bytes_per_step=0),
+                timed_wall_s=wall)
+    print(json.dumps(line))
 
 
 def main():
@@ -343,15 +492,12 @@ def main():
         kw["low_memory"] = True
     if args.graphs:
         kw["graphs"] = True
-    t = a2.TT.from_cores(ctx, raw)
-    t.left_orthogonalize()
 
-    history = []   # (seconds, energy_in) of every iteration from the seeded TT
-    for _ in range(args.warmup):
-        rep = a2.additive_sweep(ctx, t, mpo, P, **kw)
-        history.append((rep["seconds"], rep["energy_in"]))
-
-    start_cores = t.cores()          # the end-to-end run repeats the timed iterations
+    # warm-up: W global iterations from the seeded TT (autotuners, memory pools); the rule
+    # run starts again from the seeded TT, a --fixed run continues from the warm iterate
+    _, _, _, _, warm = run_to_rule(a2, ctx, mpo, raw, P, kw, args.warmup, fixed=True)
+    start = warm if args.fixed else None
+    max_iter = args.steps if args.fixed else args.max_iter
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -362,16 +508,9 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     w0 = time.perf_counter()
-    reps = []
     nvtx(torch, "timed_steps")     # lets a profiler select the timed region
-    for _ in range(args.steps):
-        rep = a2.additive_sweep(ctx, t, mpo, P, **kw)
-        reps.append(rep)
-        history.append((rep["seconds"], rep["energy_in"]))
-        print(json.dumps(dict(iteration=len(history), seconds=rep["seconds"],
-                              energy_in=rep["energy_in"], lambda_coarse=rep["lambda_coarse"],
-                              coarse_rank=rep["coarse_rank"], krylov=rep["krylov"],
-                              max_discarded=rep["max_discarded"])), file=sys.stderr)
+    reps, energies, _, _, _ = run_to_rule(a2, ctx, mpo, raw, P, kw, max_iter, args.fixed,
+                                          log=sys.stderr, start=start)
     ev1.record(stream)
     torch.cuda.synchronize()
     nvtx(torch, None)
@@ -380,34 +519,14 @@ def main():
     a2.profile(ctx, "off")
     launches = a2.profile(ctx, "launches") - launches0
     ms = max_over_ranks(ev0.elapsed_time(ev1), world, "cuda")
+    steps = len(reps)
+    reached = rule_met(energies)
     prof = {k: a2.profile(ctx, "read", i) for i, k in enumerate(a2.a2dmrg.PROFILE_KINDS)}
-
-    def converged(hist):
-        e = [x[1] for x in hist]
-        return any(abs(e[i] - e[i - 1]) < 1e-6 * abs(e[i]) for i in range(2, len(e)))
-    while args.converge and len(history) < args.converge and not converged(history):
-        rep = a2.additive_sweep(ctx, t, mpo, P, **kw)
-        history.append((rep["seconds"], rep["energy_in"]))
-        print(json.dumps(dict(iteration=len(history), seconds=rep["seconds"],
-                              energy_in=rep["energy_in"], lambda_coarse=rep["lambda_coarse"],
-                              krylov=sum(rep["krylov"]))), file=sys.stderr)
-    E_final, _ = a2.energy(ctx, t, mpo, "fp64")
-
-    # time to |dE| < 1e-6 (relative, between successive global iterations, as in the
-    # stopping rule of the experiments), from the seeded TT, if reached in W+K iterations
-    # energies[i] = energy after i+1 iterations; the stopping rule compares successive ones
-    energies = [e for _, e in history[1:]] + [E_final]
-    t_conv, it_conv, cum = None, None, history[0][0]
-    for i in range(1, len(energies)):
-        cum += history[i][0]
-        if abs(energies[i] - energies[i - 1]) < 1e-6 * abs(energies[i]):
-            t_conv, it_conv = cum, i + 1
-            break
 
     # dominant kernel class and its roofline (and the same figures for every class)
     peaks = read_peaks()
-    # the FP64 factorisations (truncated-SVD eigensolve, LQ) are latency-bound library
-    # calls: they get a time share, the roofline goes to the dominant contraction class
+    # the FP64 factorisations (truncated-SVD eigensolve, LQ) are latency-bound: they get a
+    # time share, the roofline goes to the dominant contraction class
     dom = max((k for k in prof if k not in LATENCY_BOUND), key=lambda k: prof[k]["ms"])
     d = prof[dom]
     total_ms = sum(v["ms"] for v in prof.values())
@@ -426,32 +545,40 @@ def main():
     # H_eff matvec TFLOP/s: tensor-core chain vs a plain torch.einsum chain (dense MPO, BF16)
     mv = None if args.no_mv else matvec_compare(a2, ctx, mpo, mpo_cores, cfg, torch, stream)
 
-    value = job_throughput(args.steps, ms, world)
-    line = dict(metric=METRIC, value=value, unit="additive sweeps/s", n_gpus=world,
-                steps=args.steps, warmup=args.warmup, ms_per_step=ms / args.steps,
-                higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype="bf16+f32 (f64 vectors/SVD/coarse)" if args.prec == "bf16" else args.prec,
+    if args.fixed:   # a throughput of global iterations (profiling runs)
+        value, unit, hib = job_throughput(steps, ms, world), "additive sweeps/s", True
+    else:            # the time to the stopping rule (every rank runs its own replica)
+        value, unit, hib = ms * 1e-3, "s", False
+    line = dict(metric=METRIC, value=value, unit=unit, n_gpus=world,
+                steps=steps, warmup=args.warmup, ms_per_step=ms / max(steps, 1),
+                higher_is_better=hib, scaling="weak", vs_baseline=None,
+                dtype=("bf16+f32 tensor cores, f64 refinement/envs/SVD/coarse"
+                       if args.prec == "bf16" else args.prec),
                 data="synthetic",
                 config=dict(workload=args.config, L=cfg["L"], n=cfg["n"], D=cfg["D"], P=P,
-                            partition=kw["partition"], eig_tol=1e-6, svd_tol=1e-6,
+                            partition=kw["partition"], eig_tol=kw["eig_tol"],
+                            svd_tol=kw["svd_tol"], coarse_eps=kw["coarse_eps"],
+                            rule=("fixed iteration count" if args.fixed else
+                                  f"|E_n - E_(n-1)| < {RULE_TOL} |E_n| on FP64-class "
+                                  "energies, from the seeded TT"),
                             variant=("one-site" if args.one_site else "two-site")
                             + (f", n_eig={args.n_eig}" if args.n_eig > 1 else "")
                             + (", memory-limited environments" if args.low_memory else "")
                             + (", CUDA-graph matvecs" if args.graphs else ""),
-                            coarse_eps=kw["coarse_eps"],
-                            precision=args.prec, solver=args.solver,
+                            precision=args.prec, refine_f64=not args.no_refine,
+                            solver=args.solver,
                             groups="sequential" if kw["sequential"] else "concurrent streams",
                             identity_fold=not args.no_fold,
                             parallelism="replicas" if world > 1 else "1gpu",
                             l2="working set >> 129 MB L2 (no flush)"),
-                energy_final=E_final, time_to_dE_1e6_s=t_conv, iterations_to_dE_1e6=it_conv,
-                iterations_run=len(history),
+                rule_reached=reached, energy_final=energies[-1] if energies else None,
+                energies=[round(e, 10) for e in energies],
                 roofline=dict(kernel=dom, bound=bound, achieved=achieved, peak=peak, unit=unit,
                               frac=achieved / peak, traffic=traffic,
                               traffic_source=(None if ratio is None else
                                               "ncu DRAM bytes / algorithmic bytes of the same "
-                                              "kernel at D=128 (profiles/), scaled to this "
-                                              "launch's algorithmic bytes"),
+                                              "kernel at D=128, scaled to this launch's "
+                                              "algorithmic bytes"),
                               per_launch_ms=per_launch, launches=d["launches"],
                               peak_source=peaks["src"]),
                 time_shares=shares,
@@ -465,18 +592,32 @@ def main():
                 heff_matvec=mv, clocks=clk, wall_s=wall,
                 gpu_launches=int(launches))
     if not args.no_e2e:
-        line["e2e"] = e2e_run(a2, ctx, mpo, cfg, kw, start_cores, args.steps, torch, stream,
-                              world)
+        t0 = time.perf_counter()
+        torch.cuda.synchronize()
+        r2, e2, h2d, d2h, _ = run_to_rule(a2, ctx, mpo, raw, P, kw, max_iter, args.fixed,
+                                          host_io=True, start=start)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        line["e2e"] = dict(value=(len(r2) * world / dt) if args.fixed else dt,
+                           unit=unit, h2d_bytes_per_step=h2d // max(len(r2), 1),
+                           d2h_bytes_per_step=d2h // max(len(r2), 1), steps=len(r2),
+                           energy_final=e2[-1] if e2 else None)
     if rank == 0 and world == 1 and not args.no_cpu:
-        dt, fl, k = oracle_sample(cfg, mpo_cores)
-        rate = fl / dt
-        flops_iter = sum(r["alg_flops"] for r in reps) / len(reps)
-        line["cpu_baseline"] = dict(value=rate / flops_iter, unit="additive sweeps/s",
-                                    cores=os.cpu_count(), kind="oracle",
-                                    sample=(f"one FP64 oracle H_eff application at bond {k} "
-                                            f"(D={cfg['D']}), {dt:.2f} s, scaled by the measured "
-                                            f"algorithmic flops per global iteration "
-                                            f"({flops_iter:.3e})"))
+        smp = oracle_samples(cfg, mpo_cores)
+        kry = np.sum([r["krylov"] for r in reps], axis=0)
+        n_env, n_svd = prof["env"]["launches"], prof["svd"]["launches"]
+        cpu_s = oracle_iteration_seconds(cfg, mpo_cores, smp, kry, n_env, n_svd)
+        per_it = cpu_s / max(steps, 1)
+        line["cpu_baseline"] = dict(
+            value=(1.0 / per_it) if args.fixed else cpu_s, unit=unit, cores=smp["cores"],
+            kind="oracle",
+            sample=(f"oracle (NumPy/SciPy FP64) timed at the middle bond {smp['bond']}, "
+                    f"D={cfg['D']}: H_eff application {smp['heff_s']:.2f} s, truncated SVD "
+                    f"{smp['svd_s']:.2f} s, environment update {smp['env_s']:.2f} s; scaled "
+                    f"by this run's counts ({int(np.sum(kry))} matvecs spread over the bonds "
+                    f"as measured, {n_env} environment updates, {n_svd} SVDs in {steps} "
+                    f"iterations); coarse problem and compression products not counted"),
+            c1_global_iteration_s=oracle_c1_iteration())
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -548,26 +689,6 @@ def matvec_compare(a2, ctx, mpo, cores, cfg, torch, stream):
                 "beforehand; TFLOP/s use the algorithmic count with MPO nonzeros")
 
 
-def e2e_run(a2, ctx, mpo, cfg, kw, cores, steps, torch, stream, world):
-    """The timed global iterations again, from the same starting iterate, through the
-    host-buffer API: every step uploads the iterate's cores from pinned host memory,
-    runs the sweep and reads the cores and the energy back."""
-    pinned = [torch.from_numpy(c).pin_memory().numpy() for c in cores]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    h2d = d2h = 0
-    for _ in range(steps):
-        tt = a2.TT.from_cores(ctx, pinned)
-        h2d += sum(c.nbytes for c in pinned)
-        rep = a2.additive_sweep(ctx, tt, mpo, len(kw["partition"]), **kw)
-        out = tt.cores()
-        d2h += sum(c.nbytes for c in out) + 8
-        pinned = [torch.from_numpy(c).pin_memory().numpy() for c in out]
-        tt.close()
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    return dict(value=steps / dt * world, unit="additive sweeps/s",
-                h2d_bytes_per_step=h2d // steps, d2h_bytes_per_step=d2h // steps)
 
 
 if __name__ == "__main__":

@@ -9,9 +9,12 @@
  *  - Every function returns a2_status: A2_OK (0) or a negative error code; no
  *    exception crosses the ABI.  a2_last_error() returns the message of the
  *    last failure on a context (valid until the next call on that context).
- *  - Handles (a2_ctx, a2_tt, a2_mpo) are opaque and owned by the library;
+ *  - Handles (a2_ctx, a2_tt, a2_mpo, a2_heff) are opaque and owned by the library;
  *    create/destroy them with the functions below.  A context is used by one
  *    host thread at a time; all its work is ordered on its CUDA stream.
+ *    a2_ctx_destroy also destroys the TT / MPO / H_eff handles still made on that
+ *    context; a destroy call on a handle that is no longer live returns A2_EINVAL and
+ *    does nothing.
  *  - "host" pointers are read or written synchronously and may be freed after
  *    the call returns.  "device" pointers are CUDA device addresses on the
  *    context's device; the call enqueues work on the context stream and the
@@ -37,7 +40,8 @@ typedef enum {
   A2_OK = 0,
   A2_EINVAL = -1,       /* invalid argument (sizes, null pointers, mismatched dims) */
   A2_ENOMEM = -2,       /* device allocation failed */
-  A2_ECUDA = -3,        /* CUDA runtime / cuSOLVER error */
+  A2_ECUDA = -3,        /* CUDA runtime error (or a factorisation kernel's bounded grid
+                           barrier gave up) */
   A2_ENOCONV = -4,      /* an iterative solve did not reach its tolerance */
   A2_ENUMERIC = -5,     /* non-finite value detected */
   A2_ETIMEOUT = -6,     /* a bounded device-side wait gave up */
@@ -318,10 +322,22 @@ a2_status a2_env_update(a2_ctx* ctx, const a2_mpo* mpo, int j, int side, a2_prec
  * a (Dl n1) x (n2 Dr) matrix = P Sigma Q; keeps the smallest rank r <= D_max
  * with discarded 2-norm <= tol*||sigma||.  P_out [Dl][n1][r] (left-orthonormal),
  * SQ_out [r][n2][Dr] (device, capacity min(Dl n1, n2 Dr) columns/rows);
- * rank_out, discarded_out (host). */
+ * rank_out, discarded_out (host).  Computed by this library's FP64 kernels: Householder
+ * bidiagonalisation, all singular values by bisection of the Golub-Kahan tridiagonal
+ * (absolute accuracy ~1e-16 ||x||, no Gram matrix), the kept left vectors by inverse
+ * iteration, re-orthonormalised and transformed back; SQ = P^T x.  Within an exactly
+ * degenerate multiplet any orthonormal basis may be returned. */
 a2_status a2_svd_split(a2_ctx* ctx, int Dl, int n1, int n2, int Dr, const double* x, int D_max,
                        double tol, double* P_out, double* SQ_out, int* rank_out,
                        double* discarded_out);
+
+/* LQ factorisation of Alg. 2 step 1 (W_i = L_i Q_i, and of the TT rounding) alone:
+ * M (device, rows x cols row-major, not modified) = L Q with Q (device, k x cols,
+ * k = min(rows, cols)) orthonormal rows and L (device, rows x k) lower trapezoidal with
+ * diag(L) >= 0; Householder reflections in FP64 on the device (this library's kernel).
+ * Synchronous.  Errors: A2_EINVAL on bad sizes / NULLs (rows of more than 25600 entries),
+ * A2_ECUDA if the kernel's bounded grid barrier gave up. */
+a2_status a2_lq(a2_ctx* ctx, int rows, int cols, const double* M, double* L, double* Q);
 
 /* Stages S1 and S4 of the H_eff chain alone: the tcgen05 tensor-core GEMM
  *   C[m][n] = sum_k A[m][k] B[n][k],  A: M x K (row stride lda), B: N x K (row
@@ -331,9 +347,21 @@ a2_status a2_svd_split(a2_ctx* ctx, int Dl, int n1, int n2, int Dr, const double
 a2_status a2_gemm_bf16(a2_ctx* ctx, int M, int N, int K, const void* A, long long lda,
                        const void* B, long long ldb, float* C, long long ldc, int splitk);
 
-/* Device-side error code of the bounded waits in the tensor-core kernels (0 = none);
- * reset != 0 clears it.  Synchronizes the context stream. */
+/* Device-side error code of the bounded waits (0 = none): the tensor-core kernels' mbarrier
+ * waits (codes 1-16), or 101 when a factorisation kernel's grid barrier gave up; reset != 0
+ * clears it.  Synchronizes the context stream. */
 a2_status a2_device_error(a2_ctx* ctx, int reset, int* code_out);
+
+/* Failure-path self-test of the bounded device waits (not paper content): runs one tile
+ * of the tcgen05 GEMM kernel whose producer role issues no copies, with a wait limit of
+ * 2^14 iterations, on the context stream, and waits for it.  The MMA role's first wait
+ * can never complete; it gives up, raises the device error word and the abort flag, the
+ * other roles leave, no copy or MMA is in flight and tensor memory is freed.  Returns
+ * A2_ETIMEOUT with *code_out (host) = the error code that was raised, after clearing the
+ * error word, and the context stays usable.  A2_EINVAL when the error word is already set
+ * before the call (read it with a2_device_error first), A2_ECUDA if the wait did not run
+ * out. */
+a2_status a2_selftest_timeout(a2_ctx* ctx, int* code_out);
 
 /* Live kernel timing with CUDA events on the context stream (not paper content;
  * used to report achieved throughput per kernel class).  op: 0 = disable,

@@ -103,6 +103,8 @@ def lib():
         "a2_gemm_bf16": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.c_longlong,
                          _P, ctypes.c_longlong, _P, ctypes.c_longlong, ctypes.c_int],
         "a2_device_error": [_P, ctypes.c_int, _I],
+        "a2_selftest_timeout": [_P, _I],
+        "a2_lq": [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P],
         "a2_profile": [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _D, _D,
                        _D],
         "a2_heff_apply_noalloc": [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P,
@@ -128,7 +130,8 @@ def exported_symbols():
             "a2_heff_apply", "a2_env_update", "a2_svd_split", "a2_gemm_bf16",
             "a2_device_error", "a2_profile", "a2_heff_apply_noalloc", "a2_mpo_fold_split",
             "a2_mpo_fold_info", "a2_mpo_set_fold", "a2_heff_create", "a2_heff_apply_op",
-            "a2_heff_destroy", "a2_energy_gradient", "a2_set_autotune"]
+            "a2_heff_destroy", "a2_energy_gradient", "a2_set_autotune", "a2_tt_save",
+            "a2_tt_load", "a2_selftest_timeout", "a2_lq"]
 
 
 def _dp(a):
@@ -413,6 +416,13 @@ def env_update(ctx, mpo, j, side, Hin, bra, ket, out, prec="fp64"):
                                   _ptr(Hin), _ptr(bra), _ptr(ket), _ptr(out)))
 
 
+def lq(ctx, M, L_out, Q_out):
+    """M = L Q on the device (a2_lq): CUDA float64 M (rows x cols), L_out (rows x k),
+    Q_out (k x cols), k = min(rows, cols)."""
+    rows, cols = M.shape
+    ctx.check(lib().a2_lq(ctx._h, rows, cols, _ptr(M), _ptr(L_out), _ptr(Q_out)))
+
+
 def svd_split(ctx, x, D_max, tol, P_out, SQ_out):
     Dl, n1, n2, Dr = x.shape
     r, disc = ctypes.c_int(), ctypes.c_double()
@@ -431,10 +441,23 @@ def gemm_bf16(ctx, A, B, C, K=None, splitk=1):
                                  C.shape[1], splitk))
 
 
+def last_error(ctx):
+    """Message of the last failure on the context (a2_last_error)."""
+    return lib().a2_last_error(ctx._h).decode()
+
+
 def device_error(ctx, reset=True):
     v = ctypes.c_int()
     ctx.check(lib().a2_device_error(ctx._h, int(reset), ctypes.byref(v)))
     return v.value
+
+
+def selftest_timeout(ctx):
+    """Failure-path self-test of the bounded device waits (a2_selftest_timeout): returns
+    (status, error code); the status is A2_ETIMEOUT (-6) when the wait ran out."""
+    code = ctypes.c_int(0)
+    st = lib().a2_selftest_timeout(ctx._h, ctypes.byref(code))
+    return st, code.value
 
 
 PROFILE_KINDS = ["tc_s1", "sparse_s2", "sparse_s3", "tc_s4", "heff_simt", "env", "lanczos",

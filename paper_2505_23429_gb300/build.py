@@ -1,6 +1,6 @@
 """Builds liba2dmrg.so (the C-ABI library) in-tree with nvcc for sm_103a.
 
-Translation units are compiled in parallel, then linked with cuSOLVER.
+Translation units are compiled in parallel, then linked (CUDA runtime only).
 Usage:  python -m paper_2505_23429_gb300.build  [--force]
 """
 import os
@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liba2dmrg.so")
-SOURCES = ["kernels.cu", "linalg.cu", "tc_gemm.cu", "a2dmrg.cu"]
+SOURCES = ["kernels.cu", "factor.cu", "tc_gemm.cu", "a2dmrg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--diag-suppress=177"]
@@ -49,7 +49,7 @@ def build(force=False, verbose=True):
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
         objs.append(obj)
     tmp = LIB + ".tmp"
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcusolver", "-lcublas"]
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -18,6 +18,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -1462,71 +1463,21 @@ LanczosResult davidson(a2_ctx* c, MV&& mv, const double* diag, double* x, long l
 }
 
 // ============================================================================= SVD step
-// M (rows x cols, row-major) = P Sigma Q via the left Gram matrix M M^T (FP64):
-// P = leading eigenvectors (left-orthonormal), SQ = P^T M.  Returns rank r and
-// the discarded 2-norm.  P (rows x r) and SQ (r x cols) row-major.
+// M (rows x cols, row-major) = P Sigma Q truncated (Alg. 1 step 2): P = the kept left
+// singular vectors (left-orthonormal, this library's bidiagonalisation SVD, factor.cu),
+// SQ = P^T M.  Returns the rank r and the discarded 2-norm.  P (rows x r) and SQ
+// (r x cols) row-major.
 int svd_split_dev(a2_ctx* c, const double* M, int rows, int cols, int D_max, double tol,
                   double* P, double* SQ, double* discarded, std::vector<double>* sv_out = nullptr) {
   cudaStream_t s = c->stream;
-  // Only the top min(D_max, rows) eigenpairs can be kept; the discarded weight of any
-  // rank is ||M||_F^2 minus the kept eigenvalues, so the rest need not be computed.
-  const int kmax = std::min(rows, cols);
-  const bool partial = (D_max < kmax) && (D_max * 4 <= rows * 3);
-  const int nev = partial ? D_max : kmax;   // eigenpairs computed (largest first)
-  // algorithmic flops: Gram, Householder tridiagonalisation, back-transformation of the
-  // nev eigenvectors, the product P^T M
+  const double mm = std::max(rows, cols), nn = std::min(rows, cols);
+  // algorithmic flops: bidiagonalisation, the back-transformation of the kept vectors
+  // (bounded by nn of them), the product P^T M
   ProfScope ps(PK_SVD, s,
-               2.0 * rows * rows * (double)cols + 4.0 / 3.0 * rows * rows * (double)rows +
-                   2.0 * rows * rows * (double)nev + 2.0 * nev * (double)rows * cols,
-               8.0 * (2.0 * rows * cols + 2.0 * rows * rows));
-  c->gram.ensure(sizeof(double) * ((size_t)rows * rows + rows), s);
-  double* G = c->gram.as<double>();
-  double* w = G + (size_t)rows * rows;
-  {
-    SimtGemm<double, double> g;
-    g.M = rows; g.N = rows; g.K = cols;
-    g.A = M; g.sam = cols; g.sak = 1;
-    g.B = M; g.sbn = cols; g.sbk = 1;
-    g.C = G; g.scm = rows; g.scn = 1;
-    simt_gemm(g, s);
-  }
-  std::vector<double> sv(nev);              // singular values, descending
-  int col_of_first = rows - 1;              // column of the largest eigenvector in G
-  double rest = 0.0;                        // weight beyond the computed eigenpairs
-  if (partial) {
-    const double total = dot_dev(c, M, M, (long long)rows * cols, 7);
-    c->solver.syevd_top(G, rows, nev, w, s);
-    std::vector<double> lam(nev);
-    A2_CUDA(cudaMemcpyAsync(lam.data(), w, sizeof(double) * nev, cudaMemcpyDeviceToHost, s));
-    A2_CUDA(cudaStreamSynchronize(s));
-    double kept = 0.0;
-    for (int i = 0; i < nev; ++i) {
-      sv[i] = std::sqrt(std::max(lam[nev - 1 - i], 0.0));
-      kept += sv[i] * sv[i];
-    }
-    rest = std::max(total - kept, 0.0);
-    col_of_first = nev - 1;
-  } else {
-    c->solver.syevd(G, rows, w, s);
-    std::vector<double> lam(rows);
-    A2_CUDA(cudaMemcpyAsync(lam.data(), w, sizeof(double) * rows, cudaMemcpyDeviceToHost, s));
-    A2_CUDA(cudaStreamSynchronize(s));
-    for (int i = 0; i < nev; ++i) sv[i] = std::sqrt(std::max(lam[rows - 1 - i], 0.0));
-  }
-  // tail[r] = sum_{k >= r} sigma_k^2 (computed eigenvalues summed from the small end)
-  std::vector<double> tail(nev + 1, 0.0);
-  tail[nev] = rest;
-  for (int i = nev - 1; i >= 0; --i) tail[i] = tail[i + 1] + sv[i] * sv[i];
-  const double total = tail[0];
-  int r = nev;
-  const double thr = tol * tol * total;
-  for (int cand = 1; cand <= nev; ++cand)
-    if (tail[cand] <= thr) { r = cand; break; }
-  r = std::max(1, std::min(r, D_max));
-  if (discarded) *discarded = std::sqrt(std::max(tail[r], 0.0));
-  if (sv_out) *sv_out = sv;
-  // P[i][c] = eigenvector column (col_of_first - c) of G (column-major, leading dim rows)
-  cols_rev_to_rows(G, rows, rows, col_of_first, r, P, s);
+               4.0 * mm * nn * nn - 4.0 / 3.0 * nn * nn * nn + 4.0 * (double)rows * nn * nn +
+                   2.0 * nn * (double)rows * cols,
+               8.0 * (2.0 * rows * cols + 2.0 * rows * nn));
+  const int r = svd_trunc(M, rows, cols, D_max, tol, P, discarded, sv_out, c->solver.fw, s);
   {  // SQ = P^T M : (r x cols)
     SimtGemm<double, double> g;
     g.M = r; g.N = cols; g.K = rows;
@@ -2323,6 +2274,8 @@ struct Sweeper {
       }
       round_into_tt(X, xd);
     }
+    // round_into_tt ended with a stream synchronisation: the error word is current
+    if (factor_error_flag(true)) throw CudaError("a factorisation kernel's grid barrier gave up");
     if (rep) {
       rep->energy_in = A[0] / S[0];
       rep->lambda_coarse = lam;
@@ -2562,6 +2515,44 @@ a2_status guarded(a2_ctx* c, F&& f) {
   }
 }
 
+// Registry of the live handles: a context owns the TT / MPO / H_eff handles made on it, so
+// destroying it destroys what is left of them, and a destroy call on a handle that is no
+// longer live is ignored (A2_EINVAL) instead of touching freed memory.
+enum HandleKind { HK_CTX = 0, HK_TT = 1, HK_MPO = 2, HK_HEFF = 3 };
+struct HandleInfo {
+  int kind;
+  a2_ctx* owner;
+};
+std::mutex g_handle_mu;
+std::map<const void*, HandleInfo> g_handles;
+
+void handle_add(const void* h, int kind, a2_ctx* owner) {
+  std::lock_guard<std::mutex> g(g_handle_mu);
+  g_handles[h] = HandleInfo{kind, owner};
+}
+// Removes h if it is live with the given kind; false otherwise.
+bool handle_take(const void* h, int kind) {
+  std::lock_guard<std::mutex> g(g_handle_mu);
+  auto it = g_handles.find(h);
+  if (it == g_handles.end() || it->second.kind != kind) return false;
+  g_handles.erase(it);
+  return true;
+}
+// Removes and returns every live handle owned by c (ctx itself excluded).
+std::vector<std::pair<const void*, int>> handles_owned_by(a2_ctx* c) {
+  std::lock_guard<std::mutex> g(g_handle_mu);
+  std::vector<std::pair<const void*, int>> out;
+  for (auto it = g_handles.begin(); it != g_handles.end();) {
+    if (it->second.owner == c && it->second.kind != HK_CTX) {
+      out.push_back({it->first, it->second.kind});
+      it = g_handles.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  return out;
+}
+
 uint64_t splitmix_next(uint64_t& state) {
   state += 0x9E3779B97F4A7C15ull;
   uint64_t z = state;
@@ -2617,6 +2608,9 @@ void core_gradient(a2_ctx* c, const double* HL, int Dl, int Rl, const double* U,
 }  // namespace
 
 // ============================================================================= C ABI
+// Deletes the TT / MPO / H_eff handles still registered to c (defined after a2_heff).
+void destroy_owned(a2_ctx* c);
+
 extern "C" {
 
 a2_status a2_ctx_create(int device, void* cuda_stream, a2_ctx** out) {
@@ -2648,12 +2642,16 @@ a2_status a2_ctx_create(int device, void* cuda_stream, a2_ctx** out) {
     delete c;
     return st;
   }
+  handle_add(c, HK_CTX, c);
   *out = c;
   return A2_OK;
 }
 
 a2_status a2_ctx_destroy(a2_ctx* c) {
-  if (!c) return A2_EINVAL;
+  if (!c || !handle_take(c, HK_CTX)) return A2_EINVAL;
+  // handles still attached to the context go first (their buffers use its stream)
+  cudaStreamSynchronize(c->stream);
+  destroy_owned(c);
   for (a2_ctx* l : c->lanes) {
     destroy_ctx_resources(l);
     if (l->hi) {
@@ -2725,6 +2723,7 @@ a2_status a2_tt_create(a2_ctx* c, int L, const int* phys, const int* bonds, uint
     A2_CUDA(cudaStreamSynchronize(c->stream));
   });
   if (st != A2_OK) { delete t; return st; }
+  handle_add(t, HK_TT, c);
   *out = t;
   return A2_OK;
 }
@@ -2839,6 +2838,7 @@ a2_status a2_tt_load(a2_ctx* c, const char* path, a2_tt** out) {
     delete t;
     return st;
   }
+  handle_add(t, HK_TT, c);
   *out = t;
   return A2_OK;
 }
@@ -2857,7 +2857,7 @@ a2_status a2_tt_left_orthogonalize(a2_tt* t, double* norm_out) {
 }
 
 a2_status a2_tt_destroy(a2_tt* t) {
-  if (!t) return A2_EINVAL;
+  if (!t || !handle_take(t, HK_TT)) return A2_EINVAL;
   cudaStreamSynchronize(t->ctx->stream);
   delete t;
   return A2_OK;
@@ -2884,6 +2884,7 @@ a2_status a2_mpo_load(a2_ctx* c, int L, const int* phys, const int* R, const dou
     A2_CUDA(cudaStreamSynchronize(c->stream));
   });
   if (st != A2_OK) { delete m; return st; }
+  handle_add(m, HK_MPO, c);
   *out = m;
   return A2_OK;
 }
@@ -2928,7 +2929,7 @@ a2_status a2_mpo_set_fold(a2_mpo* m, int enable) {
 }
 
 a2_status a2_mpo_destroy(a2_mpo* m) {
-  if (!m) return A2_EINVAL;
+  if (!m || !handle_take(m, HK_MPO)) return A2_EINVAL;
   cudaStreamSynchronize(m->ctx->stream);
   delete m;
   return A2_OK;
@@ -3062,6 +3063,7 @@ a2_status a2_heff_create(a2_ctx* c, const a2_mpo* m, int k, a2_precision prec, i
     A2_CUDA(cudaStreamSynchronize(s));
   });
   if (st != A2_OK) { delete h; return st; }
+  handle_add(h, HK_HEFF, c);
   *out = h;
   return A2_OK;
 }
@@ -3097,7 +3099,7 @@ a2_status a2_heff_apply_op(a2_heff* h, const double* x, double* y) {
 }
 
 a2_status a2_heff_destroy(a2_heff* h) {
-  if (!h) return A2_EINVAL;
+  if (!h || !handle_take(h, HK_HEFF)) return A2_EINVAL;
   cudaStreamSynchronize(h->ctx->stream);
   delete h;
   return A2_OK;
@@ -3286,8 +3288,38 @@ a2_status a2_device_error(a2_ctx* c, int reset, int* code_out) {
   if (!c || !code_out) return A2_EINVAL;
   return guarded(c, [&] {
     A2_CUDA(cudaStreamSynchronize(c->stream));
+    const int f = factor_error_flag(reset != 0);
     *code_out = tc_error_flag(reset != 0);
+    if (!*code_out && f) *code_out = 100 + f;
   });
+}
+
+a2_status a2_lq(a2_ctx* c, int rows, int cols, const double* M, double* L, double* Q) {
+  if (!c) return A2_EINVAL;
+  return guarded(c, [&] {
+    A2_REQUIRE(rows >= 1 && cols >= 1 && M && L && Q, "a2_lq: bad arguments");
+    c->solver.lq(M, rows, cols, L, Q, c->stream);
+    A2_CUDA(cudaStreamSynchronize(c->stream));
+    if (factor_error_flag(true)) throw CudaError("a2_lq: a bounded grid barrier gave up");
+  });
+}
+
+a2_status a2_selftest_timeout(a2_ctx* c, int* code_out) {
+  if (!c || !code_out) return A2_EINVAL;
+  int code = 0;
+  a2_status st = guarded(c, [&] {
+    A2_REQUIRE(tc_available(), "the tcgen05 path is not built");
+    A2_CUDA(cudaSetDevice(c->device));
+    A2_CUDA(cudaStreamSynchronize(c->stream));
+    A2_REQUIRE(tc_error_flag(false) == 0,
+               "a2_selftest_timeout: the device error word is already set");
+    code = tc_selftest_timeout(c->stream);
+  });
+  if (st != A2_OK) return st;
+  *code_out = code;
+  if (code == 0) return fail(c, A2_ECUDA, "a2_selftest_timeout: the wait did not run out");
+  return fail(c, A2_ETIMEOUT, "a bounded device wait gave up (error code " +
+                                  std::to_string(code) + ", self-test)");
 }
 
 a2_status a2_profile(a2_ctx* c, int op, int kind, long long* launches, double* ms,
@@ -3321,6 +3353,21 @@ a2_status a2_svd_split(a2_ctx* c, int Dl, int n1, int n2, int Dr, const double* 
 }
 
 }  // extern "C"
+
+void destroy_owned(a2_ctx* c) {
+  std::vector<a2_heff*> hs;
+  std::vector<a2_tt*> ts;
+  std::vector<a2_mpo*> ms;
+  for (auto& hk : handles_owned_by(c)) {
+    void* p = const_cast<void*>(hk.first);
+    if (hk.second == HK_HEFF) hs.push_back(static_cast<a2_heff*>(p));
+    else if (hk.second == HK_TT) ts.push_back(static_cast<a2_tt*>(p));
+    else if (hk.second == HK_MPO) ms.push_back(static_cast<a2_mpo*>(p));
+  }
+  for (auto* h : hs) delete h;     // an H_eff handle refers to its MPO
+  for (auto* t : ts) delete t;
+  for (auto* m : ms) delete m;
+}
 
 // ============================================================================= allocation-free H_eff
 // A second way to apply H_eff for callers that must not allocate device memory

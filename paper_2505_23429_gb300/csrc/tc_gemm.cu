@@ -57,8 +57,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait: returns false (and records `code`) if the phase never completes.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int code) {
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int code,
+                                          uint32_t limit = kWaitLimit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if (it > 64) __nanosleep(64);
   }
@@ -192,6 +193,9 @@ struct TcArgs {
   int pa[kMaxPairs], pb[kMaxPairs];   // A / B plane of each pair
   int tma_store;           // 1: epilogue through shared memory + TMA bulk tensor store
   long long split_ld;      // > 0: K split sp stores its own FP32 tile at C + sp * split_ld
+  uint32_t wait_limit;     // iterations of every bounded wait (kWaitLimit)
+  int no_loads;            // self-test only: the producer issues no copies, so the first
+                           // wait of the MMA role runs out (see tc_selftest_timeout)
 };
 
 // Up to three BF16 planes per operand (a value split into high, middle and low parts).
@@ -274,8 +278,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 // Bounded wait that also gives up early once another role has raised the abort flag.
 __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, int code,
-                                                   const int* abort_flag) {
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+                                                   const int* abort_flag,
+                                                   uint32_t limit = kWaitLimit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255) == 255 && *(volatile const int*)abort_flag) return false;
     if (it > 64) __nanosleep(64);
@@ -348,7 +353,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
   };
 
   if (warp == 0) {
-    if (lane == 0) {
+    if (lane == 0 && !args.no_loads) {
       // ---------------- producer
       uint32_t g = 0, issued = 0;
       for (int u = blockIdx.x; u < nunits && !*(volatile int*)&S.abort_flag; u += gridDim.x) {
@@ -361,7 +366,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
           const int s = g % STAGES;
           const uint32_t round = g / STAGES;
           if (round > 0 &&
-              !mbar_wait_or_abort(&S.empty[s], (round - 1) & 1, 1, &S.abort_flag)) {
+              !mbar_wait_or_abort(&S.empty[s], (round - 1) & 1, 1, &S.abort_flag, args.wait_limit)) {
             S.abort_flag = 1;
             break;
           }
@@ -385,7 +390,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
       // on abort: wait (bounded) for the copies still in flight before leaving
       if (*(volatile int*)&S.abort_flag) {
         for (uint32_t j = issued > (uint32_t)STAGES ? issued - STAGES : 0; j < issued; ++j)
-          mbar_wait(&S.full[j % STAGES], (j / STAGES) & 1, 2);
+          mbar_wait(&S.full[j % STAGES], (j / STAGES) & 1, 2, args.wait_limit);
       }
     }
   } else if (warp == 1) {
@@ -403,7 +408,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
         for (int st0 = 0; st0 < steps; st0 += cs, ++ch) {
           const uint32_t buf = ch & 1, use = ch >> 1;
           if (use > 0 &&
-              !mbar_wait_or_abort(&S.acc_empty[buf], (use - 1) & 1, 5, &S.abort_flag)) {
+              !mbar_wait_or_abort(&S.acc_empty[buf], (use - 1) & 1, 5, &S.abort_flag, args.wait_limit)) {
             ok = false;
             break;
           }
@@ -412,7 +417,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
           const int st1 = min(steps, st0 + cs);
           for (int kb = st0; kb < st1; ++kb, ++g) {
             const int s = g % STAGES;
-            if (!mbar_wait_or_abort(&S.full[s], (g / STAGES) & 1, 3, &S.abort_flag)) {
+            if (!mbar_wait_or_abort(&S.full[s], (g / STAGES) & 1, 3, &S.abort_flag, args.wait_limit)) {
               ok = false;
               break;
             }
@@ -433,7 +438,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
       if (!ok) S.abort_flag = 1;
       if (*(volatile int*)&S.abort_flag && issued_any) {
         mma_commit(&S.drain);      // wait (bounded) for the MMAs still in flight
-        mbar_wait(&S.drain, 0, 6);
+        mbar_wait(&S.drain, 0, 6, args.wait_limit);
       }
     }
   } else {
@@ -448,7 +453,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
     // wait for accumulator chunk `ch` and return its TMEM base
     auto acquire = [&](uint32_t& tl) -> bool {
       const uint32_t buf = ch & 1, use = ch >> 1;
-      if (!mbar_wait_or_abort(&S.acc_full[buf], use & 1, 4, &S.abort_flag)) return false;
+      if (!mbar_wait_or_abort(&S.acc_full[buf], use & 1, 4, &S.abort_flag, args.wait_limit)) return false;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       tl = tmem + buf * BN + (uint32_t)colbase + ((uint32_t)(q * 32) << 16);
       return true;
@@ -739,6 +744,8 @@ int launch(const __nv_bfloat16* const* A, long long lda, const __nv_bfloat16* co
   }
   args.splits = splitk;
   args.split_ld = split_ld;
+  args.wait_limit = kWaitLimit;
+  args.no_loads = 0;
   A2_REQUIRE(split_ld == 0 || (out_kind == OUT_F32 && !PROMOTE), "split tiles: FP32 stores");
   // TMA store epilogue when C's base and row stride allow it
   {
@@ -1115,6 +1122,52 @@ int tc_error_flag(bool reset) {
     A2_CUDA(cudaMemcpyToSymbol(tc::g_tc_error, &z, sizeof(int)));
   }
   return v;
+}
+
+int tc_selftest_timeout(cudaStream_t s) {
+  // One 128 x 128 x 128 unit of the BF16 GEMM kernel whose producer issues no copies: the
+  // MMA role's first wait (stage 0 full) can never complete, gives up after 2^14
+  // iterations, raises the error word and the abort flag; the epilogue roles see the flag
+  // and leave; no copy or MMA is ever in flight and TMEM is freed as on any abort.
+  constexpr int n = 128;
+  DevBuf a, b, c;
+  a.ensure(sizeof(__nv_bfloat16) * n * n, s);
+  b.ensure(sizeof(__nv_bfloat16) * n * n, s);
+  c.ensure(sizeof(float) * n * n, s);
+  fill_zero(a.p, sizeof(__nv_bfloat16) * n * n, s);
+  fill_zero(b.p, sizeof(__nv_bfloat16) * n * n, s);
+  tc::TcMaps maps;
+  for (int i = 0; i < tc::kMaxPlanes; ++i) {
+    maps.a[i] = tc::make_map(a.as<__nv_bfloat16>(), n, n, n, tc::BM);
+    maps.b[i] = tc::make_map(b.as<__nv_bfloat16>(), n, n, n, 128);
+  }
+  for (int i = 0; i < 3; ++i) {
+    maps.a2[i] = maps.a[i];
+    maps.b2[i] = maps.b[i];
+  }
+  maps.c = maps.a[0];
+  tc::TcArgs args{};
+  args.M = args.N = args.K = n;
+  args.nk1 = n / tc::BK;
+  args.nk2 = 0;
+  args.nbc2 = args.n12 = 1;
+  args.kblocks_per_split = args.nk1;
+  args.splits = 1;
+  args.C = c.p;
+  args.ldc = n;
+  args.out_kind = tc::OUT_F32;
+  args.npairs = 1;
+  args.tma_store = 0;
+  args.split_ld = 0;
+  args.wait_limit = 1u << 14;
+  args.no_loads = 1;
+  const size_t smem = sizeof(tc::TcSmem<128, 6, 4, 2>) + 1024;
+  A2_CUDA(cudaFuncSetAttribute(tc::tc_gemm_kernel<128, 6, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  tc::tc_gemm_kernel<128, 6, false><<<1, tc::tc_threads(false), smem, s>>>(maps, args);
+  A2_CHECK_LAUNCH();
+  A2_CUDA(cudaStreamSynchronize(s));
+  return tc_error_flag(true);
 }
 
 void tc_gemm_bf16(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B, long long ldb,

@@ -9,6 +9,9 @@ namespace a2 {
 bool tc_available();
 // Device error flag of the tcgen05 kernels (nonzero: a bounded wait gave up).
 int tc_error_flag(bool reset);
+// Runs one GEMM unit whose producer issues no copies, so that a bounded wait runs out;
+// returns the device error code it raised (and clears it).  Synchronous.
+int tc_selftest_timeout(cudaStream_t s);
 
 // C[m][n] (=|+=atomic) sum_k A[m][k] B[n][k]; A: M x K (row stride lda), B: N x K
 // (row stride ldb), both BF16 with 16-byte aligned bases and row strides that are
@@ -82,8 +85,9 @@ void ozaki_split(const double* X, long long sr, long long sk, int rows, int K, _
                  long long ldp, long long plane, cudaStream_t s);
 // C (FP64, M x N, row stride ldc) = sum_k A[m][k] B[n][k] to FP64 accuracy from the split
 // planes of A (row stride lda, plane stride aplane) and B; slab is FP32 scratch for the
-// level tiles of every K split (grown as needed).  With Cdf set the result is written as
-// an FP32 pair instead (Cdf + r*ldc + c and the same at + df_plane), C unused.
+// double-float partial sums of the K splits, when the product is split (grown as
+// needed).  With Cdf set the result is written as an FP32 pair instead (Cdf + r*ldc + c
+// and the same at + df_plane), C unused.
 void tc_gemm_f64emu(const __nv_bfloat16* A, long long lda, long long aplane,
                     const __nv_bfloat16* B, long long ldb, long long bplane, int M, int N, int K,
                     double* C, long long ldc, DevBuf& slab, cudaStream_t s,

@@ -26,10 +26,22 @@ def test_reference_arm_json_line():
                 "cpu_baseline", "e2e"):
         assert key in d, key
     assert d["impl"] == "reference"
-    assert d["value"] > 0 and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["higher_is_better"] is False and d["unit"] == "s"
     assert d["config"]["workload"] == "chem_L16_D256"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    # the timed region is the oracle work actually done, not the extrapolated value
+    assert d["ms_per_step"] * d["steps"] / 1e3 <= d["timed_wall_s"] * 1.01 + 1e-3
+
+
+def test_stopping_rule():
+    import bench
+    assert not bench.rule_met([-1.0])
+    assert not bench.rule_met([-21.0, -21.1])
+    assert bench.rule_met([-21.1, -21.1 - 1e-5])            # 4.7e-7 relative
+    assert not bench.rule_met([-21.1, -21.1 - 3e-5])        # 1.4e-6 relative
+    assert bench.rule_met([-5.0, -21.1, -21.1 + 1e-6])      # only the last two count
 
 
 def test_roofline_class_mapping():

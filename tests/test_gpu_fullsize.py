@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from oracle.env import env_left_update_entry, heff_apply_entry
-from synthetic import chemistry_integrals, chemistry_mpo
+from synthetic import chemistry_integrals, chemistry_mpo, random_tt_cores
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -110,3 +110,31 @@ def test_svd_split_full_size(ctx):
     assert np.abs(Ph.T @ Ph - np.eye(r)).max() < 1e-12
     assert np.allclose(np.linalg.svd(SQh, compute_uv=False), s[:r], rtol=1e-10, atol=1e-13)
     assert abs(np.linalg.norm(M - Ph @ SQh) - disc) < 1e-10 * np.linalg.norm(s)
+
+
+def test_c2_iterate_energy_matches_oracle_rayleigh_quotient(ctx):
+    """The L = 16, D = 256, P = 4 workload itself: six global iterations of the BF16
+    default path from the seeded TT (the middle bonds reach the cap of 256); the
+    library's FP64-class energy of the iterate (a2_energy with Ozaki-emulated
+    environments), and the energy_in the next iteration reports, equal the oracle's FP64
+    Rayleigh quotient <x, A x> / <x, x> of the same TT contracted on the host."""
+    from oracle.env import sandwich
+    from oracle.tt import tt_inner
+    from synthetic import get_config
+    cfg = get_config("chem_L16_D256")
+    h, eri = chemistry_integrals(cfg["L"], cfg["seed_int"])
+    m = chemistry_mpo(h, eri)
+    mpo = a2.MPO(ctx, m)
+    t = a2.TT.from_cores(ctx, random_tt_cores([4] * cfg["L"], cfg["r0"], cfg["seed_tt"]))
+    t.left_orthogonalize()
+    kw = dict(partition=cfg["partition"], D_max=cfg["D"], prec="bf16", svd_tol=1e-6,
+              eig_tol=1e-6, coarse_eps=1e-10, max_restarts=50, sequential=True)
+    for _ in range(6):
+        a2.additive_sweep(ctx, t, mpo, cfg["P"], **kw)
+    cores = t.cores()
+    assert max(c.shape[2] for c in cores) == cfg["D"]
+    E_gpu, _ = a2.energy(ctx, t, mpo, "f64emu")
+    E_or = sandwich(cores, m, cores) / tt_inner(cores, cores)
+    assert abs(E_gpu - E_or) < 1e-10 * abs(E_or)
+    rep = a2.additive_sweep(ctx, t, mpo, cfg["P"], **kw)
+    assert abs(rep["energy_in"] - E_or) < 1e-10 * abs(E_or)
