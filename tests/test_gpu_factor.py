@@ -140,3 +140,19 @@ def test_svd_edge_cases(ctx):
     assert np.abs(P @ SQ - M).max() < 1e-13 * np.abs(M).max()
     r, disc, P, SQ = _svd(ctx, np.array([[3.0]]), 1, 0.0)
     assert r == 1 and abs(abs(P[0, 0]) - 1.0) < 1e-15 and abs(abs(SQ[0, 0]) - 3.0) < 1e-15
+
+
+def test_svd_large_global_memory_path(ctx):
+    """2048 x 1800: too large for the shared-memory-resident bidiagonalisation, so the
+    global-memory kernel runs; kept rank, discarded weight and truncated product against
+    LAPACK."""
+    from oracle.tt import svd_split as osvd
+    rows, cols, D = 2048, 1800, 200
+    sig = 1.0 / (1.0 + np.arange(cols)) ** 0.8
+    M = _spectrum_matrix(rows, cols, sig, 21)
+    r, disc, P, SQ = _svd(ctx, M, D, 1e-8)
+    P0, s0, Q0, d0 = osvd(M, D, 1e-8)
+    assert r == len(s0) == D
+    assert abs(disc - d0) < 1e-10 * np.linalg.norm(sig)
+    assert np.abs(P.T @ P - np.eye(r)).max() < 1e-12
+    assert np.linalg.norm(P @ SQ - (P0 * s0) @ Q0) < 1e-10 * np.linalg.norm(sig)
