@@ -533,7 +533,7 @@ def main():
     shares = {k: round(v["ms"] / total_ms, 4) for k, v in prof.items() if v["ms"] > 0}
     ratio = DRAM_TRAFFIC_RATIO.get(dom)
     traffic = ratio * d["bytes"] / max(d["launches"], 1) if ratio else None
-    bound, unit, peak, achieved = class_roofline(dom, d, peaks, args.prec)
+    bound, r_unit, peak, achieved = class_roofline(dom, d, peaks, args.prec)
     per_launch = d["ms"] / max(d["launches"], 1)
     rooflines = {}
     for k, v in prof.items():
@@ -573,7 +573,7 @@ def main():
                             l2="working set >> 129 MB L2 (no flush)"),
                 rule_reached=reached, energy_final=energies[-1] if energies else None,
                 energies=[round(e, 10) for e in energies],
-                roofline=dict(kernel=dom, bound=bound, achieved=achieved, peak=peak, unit=unit,
+                roofline=dict(kernel=dom, bound=bound, achieved=achieved, peak=peak, unit=r_unit,
                               frac=achieved / peak, traffic=traffic,
                               traffic_source=(None if ratio is None else
                                               "ncu DRAM bytes / algorithmic bytes of the same "
@@ -590,6 +590,11 @@ def main():
                                         if v["ms"] > 0 else None)
                                 for k, v in prof.items()},
                 heff_matvec=mv, clocks=clk, wall_s=wall,
+                op_counts=dict(iterations=len(reps),
+                               krylov_per_bond=[round(float(v) / max(len(reps), 1), 1) for v in
+                                                np.sum([r["krylov"] for r in reps], axis=0)],
+                               env_per_iteration=round(prof["env"]["launches"] / max(steps, 1), 1),
+                               svd_per_iteration=round(prof["svd"]["launches"] / max(steps, 1), 1)),
                 gpu_launches=int(launches))
     if not args.no_e2e:
         t0 = time.perf_counter()

@@ -324,9 +324,14 @@ a2_status a2_env_update(a2_ctx* ctx, const a2_mpo* mpo, int j, int side, a2_prec
  * SQ_out [r][n2][Dr] (device, capacity min(Dl n1, n2 Dr) columns/rows);
  * rank_out, discarded_out (host).  Computed by this library's FP64 kernels: Householder
  * bidiagonalisation, all singular values by bisection of the Golub-Kahan tridiagonal
- * (absolute accuracy ~1e-16 ||x||, no Gram matrix), the kept left vectors by inverse
- * iteration, re-orthonormalised and transformed back; SQ = P^T x.  Within an exactly
- * degenerate multiplet any orthonormal basis may be returned. */
+ * (FP32 brackets refined in FP64 to a relative width 2^-46; no Gram matrix, so small
+ * singular values keep their relative accuracy), the kept left vectors by inverse
+ * iteration, re-orthonormalised (block Gram-Schmidt with CholeskyQR2 panels) and
+ * transformed back; SQ = P^T x.  Within an exactly degenerate multiplet any orthonormal
+ * basis may be returned; FP64 atomic sums in the bidiagonalisation may change the last
+ * bits of the result from run to run.  Errors: A2_EINVAL on bad sizes / NULLs (more than
+ * 12800 rows Dl n1 or, for the smaller of the two dimensions, more than 2400), A2_ECUDA
+ * on CUDA failure (including a bounded grid barrier that gave up). */
 a2_status a2_svd_split(a2_ctx* ctx, int Dl, int n1, int n2, int Dr, const double* x, int D_max,
                        double tol, double* P_out, double* SQ_out, int* rank_out,
                        double* discarded_out);

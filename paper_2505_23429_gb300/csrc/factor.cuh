@@ -22,12 +22,13 @@ int hh_lq(const double* M, int rows, int cols, double* L, double* Q, FactorWork&
 // Truncated SVD step of Alg. 1 (step 2) for a row-major (rows x cols) matrix M, in FP64:
 // Golub-Kahan bidiagonalisation of M (or of M^T when rows < cols) by Householder
 // reflections, all singular values by bisection of the Golub-Kahan tridiagonal (no Gram
-// matrix, so small singular values keep their absolute accuracy ~eps ||M||), the kept
-// left singular vectors by inverse iteration on the same tridiagonal, re-orthonormalised
-// and transformed back.  Keeps the smallest r <= D_max with discarded 2-norm
+// matrix; FP32 brackets refined in FP64 to a relative width 2^-46, so small singular
+// values keep their relative accuracy), the kept left singular vectors by inverse
+// iteration on the same tridiagonal, re-orthonormalised (block Gram-Schmidt, CholeskyQR2
+// panels) and transformed back.  Keeps the smallest r <= D_max with discarded 2-norm
 // <= tol * ||sigma|| (r >= 1); P (rows x r, row-major) receives the left singular
 // vectors, *discarded the discarded 2-norm, sv_out (optional) all singular values in
-// descending order.  Returns r.
+// descending order.  rows <= 12800, min(rows, cols) <= 2400.  Returns r.
 int svd_trunc(const double* M, int rows, int cols, int D_max, double tol, double* P,
               double* discarded, std::vector<double>* sv_out, FactorWork& w, cudaStream_t s);
 

@@ -156,3 +156,20 @@ def test_svd_large_global_memory_path(ctx):
     assert abs(disc - d0) < 1e-10 * np.linalg.norm(sig)
     assert np.abs(P.T @ P - np.eye(r)).max() < 1e-12
     assert np.linalg.norm(P @ SQ - (P0 * s0) @ Q0) < 1e-10 * np.linalg.norm(sig)
+
+
+def test_svd_tall_in_place_back_transformation(ctx):
+    """3300 x 40: more rows than the back-transformation keeps in shared memory, so the
+    kept columns are updated in place in device memory; rank, discarded weight and
+    truncated product against LAPACK.  More than 12800 rows is refused."""
+    from oracle.tt import svd_split as osvd
+    sig = np.logspace(0, -9, 40)
+    M = _spectrum_matrix(3300, 40, sig, 33)
+    r, disc, P, SQ = _svd(ctx, M, 30, 1e-7)
+    P0, s0, Q0, d0 = osvd(M, 30, 1e-7)
+    assert r == len(s0)
+    assert abs(disc - d0) < 1e-12
+    assert np.abs(P.T @ P - np.eye(r)).max() < 1e-12
+    assert np.linalg.norm(P @ SQ - (P0 * s0) @ Q0) < 1e-12
+    with pytest.raises(a2.A2Error):
+        _svd(ctx, np.ones((12801, 2)), 2, 1e-8)
