@@ -48,8 +48,9 @@ RULE_TOL = 1e-6   # relative energy change between successive iterations (Sec. 4
 # iterations the rule needed: they scale the reference arm's oracle samples, which cannot
 # run the workload itself.
 REF_COUNTS = dict(iterations=64,
-                  krylov=[12, 14, 16, 18, 22, 22, 24, 26, 27, 20, 19, 10, 17, 3, 3],
-                  env=151, svd=30)
+                  krylov=[11.4, 15.5, 16.2, 19.8, 28.4, 26.6, 29.7, 38.2, 35.9, 21.4, 16.4, 13.4,
+                          16.1, 4.6, 3.1],
+                  env=167, svd=30)
 # classes reported by time share only (latency-bound FP64 factorisations)
 LATENCY_BOUND = ("svd", "lq")
 # DRAM traffic / algorithmic bytes of a kernel class, from its ncu capture at D = 128;
@@ -90,6 +91,9 @@ def parse():
                    help="skip the H_eff matvec comparison (e.g. under a profiler)")
     p.add_argument("--profile-matvec", action="store_true",
                    help="small case for ncu: H_eff applications at the middle bond only")
+    p.add_argument("--profile-svd", action="store_true",
+                   help="time the truncated SVD alone: the (D n) x (n D) two-site matrix of "
+                        "the workload's middle bond, singular values k^-0.75, --reps calls")
     p.add_argument("--D", type=int, default=128, help="bond dimension of --profile-matvec")
     p.add_argument("--bond", type=int, default=None,
                    help="bond of --profile-matvec (default: the one left of the middle)")
@@ -292,6 +296,41 @@ def profile_matvec(args):
                           ms_per_application=classes, error_flag=a2.device_error(ctx))))
 
 
+def profile_svd(args):
+    """The truncated SVD of the two-site split alone, on the workload's middle-bond shape
+    (D n) x (n D) with a seeded spectrum sigma_k = (1 + k)^-0.75 (the slowly decaying
+    Schmidt spectrum of the chemistry iterates), kept rank D, svd_tol 1e-6: --reps calls
+    after one warm-up call, each timed with CUDA events on the library's stream."""
+    import torch
+    import paper_2505_23429_gb300 as a2
+    cfg, _, _ = workload(args.config)
+    D, n = cfg["D"], cfg["n"]
+    N = D * n
+    rng = np.random.default_rng(7)
+    U, _ = np.linalg.qr(rng.standard_normal((N, N)))
+    V, _ = np.linalg.qr(rng.standard_normal((N, N)))
+    M = (U * (1.0 / (1.0 + np.arange(N)) ** 0.75)) @ V.T
+    stream = torch.cuda.Stream()
+    ctx = a2.Context(0, stream.cuda_stream)
+    x = torch.from_numpy(M.reshape(D, n, n, D)).cuda()
+    P = torch.zeros(N * N, dtype=torch.float64, device="cuda")
+    SQ = torch.zeros(N * N, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    a2.svd_split(ctx, x, D, 1e-6, P, SQ)
+    ctx.synchronize()
+    times = []
+    for _ in range(args.reps):
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        r, disc = a2.svd_split(ctx, x, D, 1e-6, P, SQ)
+        t1.record(stream)
+        t1.synchronize()
+        times.append(t0.elapsed_time(t1))
+    print(json.dumps(dict(profile_svd=True, shape=[N, N], rank=r, discarded=disc,
+                          ms=[round(t, 3) for t in times], ms_min=round(min(times), 3),
+                          error_flag=a2.device_error(ctx))))
+
+
 def class_roofline(name, d, peaks, prec):
     """(bound, unit, peak, achieved) of one kernel class from its CUDA-event totals and
     the algorithmic flops / bytes the library counts for it."""
@@ -457,6 +496,9 @@ def reference_arm(args):
 
 def main():
     args = parse()
+    if args.profile_svd:
+        profile_svd(args)
+        return
     if args.profile_matvec:
         profile_matvec(args)
         return

@@ -1478,7 +1478,17 @@ int svd_split_dev(a2_ctx* c, const double* M, int rows, int cols, int D_max, dou
                    2.0 * nn * (double)rows * cols,
                8.0 * (2.0 * rows * cols + 2.0 * rows * nn));
   const int r = svd_trunc(M, rows, cols, D_max, tol, P, discarded, sv_out, c->solver.fw, s);
-  {  // SQ = P^T M : (r x cols)
+  // SQ = P^T M : (r x cols), on the tensor cores by the Ozaki scheme when it is large
+  // enough to pay for the splitting (as the environment updates), else FP64 SIMT
+  if (tc_available() && 2.0 * r * (double)cols * rows >= kF64eEnvMinFlops) {
+    const long long ld = pad8(rows), pA = round64((long long)r * ld), pB = round64((long long)cols * ld);
+    c->cb.ensure(sizeof(__nv_bfloat16) * (size_t)(kOzSlices * (pA + pB)), s);
+    __nv_bfloat16* Ap = c->cb.as<__nv_bfloat16>();
+    __nv_bfloat16* Bp = Ap + kOzSlices * pA;
+    ozaki_split(P, 1, r, r, rows, Ap, ld, pA, s);          // rows k, K = j: P[j][k]
+    ozaki_split(M, 1, cols, cols, rows, Bp, ld, pB, s);    // rows c, K = j: M[j][c]
+    tc_gemm_f64emu(Ap, ld, pA, Bp, ld, pB, r, cols, rows, SQ, cols, c->tf, s);
+  } else {
     SimtGemm<double, double> g;
     g.M = r; g.N = cols; g.K = rows;
     g.A = P; g.sam = 1; g.sak = r;

@@ -151,21 +151,34 @@ hh_lq_kernel(double* A, int rows, int cols, int k, double* V, double* tau, doubl
       const double* vi = V + (size_t)i * cols;
       for (int c = i + threadIdx.x; c < cols; c += blockDim.x) vs[c] = __ldcg(vi + c);
       __syncthreads();
-      // rows r > i owned by this block (r = b + nb * m), one warp per row: a lane keeps
-      // its columns, so the dot product needs only the warp's shuffles
-      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-      int r = i + 1 + ((b - (i + 1) % nb) % nb + nb) % nb + nb * warp;
-      for (; r < rows; r += nb * nw) {
-        double* ar = A + (size_t)r * cols;
-        double d0 = 0.0, d1 = 0.0;
-        for (int c = i + lane; c < cols; c += 64) {
-          d0 = fma(ar[c], vs[c], d0);
-          if (c + 32 < cols) d1 = fma(ar[c + 32], vs[c + 32], d1);
+      // rows r > i owned by this block (r = b + nb * m): one warp per row (a lane keeps
+      // its columns, the dot product needs only the warp's shuffles) when the block owns
+      // at least four of them, else the whole block on each row (the FP64 work of a row
+      // spread over the four sub-partitions)
+      const int r0 = i + 1 + ((b - (i + 1) % nb) % nb + nb) % nb;
+      const int nown = r0 < rows ? (rows - 1 - r0) / nb + 1 : 0;
+      if (nown >= 4) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int r = r0 + nb * warp; r < rows; r += nb * nw) {
+          double* ar = A + (size_t)r * cols;
+          double d0 = 0.0, d1 = 0.0;
+          for (int c = i + lane; c < cols; c += 64) {
+            d0 = fma(ar[c], vs[c], d0);
+            if (c + 32 < cols) d1 = fma(ar[c + 32], vs[c + 32], d1);
+          }
+          double d = d0 + d1;
+          for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+          d *= t;
+          for (int c = i + lane; c < cols; c += 32) ar[c] = fma(-d, vs[c], ar[c]);
         }
-        double d = d0 + d1;
-        for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-        d *= t;
-        for (int c = i + lane; c < cols; c += 32) ar[c] = fma(-d, vs[c], ar[c]);
+      } else {
+        for (int r = r0; r < rows; r += nb) {
+          double* ar = A + (size_t)r * cols;
+          double d = 0.0;
+          for (int c = i + threadIdx.x; c < cols; c += blockDim.x) d = fma(ar[c], vs[c], d);
+          d = block_sum(d, red) * t;
+          for (int c = i + threadIdx.x; c < cols; c += blockDim.x) ar[c] = fma(-d, vs[c], ar[c]);
+        }
       }
       __syncthreads();
     }
@@ -174,32 +187,29 @@ hh_lq_kernel(double* A, int rows, int cols, int k, double* V, double* tau, doubl
   }
 }
 
-// Row j of Q = e_j^T H_j H_{j-1} ... H_0, one warp per row, formed in place in Q (a lane
-// keeps its columns, so each reflection needs only the warp's shuffles).
+// Row j of Q = e_j^T H_j H_{j-1} ... H_0 (in shared memory), one block per row.
 __global__ void __launch_bounds__(kFacThreads)
 hh_form_q_kernel(const double* V, const double* tau, int cols, int k, double* Q) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int j = blockIdx.x * nw + warp; j < k; j += gridDim.x * nw) {
-    double* q = Q + (size_t)j * cols;
+  extern __shared__ double q[];
+  __shared__ double red[32];
+  for (int j = blockIdx.x; j < k; j += gridDim.x) {
     const double tj = tau[j];
     const double* vj = V + (size_t)j * cols;
-    for (int c = lane; c < cols; c += 32) q[c] = (c == j ? 1.0 : 0.0) - tj * vj[c];
+    for (int c = threadIdx.x; c < cols; c += blockDim.x)
+      q[c] = (c == j ? 1.0 : 0.0) - tj * vj[c];
+    __syncthreads();
     for (int i = j - 1; i >= 0; --i) {
       const double ti = tau[i];
       if (ti == 0.0) continue;
       const double* vi = V + (size_t)i * cols;
-      const int cb = i & ~31;
-      double d0 = 0.0, d1 = 0.0;
-      for (int c = cb + lane; c < cols; c += 64) {
-        if (c >= i) d0 = fma(q[c], __ldg(vi + c), d0);
-        if (c + 32 < cols) d1 = fma(q[c + 32], __ldg(vi + c + 32), d1);
-      }
-      double d = d0 + d1;
-      for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-      d *= ti;
-      for (int c = cb + lane; c < cols; c += 32)
-        if (c >= i) q[c] = fma(-d, __ldg(vi + c), q[c]);
+      double d = 0.0;
+      for (int c = i + threadIdx.x; c < cols; c += blockDim.x) d += q[c] * vi[c];
+      d = block_sum(d, red) * ti;
+      for (int c = i + threadIdx.x; c < cols; c += blockDim.x) q[c] -= d * vi[c];
+      __syncthreads();
     }
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) Q[(size_t)j * cols + c] = q[c];
+    __syncthreads();
   }
 }
 
@@ -558,7 +568,8 @@ hh_bidiag_smem_kernel(double* A, int m, int n, double* d, double* e, double* tau
 // T scaled by a power of two to entries <= 1 (nt2[j] = -t_j^2, nt2[0] unused).  Each step
 // is one multiply and one fused multiply-add (no division on the dependent chain); signs,
 // zero tests and exponents are read from the bits.  The pair (p_{j-1}, p_j) is rescaled by
-// a power of two (exact) whenever its larger entry leaves [2^-E, 2^E].  With the fused
+// a power of two through the exponent fields whenever its larger entry leaves
+// [2^-E, 2^E] (exact; an entry pushed below the normal range becomes zero).  With the fused
 // multiply-add the computed signs are those of the exact minors of T + F, F a diagonal of
 // size <= eps |x| and a relative change <= eps of each t_j^2 (the rounding factors of the
 // steps cancel from the signs), as for the pivot recurrence.  A ratio p_j / p_{j-1} below
@@ -577,35 +588,61 @@ __device__ __forceinline__ bool sign_change(float a, float b) {
   const int ba = __float_as_int(a);
   return ((ba ^ __float_as_int(b)) < 0) & ((ba << 1) != 0);
 }
-__device__ __forceinline__ double pow2_scale(int emax, double) {   // 2^(1023 - emax)
-  return __longlong_as_double((long long)(2046 - emax) << 52);
+// v * 2^s by the exponent field (no floating-point instruction: on this part an FP64
+// instruction, even a predicated-off one, costs a slot of the narrow FP64 pipe); a result
+// below the normal range (or a zero / subnormal v) becomes a signed zero.
+__device__ __forceinline__ double scale_exp(double v, int s) {
+  const long long b = __double_as_longlong(v);
+  const int ev = (int)((b >> 52) & 0x7ff), en = ev + s;
+  return __longlong_as_double((ev == 0 || en <= 0) ? (b & (long long)0x8000000000000000ull)
+                                                   : b + ((long long)s << 52));
 }
-__device__ __forceinline__ float pow2_scale(int emax, float) {     // 2^(127 - emax)
-  return __int_as_float((254 - emax) << 23);
+__device__ __forceinline__ double flip_sign(double v) {
+  return __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
 }
-template <typename R>
-__device__ int tgk_count(const R* nt2, int N, R xs) {
+template <typename R, int K>
+__device__ void tgk_count(const R* nt2, int N, const R (&xs)[K], int (&cnt)[K]) {
   constexpr int bias = sizeof(R) == 8 ? 1023 : 127;
   constexpr int E = sizeof(R) == 8 ? 256 : 32;
   constexpr int G = sizeof(R) == 8 ? 300 : 40;
-  const R guard = sizeof(R) == 8 ? (R)0x1p-300 : (R)0x1p-40;
-  const R nxs = -xs;
-  R pm = 1, p = nxs;
-  int cnt = xs > 0;
-  for (int j = 1; j < N; ++j) {
-    if (expo(p) + G < expo(pm)) p = -pm * guard;
-    R pn = fma(nt2[j], pm, nxs * p);
-    cnt += sign_change(pn, p);
-    const int emax = max(expo(pn), expo(p));
-    if (emax > bias + E || emax < bias - E) {
-      const R sc = pow2_scale(emax, R());
-      pn *= sc;
-      p *= sc;
-    }
-    pm = p;
-    p = pn;
+  R nxs[K], pm[K], p[K];
+#pragma unroll
+  for (int u = 0; u < K; ++u) {   // K independent counts interleaved (their chains overlap)
+    nxs[u] = -xs[u];
+    pm[u] = 1;
+    p[u] = nxs[u];
+    cnt[u] = xs[u] > 0;
   }
-  return cnt;
+  for (int j = 1; j < N; ++j) {
+    const R t = nt2[j];
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+      // guard: p / pm below 2^-G in magnitude counts as -2^-G, i.e. p = -pm 2^-G; the
+      // larger entry of the pair is kept near 1.  FP64: by the exponent fields (integer
+      // instructions); FP32: by multiplications (the FP32 pipe is wide, integer work is
+      // what the FP32 count is bound by)
+      if constexpr (sizeof(R) == 8) {
+        if (expo(p[u]) + G < expo(pm[u])) p[u] = flip_sign(scale_exp(pm[u], -G));
+      } else {
+        if (expo(p[u]) + G < expo(pm[u])) p[u] = -pm[u] * 0x1p-40f;
+      }
+      R pn = fma(t, pm[u], nxs[u] * p[u]);
+      cnt[u] += sign_change(pn, p[u]);
+      const int emax = max(expo(pn), expo(p[u]));
+      if (emax > bias + E || emax < bias - E) {
+        if constexpr (sizeof(R) == 8) {
+          pn = scale_exp(pn, bias - emax);
+          p[u] = scale_exp(p[u], bias - emax);
+        } else {
+          const float sc = __int_as_float((254 - emax) << 23);   // 2^(127 - emax)
+          pn *= sc;
+          p[u] *= sc;
+        }
+      }
+      pm[u] = p[u];
+      p[u] = pn;
+    }
+  }
 }
 
 // Scale of the Golub-Kahan tridiagonal: 2^ex > max_j |t_j| + |t_{j+1}| (every warp forms
@@ -625,27 +662,38 @@ __device__ int tgk_scale_exponent(const double* d, const double* e, int n) {
   return bound > 0.0 ? ex : 0x7fffffff;   // a zero matrix is flagged
 }
 
-// Multisection step shared by both phases: L lanes per value k evaluate the count at L
-// interior points of [lo, hi] and keep the sub-interval holding the eigenvalue of
-// ascending index j (the count crosses j there).
-template <int L, typename R>
+// Multisection step shared by both phases: L lanes per value k evaluate the count at
+// K points each, L K interior points of [lo, hi] in all, and keep the sub-interval holding
+// the eigenvalue of ascending index j (the count crosses j there).
+template <int L, int K, typename R>
 __device__ void multisect(const R* nt2, int N, int j, bool done, double& lo, double& hi) {
-  const int lane = threadIdx.x & 31, sub = lane & (L - 1);
+  const int lane = threadIdx.x & 31, sub = lane & (L - 1), base = lane & (32 - L);
   const unsigned mask = L == 32 ? 0xffffffffu : ((1u << L) - 1u);
-  const double x = lo + (hi - lo) * (double)(sub + 1) / (double)(L + 1);
-  const int c = done ? 0 : tgk_count<R>(nt2, N, (R)x);
-  const unsigned bits = (__ballot_sync(0xffffffffu, c > j) >> (lane & (32 - L))) & mask;
+  constexpr int P = L * K;
+  R xs[K];
+  int c[K];
+#pragma unroll
+  for (int u = 0; u < K; ++u)
+    xs[u] = (R)(lo + (hi - lo) * (double)(sub * K + u + 1) / (double)(P + 1));
+  if (!done) tgk_count<R, K>(nt2, N, xs, c);
+  unsigned mine = 0;
+#pragma unroll
+  for (int u = 0; u < K; ++u)
+    if (!done && c[u] > j) mine |= 1u << u;
+  const unsigned any = (__ballot_sync(0xffffffffu, mine != 0) >> base) & mask;
+  const int fl = any ? __ffs(any) - 1 : 0;
+  const unsigned fb = __shfl_sync(0xffffffffu, mine, base + fl);
   if (!done) {
-    const int first = bits ? __ffs(bits) - 1 : L;   // first point above the eigenvalue
-    const double nlo = first == 0 ? lo : lo + (hi - lo) * (double)first / (double)(L + 1);
-    const double nhi = first == L ? hi : lo + (hi - lo) * (double)(first + 1) / (double)(L + 1);
+    const int first = any ? fl * K + __ffs(fb) - 1 : P;   // first point above the eigenvalue
+    const double nlo = first == 0 ? lo : lo + (hi - lo) * (double)first / (double)(P + 1);
+    const double nhi = first == P ? hi : lo + (hi - lo) * (double)(first + 1) / (double)(P + 1);
     lo = nlo;
     hi = nhi;
   }
 }
 
 // Phase 1, FP32: brackets [lo_k, hi_k] (scaled by 2^-ex) of the nev largest singular values,
-// descending, to a relative width 2^-20, by L-lane multisection of the FP32 count.  Four
+// descending, to a relative width 2^-20, by multisection of the FP32 count.  Four
 // warps per block (one per sub-partition), 32 / L values per warp; -t^2 in shared memory.
 template <int L>
 __global__ void __launch_bounds__(128)
@@ -666,7 +714,7 @@ tgk_bisect32_kernel(const double* d, const double* e, int n, int nev, double* bl
   for (int pass = 0; pass < 48; ++pass) {
     if (!done && (hi - lo <= 0x1p-20 * hi || hi < 0x1p-120)) done = true;
     if (__all_sync(0xffffffffu, done)) break;
-    multisect<L, float>(nt2f, N, j, done, lo, hi);
+    multisect<L, 1, float>(nt2f, N, j, done, lo, hi);
   }
   if (k < nev && (threadIdx.x & (L - 1)) == 0) {
     blo[k] = lo;
@@ -674,7 +722,7 @@ tgk_bisect32_kernel(const double* d, const double* e, int n, int nev, double* bl
   }
 }
 
-// Phase 2, FP64: sigma_k to a relative width 2^-46.  The FP32 bracket is first widened and
+// Phase 2, FP64: sigma_k to a relative width 2^-40.  The FP32 bracket is first widened and
 // checked with FP64 counts: half of the lanes test lower ends lo (1 - w_c), the other half
 // upper ends hi (1 + w_c), w_c from 2^-24 up to ~2^-9 (beyond the worst-case relative error
 // of the FP32 phase), and the tightest ends that hold are kept (0 or the bound when none
@@ -701,9 +749,10 @@ tgk_refine64_kernel(const double* d, const double* e, int n, int nev, const doub
     const double l0 = done ? 0.0 : blo[k], h0 = done ? 0.0 : bhi[k];
     const int c = sub < H ? sub : sub - H;
     const double w = ldexp(1.0, -24 + step * c);
-    const double x = sub < H ? l0 * (1.0 - w) : fmin(h0 * (1.0 + w), 1.0);
-    const int cnt = done ? 0 : tgk_count<double>(nt2, N, x);
-    const bool ok = sub < H ? cnt <= j : cnt > j;
+    const double x[1] = {sub < H ? l0 * (1.0 - w) : fmin(h0 * (1.0 + w), 1.0)};
+    int cnt[1] = {0};
+    if (!done) tgk_count<double, 1>(nt2, N, x, cnt);
+    const bool ok = sub < H ? cnt[0] <= j : cnt[0] > j;
     const unsigned grp = (__ballot_sync(0xffffffffu, ok) >> (lane & (32 - L))) &
                          (L == 32 ? 0xffffffffu : ((1u << L) - 1u));
     const unsigned lo_ok = grp & ((1u << H) - 1u), hi_ok = grp >> H;
@@ -713,9 +762,9 @@ tgk_refine64_kernel(const double* d, const double* e, int n, int nev, const doub
     }
   }
   for (int pass = 0; pass < 64; ++pass) {
-    if (!done && (hi - lo <= 0x1p-46 * hi || hi < 0x1p-600)) done = true;
+    if (!done && (hi - lo <= 0x1p-40 * hi || hi < 0x1p-600)) done = true;
     if (__all_sync(0xffffffffu, done)) break;
-    multisect<L, double>(nt2, N, j, done, lo, hi);
+    multisect<L, 2, double>(nt2, N, j, done, lo, hi);
   }
   if (k < nev && sub == 0) sigma[k] = zero ? 0.0 : ldexp(0.5 * (lo + hi), ex);
 }
@@ -1194,6 +1243,7 @@ void set_attributes() {
   static std::once_flag attr;
   std::call_once(attr, [] {
     set_smem((const void*)hh_lq_kernel, 200 * 1024);
+    set_smem((const void*)hh_form_q_kernel, 200 * 1024);
     set_smem((const void*)bidiag_apply_kernel, 200 * 1024);
     set_smem((const void*)tgk_bisect32_kernel<32>, 200 * 1024);
     set_smem((const void*)tgk_refine64_kernel<8>, 200 * 1024);
@@ -1265,13 +1315,13 @@ int svd_trunc(const double* M, int rows, int cols, int D_max, double tol, double
         d, e, n, nev, blo, bhi);
     A2_CHECK_LAUNCH();
     // lanes per value L of the FP64 phase: fewest passes (one to check the bracket, then
-    // ~27 bits / log2(L + 1)) times the warps that share a sub-partition's FP64 pipe
+    // ~21 bits / log2(2 L + 1)) times the warps that share a sub-partition's FP64 pipe
     const size_t sm2 = sizeof(double) * 2 * (size_t)n;
     int best = 8;
     double best_cost = 1e300;
     for (int L : {8, 16, 32}) {
       const double share = std::ceil((double)cdiv(nev * L, 32) / (4.0 * num_sms()));
-      const double cost = (1.0 + std::ceil(27.0 / std::log2(L + 1.0))) * std::max(1.0, share);
+      const double cost = (1.0 + std::ceil(21.0 / std::log2(2.0 * L + 1.0))) * std::max(1.0, share);
       if (cost <= best_cost) { best_cost = cost; best = L; }
     }
     const int grid = cdiv(nev * best, 128);
@@ -1409,8 +1459,7 @@ int hh_lq(const double* M, int rows, int cols, double* L, double* Q, FactorWork&
   A2_CUDA(cudaLaunchCooperativeKernel((const void*)hh_lq_kernel, dim3(grid), dim3(kFacThreads),
                                       args, vbytes, s));
   count_launch();
-  hh_form_q_kernel<<<std::max(1, std::min(cdiv(k, kFacThreads / 32), 4 * num_sms())), kFacThreads,
-                     0, s>>>(V, tau, cols, k, Q);
+  hh_form_q_kernel<<<std::min(k, 4 * num_sms()), kFacThreads, vbytes, s>>>(V, tau, cols, k, Q);
   A2_CHECK_LAUNCH();
   {
     const long long n = (long long)rows * k;
