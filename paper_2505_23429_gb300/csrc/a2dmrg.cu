@@ -44,6 +44,10 @@ struct a2_ctx {
   double* h_scal = nullptr;     // pinned host mirror
   DevBuf t1, t2, t3, xa, ya, cb, ck, gram, wv, tmp1, tmp2, tf;   // scratch
   std::vector<a2_ctx*> lanes;   // per-group contexts (own stream, scratch, solver)
+  const a2_ctx* parent = nullptr;   // group lanes: the context they belong to
+  // the FP64 products of the sweep's folds, overlaps and SVD splits may run on the
+  // tensor cores by the Ozaki scheme (set while a mixed or FP64-emulated sweep runs)
+  bool gemm_tc = false;
   std::mutex lane_mu;
   // group lanes only: a high-priority stream for the latency-bound factorisations, so
   // that their many small kernels are not queued behind the other groups' matvecs
@@ -234,6 +238,7 @@ a2_ctx* lane(a2_ctx* c, int i) {
   while ((int)c->lanes.size() <= i) {
     auto* l = new a2_ctx();
     l->device = c->device;
+    l->parent = c;
     A2_CUDA(cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking));
     l->own_stream = true;
     int least = 0, greatest = 0;
@@ -1467,6 +1472,9 @@ LanczosResult davidson(a2_ctx* c, MV&& mv, const double* diag, double* x, long l
 // singular vectors (left-orthonormal, this library's bidiagonalisation SVD, factor.cu),
 // SQ = P^T M.  Returns the rank r and the discarded 2-norm.  P (rows x r) and SQ
 // (r x cols) row-major.
+void gemm_f64(a2_ctx* c, int M, int N, int K, const double* A, long long sam, long long sak,
+              const double* B, long long sbn, long long sbk, double* C, long long ldc);
+
 int svd_split_dev(a2_ctx* c, const double* M, int rows, int cols, int D_max, double tol,
                   double* P, double* SQ, double* discarded, std::vector<double>* sv_out = nullptr) {
   cudaStream_t s = c->stream;
@@ -1478,35 +1486,47 @@ int svd_split_dev(a2_ctx* c, const double* M, int rows, int cols, int D_max, dou
                    2.0 * nn * (double)rows * cols,
                8.0 * (2.0 * rows * cols + 2.0 * rows * nn));
   const int r = svd_trunc(M, rows, cols, D_max, tol, P, discarded, sv_out, c->solver.fw, s);
-  // SQ = P^T M : (r x cols), on the tensor cores by the Ozaki scheme when it is large
-  // enough to pay for the splitting (as the environment updates), else FP64 SIMT
-  if (tc_available() && 2.0 * r * (double)cols * rows >= kF64eEnvMinFlops) {
-    const long long ld = pad8(rows), pA = round64((long long)r * ld), pB = round64((long long)cols * ld);
-    c->cb.ensure(sizeof(__nv_bfloat16) * (size_t)(kOzSlices * (pA + pB)), s);
-    __nv_bfloat16* Ap = c->cb.as<__nv_bfloat16>();
-    __nv_bfloat16* Bp = Ap + kOzSlices * pA;
-    ozaki_split(P, 1, r, r, rows, Ap, ld, pA, s);          // rows k, K = j: P[j][k]
-    ozaki_split(M, 1, cols, cols, rows, Bp, ld, pB, s);    // rows c, K = j: M[j][c]
-    tc_gemm_f64emu(Ap, ld, pA, Bp, ld, pB, r, cols, rows, SQ, cols, c->tf, s);
-  } else {
-    SimtGemm<double, double> g;
-    g.M = r; g.N = cols; g.K = rows;
-    g.A = P; g.sam = 1; g.sak = r;
-    g.B = M; g.sbn = 1; g.sbk = cols;
-    g.C = SQ; g.scm = cols; g.scn = 1;
-    simt_gemm(g, s);
-  }
+  // SQ = P^T M : (r x cols)
+  gemm_f64(c, r, cols, rows, P, 1, r, M, 1, cols, SQ, cols);
   return r;
 }
 
 // C = A (ra x k) * B (k x cb), all row-major FP64
-void matmul_dev(a2_ctx* c, const double* A, int ra, int k, const double* B, int cb, double* C) {
+// C[m][n] (row stride ldc) = sum_k A(m, k) B(n, k) in FP64, A(m, k) at A[m sam + k sak],
+// B(n, k) at B[n sbn + k sbk]: on the tensor cores by the Ozaki scheme (FP64-class) when
+// the context allows it (a mixed or FP64-emulated sweep) and the product is large enough
+// to pay for the slicing, else on the FP64 SIMT kernel.
+struct GemmTcScope {   // allows the Ozaki path for the lifetime of the scope
+  a2_ctx* c;
+  bool saved;
+  GemmTcScope(a2_ctx* ctx, bool on) : c(ctx), saved(ctx->gemm_tc) { c->gemm_tc = on; }
+  ~GemmTcScope() { c->gemm_tc = saved; }
+};
+constexpr double kF64eGemmMinFlops = 5e7;
+void gemm_f64(a2_ctx* c, int M, int N, int K, const double* A, long long sam, long long sak,
+              const double* B, long long sbn, long long sbk, double* C, long long ldc) {
+  cudaStream_t s = c->stream;
+  const bool tc_ok = (c->parent ? c->parent->gemm_tc : c->gemm_tc) && tc_available();
+  if (tc_ok && M >= 16 && N >= 16 && K >= 16 && 2.0 * M * (double)N * K >= kF64eGemmMinFlops) {
+    const long long ld = pad8(K), pA = round64((long long)M * ld), pB = round64((long long)N * ld);
+    c->cb.ensure(sizeof(__nv_bfloat16) * (size_t)(kOzSlices * (pA + pB)), s);
+    __nv_bfloat16* Ap = c->cb.as<__nv_bfloat16>();
+    __nv_bfloat16* Bp = Ap + kOzSlices * pA;
+    ozaki_split(A, sam, sak, M, K, Ap, ld, pA, s);
+    ozaki_split(B, sbn, sbk, N, K, Bp, ld, pB, s);
+    tc_gemm_f64emu(Ap, ld, pA, Bp, ld, pB, M, N, K, C, ldc, c->tf, s);
+    return;
+  }
   SimtGemm<double, double> g;
-  g.M = ra; g.N = cb; g.K = k;
-  g.A = A; g.sam = k; g.sak = 1;
-  g.B = B; g.sbn = 1; g.sbk = cb;
-  g.C = C; g.scm = cb; g.scn = 1;
-  simt_gemm(g, c->stream);
+  g.M = M; g.N = N; g.K = K;
+  g.A = A; g.sam = sam; g.sak = sak;
+  g.B = B; g.sbn = sbn; g.sbk = sbk;
+  g.C = C; g.scm = ldc; g.scn = 1;
+  simt_gemm(g, s);
+}
+
+void matmul_dev(a2_ctx* c, const double* A, int ra, int k, const double* B, int cb, double* C) {
+  gemm_f64(c, ra, cb, k, A, k, 1, B, 1, cb, C, cb);
 }
 
 // ============================================================================= TT helpers
@@ -2040,12 +2060,8 @@ struct Sweeper {
       Tm.ensure(sizeof(double) * (size_t)bl * n * kr, s);
       matmul_dev(c, E.as<double>(), bl, kl, ket.core[j], n * kr, Tm.as<double>());  // [a][(s b')]
       En.ensure(sizeof(double) * (size_t)br * kr, s);
-      SimtGemm<double, double> g;   // En[b][b'] = sum_{(a s)} bra[(a s)][b] Tm[(a s)][b']
-      g.M = br; g.N = kr; g.K = bl * n;
-      g.A = bra.core[j]; g.sam = 1; g.sak = br;
-      g.B = Tm.as<double>(); g.sbn = 1; g.sbk = kr;
-      g.C = En.as<double>(); g.scm = kr; g.scn = 1;
-      simt_gemm(g, s);
+      // En[b][b'] = sum_{(a s)} bra[(a s)][b] Tm[(a s)][b']
+      gemm_f64(c, br, kr, bl * n, bra.core[j], 1, br, Tm.as<double>(), 1, kr, En.as<double>(), kr);
       std::swap(E, En);
     }
     const int Df = bra.Dr[hi];
@@ -2964,6 +2980,7 @@ static a2_status run_sweep(a2_ctx* c, a2_tt* t, const a2_mpo* m, const a2_sweep_
       // FP64 environments; the tensor-core modes keep them to FP64-class accuracy
       if (o->prec != A2_FP64 && !tc_available())
         throw ArgError("this precision needs the tcgen05 path, which this build lacks");
+      GemmTcScope gs(c, o->prec != A2_FP64);
       Sweeper<double> sw(c, t, m, *o);
       sw.run(rep, classical);
     } else if (o->prec == A2_FP32) {
@@ -3023,7 +3040,10 @@ a2_status a2_energy(a2_ctx* c, const a2_tt* t, const a2_mpo* m, a2_precision pre
     tt_check(t);
     A2_REQUIRE(t->phys == m->phys, "TT and MPO physical dims differ");
     if (prec == A2_FP64) *E = energy_T<double>(c, t, m, norm_out);
-    else if (prec == A2_F64EMU) *E = energy_T<double>(c, t, m, norm_out, A2_F64EMU);
+    else if (prec == A2_F64EMU) {
+      GemmTcScope gs(c, true);
+      *E = energy_T<double>(c, t, m, norm_out, A2_F64EMU);
+    }
     else *E = energy_T<float>(c, t, m, norm_out);
   });
 }
