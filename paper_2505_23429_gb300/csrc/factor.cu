@@ -5,9 +5,11 @@
 // part of row i onto a multiple of e_i and is applied from the right to the rows below.
 // One cooperative persistent kernel walks the k reflections; every block owns the rows
 // r with r % gridDim.x == blockIdx.x, so a row is only ever touched by one block, and the
-// block that owns row i + 1 forms the next reflection as soon as it has updated that row.
-// A grid-wide barrier (bounded: after kBarrierLimit polls it raises the error word and
-// every block leaves) separates the reflections.  Q is then formed row by row: row j of
+// block that owns row i + 1 forms and publishes the next reflection as soon as it has
+// updated that row.  The blocks synchronise on those publications alone (one flag per
+// reflection, bounded waits: after kBarrierLimit polls a wait raises the error word and
+// every block leaves), so they pipeline behind the owners instead of meeting at a
+// grid-wide barrier per reflection.  Q is then formed row by row: row j of
 // Q is e_j^T H_j H_{j-1} ... H_0 (the reflections H_i with i > j leave e_j unchanged),
 // so every row is independent.
 #include <algorithm>
@@ -114,14 +116,23 @@ __device__ void make_reflection(double* A, int cols, int i, double* V, double* t
   double s2 = 0.0;
   for (int c = i + 1 + threadIdx.x; c < cols; c += blockDim.x) s2 += x[c] * x[c];
   s2 = block_sum(s2, red);
-  const double alpha = x[i];
-  double t = 0.0, b = alpha, scale = 0.0;
-  if (s2 > 0.0) {
-    const double nrm = sqrt(alpha * alpha + s2);
-    b = alpha >= 0.0 ? -nrm : nrm;
-    t = (b - alpha) / b;
-    scale = 1.0 / (alpha - b);
+  // the scalars in one thread, broadcast through shared memory (an FP64 instruction holds
+  // a sub-partition's FP64 pipe for many cycles on this part)
+  if (threadIdx.x == 0) {
+    const double alpha = x[i];
+    double t = 0.0, b = alpha, scale = 0.0;
+    if (s2 > 0.0) {
+      const double nrm = sqrt(fma(alpha, alpha, s2));
+      b = alpha >= 0.0 ? -nrm : nrm;
+      t = (b - alpha) / b;
+      scale = 1.0 / (alpha - b);
+    }
+    red[1] = t;
+    red[2] = b;
+    red[3] = scale;
   }
+  __syncthreads();
+  const double t = red[1], b = red[2], scale = red[3];
   for (int c = threadIdx.x; c < cols; c += blockDim.x) {
     const double xc = x[c];
     v[c] = c < i ? 0.0 : (c == i ? 1.0 : xc * scale);
@@ -136,26 +147,87 @@ __device__ void make_reflection(double* A, int cols, int i, double* V, double* t
   __syncthreads();
 }
 
+// Point-to-point publication of reflection j: every thread's writes of it are ordered
+// before the flag (the block's barrier, then thread 0 fences and sets ready[j]).
+__device__ void publish_ready(int* ready, int j) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicExch(ready + j, 1);
+  }
+}
+// Bounded wait of the block for ready[j] (thread 0 polls, then fences); false if it gave
+// up after kBarrierLimit polls (raising the error word) or another block did.
+__device__ bool wait_ready(const int* ready, int j, GridBarrier* b) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    ok = 1;
+    for (unsigned int it = 0;; ++it) {
+      if (*(volatile const int*)(ready + j)) break;
+      if (*(volatile int*)&b->abort) { ok = 0; break; }
+      if (it >= kBarrierLimit) {
+        atomicExch(&g_factor_error, 1);
+        atomicExch(&b->abort, 1);
+        ok = 0;
+        break;
+      }
+      if (it > 64) __nanosleep(32);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Applies reflection i (vector in vs, factor t) to row r of A, the whole block on the row.
+__device__ void lq_update_row_block(double* A, int cols, int i, int r, const double* vs,
+                                    double t, double* red) {
+  double* ar = A + (size_t)r * cols;
+  double d = 0.0;
+  for (int c = i + threadIdx.x; c < cols; c += blockDim.x) d = fma(ar[c], vs[c], d);
+  d = block_sum(d, red) * t;
+  for (int c = i + threadIdx.x; c < cols; c += blockDim.x) ar[c] = fma(-d, vs[c], ar[c]);
+  __syncthreads();
+}
+
+// The reflections need no grid-wide barrier: a row only ever changes in the block that
+// owns it, so the one dependency between blocks is reflection i itself, which its row's
+// owner publishes (ready[i]) as soon as that row has received reflections 0..i-1.  The
+// owner of row i + 1 therefore applies reflection i to that row first, forms and
+// publishes reflection i + 1, and only then updates its other rows, while the other
+// blocks run behind it.  ready (k ints) must be zero on entry.
 __global__ void __launch_bounds__(kFacThreads)
 hh_lq_kernel(double* A, int rows, int cols, int k, double* V, double* tau, double* beta,
-             GridBarrier* bar) {
-  unsigned epoch = 0;
+             GridBarrier* bar, int* ready) {
   extern __shared__ double vs[];                 // the current reflection vector
   __shared__ double red[32];
   const int nb = gridDim.x, b = blockIdx.x;
-  if (b == 0) make_reflection(A, cols, 0, V, tau, beta, red);
-  if (!grid_sync(bar, epoch)) return;
+  if (b == 0) {
+    make_reflection(A, cols, 0, V, tau, beta, red);
+    publish_ready(ready, 0);
+  }
   for (int i = 0; i < k; ++i) {
+    if (!wait_ready(ready, i, bar)) return;
     const double t = __ldcg(tau + i);
+    const int nxt = i + 1;
+    const bool own_next = nxt < k && nxt % nb == b;
     if (t != 0.0) {
       const double* vi = V + (size_t)i * cols;
       for (int c = i + threadIdx.x; c < cols; c += blockDim.x) vs[c] = __ldcg(vi + c);
       __syncthreads();
-      // rows r > i owned by this block (r = b + nb * m): one warp per row (a lane keeps
-      // its columns, the dot product needs only the warp's shuffles) when the block owns
-      // at least four of them, else the whole block on each row (the FP64 work of a row
-      // spread over the four sub-partitions)
-      const int r0 = i + 1 + ((b - (i + 1) % nb) % nb + nb) % nb;
+      if (own_next) lq_update_row_block(A, cols, i, nxt, vs, t, red);
+    }
+    if (own_next) {
+      make_reflection(A, cols, nxt, V, tau, beta, red);
+      publish_ready(ready, nxt);
+    }
+    if (t != 0.0) {
+      // the other rows r > i owned by this block (r = b + nb * m): one warp per row (a
+      // lane keeps its columns, the dot product needs only the warp's shuffles) when the
+      // block owns at least four of them, else the whole block on each row (the FP64
+      // work of a row spread over the four sub-partitions)
+      int r0 = i + 1 + ((b - (i + 1) % nb) % nb + nb) % nb;
+      if (own_next) r0 += nb;                      // row i + 1 is done
       const int nown = r0 < rows ? (rows - 1 - r0) / nb + 1 : 0;
       if (nown >= 4) {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -172,18 +244,10 @@ hh_lq_kernel(double* A, int rows, int cols, int k, double* V, double* tau, doubl
           for (int c = i + lane; c < cols; c += 32) ar[c] = fma(-d, vs[c], ar[c]);
         }
       } else {
-        for (int r = r0; r < rows; r += nb) {
-          double* ar = A + (size_t)r * cols;
-          double d = 0.0;
-          for (int c = i + threadIdx.x; c < cols; c += blockDim.x) d = fma(ar[c], vs[c], d);
-          d = block_sum(d, red) * t;
-          for (int c = i + threadIdx.x; c < cols; c += blockDim.x) ar[c] = fma(-d, vs[c], ar[c]);
-        }
+        for (int r = r0; r < rows; r += nb) lq_update_row_block(A, cols, i, r, vs, t, red);
       }
-      __syncthreads();
     }
-    if (i + 1 < k && (i + 1) % nb == b) make_reflection(A, cols, i + 1, V, tau, beta, red);
-    if (!grid_sync(bar, epoch)) return;
+    __syncthreads();   // vs is reloaded for the next reflection
   }
 }
 
@@ -1440,22 +1504,23 @@ int hh_lq(const double* M, int rows, int cols, double* L, double* Q, FactorWork&
   ProfScope ps(PK_LQ, s, 4.0 * (double)rows * rows * cols, 8.0 * 3.0 * rows * (double)cols);
   w.a.ensure(sizeof(double) * (size_t)rows * cols, s);
   w.v.ensure(sizeof(double) * ((size_t)k * cols + 2 * (size_t)k), s);
-  w.bar.ensure(sizeof(GridBarrier), s);
+  w.bar.ensure(sizeof(GridBarrier) + sizeof(int) * (size_t)k, s);
   double* A = w.a.as<double>();
   double* V = w.v.as<double>();
   double* tau = V + (size_t)k * cols;
   double* beta = tau + k;
   A2_CUDA(cudaMemcpyAsync(A, M, sizeof(double) * (size_t)rows * cols, cudaMemcpyDeviceToDevice, s));
-  A2_CUDA(cudaMemsetAsync(w.bar.p, 0, sizeof(GridBarrier), s));
+  A2_CUDA(cudaMemsetAsync(w.bar.p, 0, sizeof(GridBarrier) + sizeof(int) * (size_t)k, s));
   set_attributes();
-  // cooperative launch: every block resident at once (the grid barrier relies on it)
+  // cooperative launch: every block resident at once (the ready flags rely on it)
   int per_sm = 0;
   A2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hh_lq_kernel, kFacThreads,
                                                         vbytes));
   A2_REQUIRE(per_sm >= 1, "LQ: kernel does not fit on an SM");
   const int grid = std::max(1, std::min({rows, num_sms() * per_sm, num_sms()}));
   GridBarrier* bar = w.bar.as<GridBarrier>();
-  void* args[] = {&A, &rows, &cols, const_cast<int*>(&k), &V, &tau, &beta, &bar};
+  int* ready = reinterpret_cast<int*>(bar + 1);
+  void* args[] = {&A, &rows, &cols, const_cast<int*>(&k), &V, &tau, &beta, &bar, &ready};
   A2_CUDA(cudaLaunchCooperativeKernel((const void*)hh_lq_kernel, dim3(grid), dim3(kFacThreads),
                                       args, vbytes, s));
   count_launch();
