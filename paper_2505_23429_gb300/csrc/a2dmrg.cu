@@ -2077,10 +2077,28 @@ struct Sweeper {
 
   // <bra, A ket> over sites lo..hi, closed by the iterate's envs HL[lo] and HR[hi+1]
   double sandwich_span(const View& bra, const View& ket, int lo, int hi) {
+    DevBuf Hb;
+    return sandwich_from(hl_at(lo, eng, Hb), lo, bra, ket, hi);
+  }
+  // Mixed left environment E of (bra, ket) at site p (sites before p contracted) advanced
+  // to site q: the left updates of sites p..q-1 (E is replaced).
+  void advance_left(DevBuf& E, int p, int q, const View& bra, const View& ket) {
     cudaStream_t s = c->stream;
-    DevBuf E, En, Hb;
-    const T* Ecur = hl_at(lo, eng, Hb);
-    for (int j = lo; j <= hi; ++j) {
+    DevBuf En;
+    for (int j = p; j < q; ++j) {
+      En.ensure(sizeof(T) * (size_t)bra.Dr[j] * mpo->R[j + 1] * ket.Dr[j], s);
+      eng.left_update(E.template as<T>(), j, bra.core[j], bra.Dl[j], bra.Dr[j], ket.core[j],
+                      ket.Dl[j], ket.Dr[j], En.template as<T>());
+      std::swap(E, En);
+    }
+  }
+  // <bra, A ket> from the mixed left environment E0 at site p (not modified) over sites
+  // p..hi, closed by the iterate's HR[hi+1]
+  double sandwich_from(const T* E0, int p, const View& bra, const View& ket, int hi) {
+    cudaStream_t s = c->stream;
+    DevBuf E, En;
+    const T* Ecur = E0;
+    for (int j = p; j <= hi; ++j) {
       En.ensure(sizeof(T) * (size_t)bra.Dr[j] * mpo->R[j + 1] * ket.Dr[j], s);
       eng.left_update(Ecur, j, bra.core[j], bra.Dl[j], bra.Dr[j], ket.core[j], ket.Dl[j],
                       ket.Dr[j], En.template as<T>());
@@ -2251,10 +2269,26 @@ struct Sweeper {
       A[(size_t)(a + 1)] = A[(size_t)(a + 1) * m] = sandwich_span(b, gv[a], lo, hi);
       S[(size_t)(a + 1) * m + a + 1] = overlap_span(gv[a], gv[a], lo, hi);
       A[(size_t)(a + 1) * m + a + 1] = sandwich_span(gv[a], gv[a], lo, hi);
+      // cross entries with the later items: left of item b2's first site its TT is the
+      // iterate's left-orthogonal cores, so the mixed left environment of (gv[a], iterate)
+      // from lo up to that site is shared by all b2 and advanced once
+      DevBuf Pre;
+      int pre_at = lo;
+      {
+        DevBuf Hb;
+        const T* h0 = hl_at(lo, eng, Hb);
+        const size_t nb0 = sizeof(T) * (size_t)gv[a].Dl[lo] * mpo->R[lo] * gv[a].Dl[lo];
+        Pre.ensure(nb0, c->stream);
+        A2_CUDA(cudaMemcpyAsync(Pre.p, h0, nb0, cudaMemcpyDeviceToDevice, c->stream));
+      }
       for (int b2 = a + 1; b2 + 1 < m; ++b2) {
-        const int hi2 = groups[items[b2].g].mg + 1;
+        const int lo2 = groups[items[b2].g].kg, hi2 = groups[items[b2].g].mg + 1;
         const double sv = overlap_span(gv[a], gv[b2], lo, hi2);
-        const double av = sandwich_span(gv[a], gv[b2], lo, hi2);
+        if (lo2 > pre_at) {
+          advance_left(Pre, pre_at, lo2, gv[a], gv[b2]);
+          pre_at = lo2;
+        }
+        const double av = sandwich_from(Pre.template as<T>(), pre_at, gv[a], gv[b2], hi2);
         S[(size_t)(a + 1) * m + b2 + 1] = S[(size_t)(b2 + 1) * m + a + 1] = sv;
         A[(size_t)(a + 1) * m + b2 + 1] = A[(size_t)(b2 + 1) * m + a + 1] = av;
       }
