@@ -361,6 +361,28 @@ __device__ __forceinline__ void store_vec(TO* p, const A (&x)[NV]) {
   }
 }
 
+// U consecutive nonzeros e .. e + U - 1 of one row: their index loads, then their row
+// loads, are issued together; the FMAs into acc keep the nonzero order.
+template <int U, typename TI, typename V, typename Acc, int NV>
+__device__ __forceinline__ void nz_batch(const SparseRows<V>& sp, const SparseGeom& g,
+                                         const TI* __restrict__ in, long long ib, int e,
+                                         Acc (&acc)[NV]) {
+  long long ci[U];
+  Acc w[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    ci[u] = __ldg(sp.nz_w + e + u) * g.in_sw + __ldg(sp.nz_t + e + u) * g.in_st;
+    w[u] = (Acc)__ldg(sp.nz_val + e + u);
+  }
+  Acc x[U][NV];
+#pragma unroll
+  for (int u = 0; u < U; ++u) load_vec<TI, Acc>(in + ib + ci[u], x[u]);
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = fma(w[u], x[u][i], acc[i]);
+}
+
 template <typename TI, typename TO, typename V, bool ACC>
 __global__ void __launch_bounds__(256)
 sparse_rows_vec_kernel(SparseRows<V> sp, SparseGeom g, const TI* __restrict__ in,
@@ -386,23 +408,9 @@ sparse_rows_vec_kernel(SparseRows<V> sp, SparseGeom g, const TI* __restrict__ in
     const int e1 = __ldg(sp.row_ptr + r + 1);
     int e = __ldg(sp.row_ptr + r);
     // four nonzeros at a time: their index loads, then their row loads, are issued
-    // together (more loads in flight); the FMAs keep the nonzero order
-    for (; e + 4 <= e1; e += 4) {
-      long long ci[4];
-      Acc w[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        ci[u] = __ldg(sp.nz_w + e + u) * g.in_sw + __ldg(sp.nz_t + e + u) * g.in_st;
-        w[u] = (Acc)__ldg(sp.nz_val + e + u);
-      }
-      Acc x[4][NV];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) load_vec<TI, Acc>(in + ib + ci[u], x[u]);
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int i = 0; i < NV; ++i) acc[i] = fma(w[u], x[u][i], acc[i]);
-    }
+    // together (more loads in flight; eight at a time cost more in occupancy than they
+    // gained); the FMAs keep the nonzero order
+    for (; e + 4 <= e1; e += 4) nz_batch<4, TI, V, Acc, NV>(sp, g, in, ib, e, acc);
     for (; e < e1; ++e) {
       const long long ci = __ldg(sp.nz_w + e) * g.in_sw + __ldg(sp.nz_t + e) * g.in_st;
       const Acc w = (Acc)__ldg(sp.nz_val + e);
@@ -459,22 +467,7 @@ sparse_rows_split3_kernel(SparseRows<V> sp, SparseGeom g, const TI* __restrict__
     const int e1 = __ldg(sp.row_ptr + r + 1);
     int e = __ldg(sp.row_ptr + r);
     if constexpr (!PLANES) {   // four nonzeros at a time, as in sparse_rows_vec_kernel
-      for (; e + 4 <= e1; e += 4) {
-        long long ci[4];
-        Acc w[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          ci[u] = __ldg(sp.nz_w + e + u) * g.in_sw + __ldg(sp.nz_t + e + u) * g.in_st;
-          w[u] = (Acc)__ldg(sp.nz_val + e + u);
-        }
-        Acc x[4][NV];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) load_vec<TI, Acc>(in + ib + ci[u], x[u]);
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int i = 0; i < NV; ++i) acc[i] = fma(w[u], x[u][i], acc[i]);
-      }
+      for (; e + 4 <= e1; e += 4) nz_batch<4, TI, V, Acc, NV>(sp, g, in, ib, e, acc);
     }
     for (; e < e1; ++e) {
       const long long ci = __ldg(sp.nz_w + e) * g.in_sw + __ldg(sp.nz_t + e) * g.in_st;
