@@ -455,8 +455,10 @@ hh_bidiag_kernel(double* A, int m, int n, double* d, double* e, double* tau_u,
 // Step i then runs in every block without further exchange: the left reflection
 // (beta, tau_u, scale) from the norm and the pivot, y = u^T A = row_i + scale Z_i (u_i = 1,
 // u_r = scale A[r][i]), the left update of its rows, the right reflection from row i after
-// the left update (row_i - tau_u y), the right update of its rows (one warp per row), and
-// the publications for step i + 1.  The scalar work of a reflection runs in one warp and
+// the left update (x = row_i - tau_u y, formed by one warp while the others update the
+// rows; each row's left update also accumulates its dot product with x, so the right
+// update is one more pass over the row), the right update of its rows (one warp per row),
+// and the publications for step i + 1.  The scalar work of a reflection runs in one warp and
 // is broadcast through shared memory: an FP64 instruction holds a sub-partition's FP64
 // pipe for many cycles on this part, so the other warps must not repeat it.  At the end
 // the rows, holding the reflection vectors in place, are written back to A for the
@@ -492,7 +494,8 @@ hh_bidiag_smem_kernel(double* A, int m, int n, double* d, double* e, double* tau
   const int R = (m - b + nb - 1) / nb;          // rows of this block
   double* rows = sm;                            // R x n
   double* yv = sm + (size_t)R * n;              // y of the current step (n)
-  double* wv = yv + n;                          // row i, then w of the right reflection (n)
+  double* wv = yv + n;                          // row i after the left update, x (n)
+  double* zr = wv + n;                          // x . row_r beyond the superdiagonal (R)
   for (int q = 0; q < R; ++q)
     for (int c = tid; c < n; c += blockDim.x) rows[(size_t)q * n + c] = A[(size_t)(b + nb * q) * n + c];
   __syncthreads();
@@ -566,7 +569,11 @@ hh_bidiag_smem_kernel(double* A, int m, int n, double* d, double* e, double* tau
       wv[c] = fma(-tu, yc, wv[c]);
     }
     __syncthreads();
-    // warp 0 forms the right reflection from row i while the block applies the left update
+    // warp 0 forms the right reflection from x = row i after the left update (in wv)
+    // while warps 1.. apply the left update to the block's rows, one warp per row; a row
+    // r > i also accumulates its dot product with x beyond the superdiagonal, z_r, so that
+    // the right update needs no second pass over it: with w = (1, sv x_{i+2:}),
+    // w . row_r = row_r[i+1] + sv z_r
     if (warp == 0) {
       double t2 = 0.0;
       for (int c = i + 2 + lane; c < n; c += 32) t2 = fma(wv[c], wv[c], t2);
@@ -581,34 +588,50 @@ hh_bidiag_smem_kernel(double* A, int m, int n, double* d, double* e, double* tau
           tau_v[i] = tv;
         }
       }
-    }
-    if (tu != 0.0)
-      for (int q = q0; q < R; ++q) {
-        const double f = tu * ((own_i && q == q0) ? 1.0 : rows[(size_t)q * n + i]);
-        double* rq = rows + (size_t)q * n;
-        for (int c = i + 1 + tid; c < n; c += blockDim.x) rq[c] = fma(-f, yv[c], rq[c]);
-      }
-    __syncthreads();
-    const double tv = sc[2], sv = sc[3];
-    for (int c = i + 2 + tid; c < n; c += blockDim.x) wv[c] *= sv;
-    if (tid == 0) wv[i + 1] = 1.0;
-    __syncthreads();
-    if (own_i)   // w_i is stored in row i right of the superdiagonal
-      for (int c = i + 2 + tid; c < n; c += blockDim.x) rows[(size_t)q0 * n + c] = wv[c];
-    // right update of the own rows r > i with w = (1, w[i+2:]): one warp per row, so the
-    // dot product needs only the warp's shuffles (each lane keeps its columns)
-    if (tv != 0.0) {
+    } else {
       const int cb = (i + 1) & ~31;
-      for (int q = q1 + warp; q < R; q += nw) {
+      for (int q = q0 + warp - 1; q < R; q += nw - 1) {
+        const bool row_i = own_i && q == q0;
+        const double f = tu * (row_i ? 1.0 : rows[(size_t)q * n + i]);
         double* rq = rows + (size_t)q * n;
         double z0 = 0.0, z1 = 0.0;
         for (int c = cb + lane; c < n; c += 64) {
-          if (c > i) z0 = fma(rq[c], wv[c], z0);
-          if (c + 32 < n) z1 = fma(rq[c + 32], wv[c + 32], z1);
+          if (c > i) {
+            const double v = tu != 0.0 ? fma(-f, yv[c], rq[c]) : rq[c];
+            rq[c] = v;
+            if (c > i + 1) z0 = fma(v, wv[c], z0);
+          }
+          if (c + 32 < n) {
+            const double v = tu != 0.0 ? fma(-f, yv[c + 32], rq[c + 32]) : rq[c + 32];
+            rq[c + 32] = v;
+            if (c + 32 > i + 1) z1 = fma(v, wv[c + 32], z1);
+          }
         }
-        const double f = tv * warp_sum(z0 + z1);
-        for (int c = cb + lane; c < n; c += 32)
-          if (c > i) rq[c] = fma(-f, wv[c], rq[c]);
+        const double z = warp_sum(z0 + z1);
+        if (lane == 0) zr[q] = z;
+      }
+    }
+    __syncthreads();
+    const double tv = sc[2], sv = sc[3];
+    // right update of the own rows r > i: row_r -= tv (w . row_r) w, each warp on the rows
+    // whose dot product it formed; the owner of row i stores w_i right of the superdiagonal
+    if (warp > 0) {
+      const int cb = (i + 1) & ~31;
+      for (int q = q0 + warp - 1; q < R; q += nw - 1) {
+        double* rq = rows + (size_t)q * n;
+        if (own_i && q == q0) {
+          for (int c = cb + lane; c < n; c += 32)
+            if (c > i + 1) rq[c] = sv * wv[c];
+          continue;
+        }
+        if (tv == 0.0) continue;
+        const double f = tv * fma(sv, zr[q], rq[i + 1]);
+        const double fs = f * sv;
+        __syncwarp();   // every lane has read rq[i + 1] before its owner changes it
+        for (int c = cb + lane; c < n; c += 32) {
+          if (c == i + 1) rq[c] -= f;
+          else if (c > i + 1) rq[c] = fma(-fs, wv[c], rq[c]);
+        }
       }
     }
     __syncthreads();
@@ -1355,7 +1378,7 @@ int svd_trunc(const double* M, int rows, int cols, int D_max, double tol, double
   {
     GridBarrier* bar = w.bar.as<GridBarrier>();
     int mm = m, nn = n;
-    const size_t smem = sizeof(double) * ((size_t)cdiv(m, nb) + 2) * n;
+    const size_t smem = sizeof(double) * (((size_t)cdiv(m, nb) + 2) * n + cdiv(m, nb));
     if (smem <= 200 * 1024) {   // every block's rows resident in shared memory
       A2_CUDA(cudaMemsetAsync(zbuf, 0, sizeof(double) * 3 * (size_t)n, s));
       void* args[] = {&A, &mm, &nn, &d, &e, &tu, &tv, &part, &zbuf, &alpha, &rowg, &bar};
