@@ -339,9 +339,10 @@ a2_status a2_svd_split(a2_ctx* ctx, int Dl, int n1, int n2, int Dr, const double
 /* LQ factorisation of Alg. 2 step 1 (W_i = L_i Q_i, and of the TT rounding) alone:
  * M (device, rows x cols row-major, not modified) = L Q with Q (device, k x cols,
  * k = min(rows, cols)) orthonormal rows and L (device, rows x k) lower trapezoidal with
- * diag(L) >= 0; Householder reflections in FP64 on the device (this library's kernel).
- * Synchronous.  Errors: A2_EINVAL on bad sizes / NULLs (rows of more than 25600 entries),
- * A2_ECUDA if the kernel's bounded grid barrier gave up. */
+ * diag(L) >= 0; Householder reflections in FP64 on the device (this library's kernel:
+ * the owner of row i + 1 publishes reflection i + 1 on a ready flag that the other blocks
+ * wait for).  Synchronous.  Errors: A2_EINVAL on bad sizes / NULLs (rows of more than
+ * 25600 entries), A2_ECUDA if a bounded wait of the kernel gave up. */
 a2_status a2_lq(a2_ctx* ctx, int rows, int cols, const double* M, double* L, double* Q);
 
 /* Stages S1 and S4 of the H_eff chain alone: the tcgen05 tensor-core GEMM
@@ -353,7 +354,8 @@ a2_status a2_gemm_bf16(a2_ctx* ctx, int M, int N, int K, const void* A, long lon
                        const void* B, long long ldb, float* C, long long ldc, int splitk);
 
 /* Device-side error code of the bounded waits (0 = none): the tensor-core kernels' mbarrier
- * waits (codes 1-16), or 101 when a factorisation kernel's grid barrier gave up; reset != 0
+ * waits (codes 1-16), or 101 when a bounded wait of a factorisation kernel (grid barrier
+ * or ready flag) gave up; reset != 0
  * clears it.  Synchronizes the context stream. */
 a2_status a2_device_error(a2_ctx* ctx, int reset, int* code_out);
 

@@ -2335,7 +2335,7 @@ struct Sweeper {
       round_into_tt(X, xd);
     }
     // round_into_tt ended with a stream synchronisation: the error word is current
-    if (factor_error_flag(true)) throw CudaError("a factorisation kernel's grid barrier gave up");
+    if (factor_error_flag(true)) throw CudaError("a factorisation kernel's bounded wait gave up");
     if (rep) {
       rep->energy_in = A[0] / S[0];
       rep->lambda_coarse = lam;
@@ -3364,7 +3364,7 @@ a2_status a2_lq(a2_ctx* c, int rows, int cols, const double* M, double* L, doubl
     A2_REQUIRE(rows >= 1 && cols >= 1 && M && L && Q, "a2_lq: bad arguments");
     c->solver.lq(M, rows, cols, L, Q, c->stream);
     A2_CUDA(cudaStreamSynchronize(c->stream));
-    if (factor_error_flag(true)) throw CudaError("a2_lq: a bounded grid barrier gave up");
+    if (factor_error_flag(true)) throw CudaError("a2_lq: a bounded wait of the LQ kernel gave up");
   });
 }
 
