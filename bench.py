@@ -53,9 +53,13 @@ REF_COUNTS = dict(iterations=64,
                   env=167, svd=30)
 # classes reported by time share only (latency-bound FP64 factorisations)
 LATENCY_BOUND = ("svd", "lq")
-# DRAM traffic / algorithmic bytes of a kernel class, from its ncu capture at D = 128;
+# DRAM traffic / algorithmic bytes of a kernel class, from its ncu capture (the sparse
+# stages at D = 128, one FP64-class environment update at D = 256: all its launches);
 # the bench scales it to its own launches
-DRAM_TRAFFIC_RATIO = {"emu_s2": 0.963, "emu_s3": 0.961}
+DRAM_TRAFFIC_RATIO = {"emu_s2": 0.963, "emu_s3": 0.961, "env": 3.78}
+DRAM_TRAFFIC_CAPTURE = {"emu_s2": "profiles/sparse_rows_kernel_heff_D128.md",
+                        "emu_s3": "profiles/sparse_rows_kernel_heff_D128.md",
+                        "env": "profiles/env_update_f64e_D256.md"}
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 FP64_PEAK_TFLOPS = 1.2   # FP64 (SIMT) rate measured on this part with a DGEMM loop
 
@@ -94,6 +98,10 @@ def parse():
     p.add_argument("--profile-svd", action="store_true",
                    help="time the truncated SVD alone: the (D n) x (n D) two-site matrix of "
                         "the workload's middle bond, singular values k^-0.75, --reps calls")
+    p.add_argument("--profile-env", action="store_true",
+                   help="time the FP64-class (Ozaki-emulated) left environment update alone at "
+                        "site --bond (default: left of the middle) with bond dimension --D, "
+                        "--reps calls")
     p.add_argument("--D", type=int, default=128, help="bond dimension of --profile-matvec")
     p.add_argument("--bond", type=int, default=None,
                    help="bond of --profile-matvec (default: the one left of the middle)")
@@ -331,6 +339,42 @@ def profile_svd(args):
                           error_flag=a2.device_error(ctx))))
 
 
+def profile_env(args):
+    """The left environment update of the FP64-class mixed path alone (a2_env_update with
+    Ozaki-emulated GEMMs and the double-float sparse stage): random FP64 environment, bra
+    and ket of bond dimension --D at one site of the workload's MPO, --reps calls after a
+    warm-up call, CUDA events on the library's stream."""
+    import torch
+    import paper_2505_23429_gb300 as a2
+    cfg, cores, _ = workload(args.config)
+    j = cfg["L"] // 2 - 3 if args.bond is None else args.bond
+    D, n = args.D, cfg["n"]
+    stream = torch.cuda.Stream()
+    ctx = a2.Context(0, stream.cuda_stream)
+    mpo = a2.MPO(ctx, cores)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    Hin = torch.randn(D, cores[j].shape[0], D, device="cuda", dtype=torch.float64, generator=g)
+    bra = torch.randn(D, n, D, device="cuda", dtype=torch.float64, generator=g) / D ** 0.5
+    ket = torch.randn(D, n, D, device="cuda", dtype=torch.float64, generator=g) / D ** 0.5
+    out = torch.empty(D, cores[j].shape[3], D, device="cuda", dtype=torch.float64)
+    torch.cuda.synchronize()
+    a2.env_update(ctx, mpo, j, 0, Hin, bra, ket, out, prec="f64emu")
+    ctx.synchronize()
+    times = []
+    for _ in range(args.reps):
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        a2.env_update(ctx, mpo, j, 0, Hin, bra, ket, out, prec="f64emu")
+        t1.record(stream)
+        t1.synchronize()
+        times.append(t0.elapsed_time(t1))
+    R_l, R_r = cores[j].shape[0], cores[j].shape[3]
+    alg_bytes = 8.0 * (D * R_l * D + D * R_r * D + 2.0 * D * R_l * n * D + 2.0 * D * n * R_r * D)
+    print(json.dumps(dict(profile_env=True, site=j, D=D, R=[R_l, R_r], alg_bytes=alg_bytes,
+                          ms=[round(t, 3) for t in times], ms_min=round(min(times), 3),
+                          error_flag=a2.device_error(ctx))))
+
+
 def class_roofline(name, d, peaks, prec):
     """(bound, unit, peak, achieved) of one kernel class from its CUDA-event totals and
     the algorithmic flops / bytes the library counts for it."""
@@ -499,6 +543,9 @@ def main():
     if args.profile_svd:
         profile_svd(args)
         return
+    if args.profile_env:
+        profile_env(args)
+        return
     if args.profile_matvec:
         profile_matvec(args)
         return
@@ -619,8 +666,9 @@ def main():
                               frac=achieved / peak, traffic=traffic,
                               traffic_source=(None if ratio is None else
                                               "ncu DRAM bytes / algorithmic bytes of the same "
-                                              "kernel at D=128, scaled to this launch's "
-                                              "algorithmic bytes"),
+                                              "class in a smaller capture ("
+                                              + DRAM_TRAFFIC_CAPTURE[dom] + "), scaled to "
+                                              "this launch's algorithmic bytes"),
                               per_launch_ms=per_launch, launches=d["launches"],
                               peak_source=peaks["src"]),
                 time_shares=shares,
