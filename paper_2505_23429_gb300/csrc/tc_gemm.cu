@@ -1573,39 +1573,64 @@ __device__ __forceinline__ float pow2f(int k) {
   return (k >= -126 && k <= 127) ? __int_as_float((k + 127) << 23) : 0.f;
 }
 
-__global__ void ozaki_split_kernel(const double* __restrict__ X, long long sr, long long sk,
-                                   int rows, int K, __nv_bfloat16* __restrict__ P, long long ldp,
-                                   long long plane) {
-  __shared__ int red[32];
-  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+// One warp per row: the row's largest exponent by a warp reduction (no block barrier),
+// then the slices of four consecutive entries per lane, each plane written as one 8-byte
+// vector per lane (the kernel is bound by its 16 bytes of writes per entry).
+// The 56-bit fixed-point magnitude of v at the row's scale 2^e (|v| < 2^e) and its sign.
+__device__ __forceinline__ unsigned long long oz_fixed(double v, int e, float& sgn) {
+  const long long bits = __double_as_longlong(v);
+  int f = (int)((bits >> 52) & 0x7FF);
+  unsigned long long m = (unsigned long long)bits & ((1ull << 52) - 1);
+  if (f) m |= 1ull << 52;
+  else f = 1;                                    // subnormal: no hidden bit
+  const int sh = f - e - 1019;                   // <= 3 since |v| < 2^e
+  sgn = bits < 0 ? -1.f : 1.f;
+  return sh >= 0 ? (m << sh) : (sh > -64 ? (m >> -sh) : 0ull);
+}
+__global__ void __launch_bounds__(256)
+ozaki_split_kernel(const double* __restrict__ X, long long sr, long long sk, int rows, int K,
+                   __nv_bfloat16* __restrict__ P, long long ldp, long long plane) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); r < rows; r += nwarps) {
     const double* xr = X + (long long)r * sr;
     int fm = 0;
-    for (int k = threadIdx.x; k < K; k += blockDim.x)
+    for (int k = lane; k < K; k += 32)
       fm = max(fm, (int)((__double_as_longlong(xr[(long long)k * sk]) >> 52) & 0x7FF));
     for (int o = 16; o; o >>= 1) fm = max(fm, __shfl_xor_sync(0xffffffffu, fm, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = fm;
-    __syncthreads();
-    int f_max = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) f_max = max(f_max, red[w]);
-    const int e = max(f_max, 1) - 1022;
+    const int e = max(fm, 1) - 1022;
     __nv_bfloat16* pr = P + (long long)r * ldp;
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-      const long long bits = __double_as_longlong(xr[(long long)k * sk]);
-      int f = (int)((bits >> 52) & 0x7FF);
-      unsigned long long m = (unsigned long long)bits & ((1ull << 52) - 1);
-      if (f) m |= 1ull << 52;
-      else f = 1;                                    // subnormal: no hidden bit
-      const int sh = f - e - 1019;                   // <= 3 since |v| < 2^e
-      const unsigned long long N = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> -sh) : 0ull);
-      const float sgn = bits < 0 ? -1.f : 1.f;
+    for (int k0 = 4 * lane; k0 < K; k0 += 128) {
+      unsigned long long N[4];
+      float sgn[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        sgn[u] = 1.f;
+        N[u] = k0 + u < K ? oz_fixed(xr[(long long)(k0 + u) * sk], e, sgn[u]) : 0ull;
+      }
 #pragma unroll
       for (int i = 1; i <= kOzSlices; ++i) {
-        const int q = (int)((N >> (56 - kOzBits * i)) & ((1u << kOzBits) - 1));
-        pr[(long long)(i - 1) * plane + k] =
-            __float2bfloat16_rn(sgn * (float)q * pow2f(e - kOzBits * i));   // exact
+        const float sc = pow2f(e - kOzBits * i);
+        float w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = (int)((N[u] >> (56 - kOzBits * i)) & ((1u << kOzBits) - 1));
+          w[u] = sgn[u] * (float)q * sc;   // exact in BF16
+        }
+        __nv_bfloat16* dst = pr + (long long)(i - 1) * plane + k0;
+        if (k0 + 4 <= K) {   // ldp % 8 == 0, plane % 64 == 0, k0 % 4 == 0: 8-byte aligned
+          const __nv_bfloat162 lo = __floats2bfloat162_rn(w[0], w[1]);
+          const __nv_bfloat162 hi = __floats2bfloat162_rn(w[2], w[3]);
+          uint2 pk;
+          pk.x = *reinterpret_cast<const unsigned int*>(&lo);
+          pk.y = *reinterpret_cast<const unsigned int*>(&hi);
+          *reinterpret_cast<uint2*>(dst) = pk;
+        } else {
+          for (int u = 0; u < 4; ++u)
+            if (k0 + u < K) dst[u] = __float2bfloat16_rn(w[u]);
+        }
       }
     }
-    __syncthreads();   // red is reused by the next row
   }
 }
 
@@ -1646,7 +1671,7 @@ __global__ void ozaki_combine_kernel(const float* __restrict__ T, long long MN, 
 void ozaki_split(const double* X, long long sr, long long sk, int rows, int K, __nv_bfloat16* P,
                  long long ldp, long long plane, cudaStream_t s) {
   if (rows <= 0 || K <= 0) return;
-  const int grid = std::min(rows, 152 * 8);
+  const int grid = std::min((rows + 7) / 8, 152 * 8);   // eight rows (warps) per block
   ozaki_split_kernel<<<grid, 256, 0, s>>>(X, sr, sk, rows, K, P, ldp, plane);
   A2_CHECK_LAUNCH();
 }
