@@ -537,7 +537,6 @@ void env_left_f64e(a2_ctx* c, const SiteOps& so, const double* Hin, const double
   c->t3.ensure(sizeof(__nv_bfloat16) * (size_t)(kOzSlices * pT), s);
   float* T1 = c->tmp1.as<float>();
   double* T2 = c->tmp2.as<double>();
-  double* T2t = c->tmp1.as<double>();   // after E2 has consumed T1
   __nv_bfloat16* T2p = c->t3.as<__nv_bfloat16>();
   ozaki_split(Hin, Dlk, 1, (int)M1, Dlk, Hp, ldH, pH, s);            // rows (a w), K = a'
   ozaki_split(ket, 1, N1, (int)N1, Dlk, Kp, ldK, pK, s);             // rows (t b'), K = a'
@@ -553,8 +552,7 @@ void env_left_f64e(a2_ctx* c, const SiteOps& so, const double* Hin, const double
   }
   // E3: Hout[b][(w' b')] = sum_{(a s)} bra[(a s)][b] T2[(a s)][(w' b')]
   ozaki_split(bra, 1, Drb, Drb, (int)K3, Bp, ldB, pB, s);            // rows b, K = (a s)
-  transpose2d<double, double>(T2, T2t, (int)K3, (int)N3, s);         // [(w' b')][(a s)]
-  ozaki_split(T2t, K3, 1, (int)N3, (int)K3, T2p, ldB, pT, s);
+  ozaki_split_cols(T2, N3, (int)N3, (int)K3, T2p, ldB, pT, s);      // rows (w' b'), K = (a s)
   tc_gemm_f64emu(Bp, ldB, pB, T2p, ldB, pT, Drb, (int)N3, (int)K3, Hout, N3, c->tf, s);
 }
 
@@ -583,7 +581,6 @@ void env_right_f64e(a2_ctx* c, const SiteOps& so, const double* Hin, const doubl
   c->t3.ensure(sizeof(__nv_bfloat16) * (size_t)(kOzSlices * pT), s);
   float* T1 = c->tmp1.as<float>();
   double* T2 = c->tmp2.as<double>();
-  double* T2t = c->tmp1.as<double>();
   __nv_bfloat16* T2p = c->t3.as<__nv_bfloat16>();
   permute_swap01<double, double>(ket, Vt, n, Dlk, Drk, s);            // Vt[t][a'][b']
   ozaki_split(Hin, Drk, 1, (int)M1, Drk, Hp, ldH, pH, s);             // rows (b w'), K = b'
@@ -600,8 +597,7 @@ void env_right_f64e(a2_ctx* c, const SiteOps& so, const double* Hin, const doubl
   }
   // F3: Hout[a][(w a')] = sum_{(s b)} bra[a][(s b)] T2[(s b)][(w a')]
   ozaki_split(bra, K3, 1, Dlb, (int)K3, Bp, ldB, pB, s);             // rows a, K = (s b)
-  transpose2d<double, double>(T2, T2t, (int)K3, (int)N3, s);         // [(w a')][(s b)]
-  ozaki_split(T2t, K3, 1, (int)N3, (int)K3, T2p, ldB, pT, s);
+  ozaki_split_cols(T2, N3, (int)N3, (int)K3, T2p, ldB, pT, s);      // rows (w a'), K = (s b)
   tc_gemm_f64emu(Bp, ldB, pB, T2p, ldB, pT, Dlb, (int)N3, (int)K3, Hout, N3, c->tf, s);
 }
 

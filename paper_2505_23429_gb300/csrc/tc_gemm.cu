@@ -1634,6 +1634,59 @@ ozaki_split_kernel(const double* __restrict__ X, long long sr, long long sk, int
   }
 }
 
+// Slices of the rows of X^T, X a (K x N) row-major matrix (row stride ldx): output row n
+// holds X[k][n], k < K.  A block takes 32 consecutive output rows: the exponent pass and
+// the slicing read X row by row (coalesced across the 32 columns), the slices of a
+// 64-wide K chunk are staged in shared memory and leave as 8-byte vectors along K.  Same
+// slices as ozaki_split of the transposed matrix.
+constexpr int kOzColChunk = 64, kOzColPad = kOzColChunk + 4;   // row of 68 BF16 = 136 B
+__global__ void __launch_bounds__(256)
+ozaki_split_cols_kernel(const double* __restrict__ X, long long ldx, int N, int K,
+                        __nv_bfloat16* __restrict__ P, long long ldp, long long plane) {
+  __shared__ int emax[8][32];
+  __shared__ __align__(16) __nv_bfloat16 tile[kOzSlices][32][kOzColPad];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n0 = blockIdx.x * 32, n = n0 + lane;
+  int fm = 0;
+  if (n < N)
+    for (int k = warp; k < K; k += 8)
+      fm = max(fm, (int)((__double_as_longlong(X[(long long)k * ldx + n]) >> 52) & 0x7FF));
+  emax[warp][lane] = fm;
+  __syncthreads();
+  fm = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) fm = max(fm, emax[w][lane]);
+  const int e = max(fm, 1) - 1022;
+  for (int k0 = 0; k0 < K; k0 += kOzColChunk) {
+#pragma unroll
+    for (int t = 0; t < kOzColChunk / 8; ++t) {
+      const int kk = warp + 8 * t, k = k0 + kk;
+      float sgn = 1.f;
+      const unsigned long long Nq =
+          (n < N && k < K) ? oz_fixed(X[(long long)k * ldx + n], e, sgn) : 0ull;
+#pragma unroll
+      for (int i = 1; i <= kOzSlices; ++i) {
+        const int q = (int)((Nq >> (56 - kOzBits * i)) & ((1u << kOzBits) - 1));
+        tile[i - 1][lane][kk] = __float2bfloat16_rn(sgn * (float)q * pow2f(e - kOzBits * i));
+      }
+    }
+    __syncthreads();
+    // 8 slices x 32 rows x 16 vectors of 4 values
+    for (int v = threadIdx.x; v < kOzSlices * 32 * (kOzColChunk / 4); v += blockDim.x) {
+      const int i = v / (32 * (kOzColChunk / 4)), r = (v / (kOzColChunk / 4)) % 32;
+      const int c4 = v % (kOzColChunk / 4), k = k0 + 4 * c4;
+      if (n0 + r >= N || k >= K) continue;
+      __nv_bfloat16* dst = P + (long long)i * plane + (long long)(n0 + r) * ldp + k;
+      const __nv_bfloat16* src = &tile[i][r][4 * c4];
+      if (k + 4 <= K)   // ldp % 8 == 0, plane % 64 == 0, k % 4 == 0: 8-byte aligned
+        *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(src);
+      else
+        for (int u = 0; k + u < K; ++u) dst[u] = src[u];
+    }
+    __syncthreads();
+  }
+}
+
 // C[r][c] = sum over the level tiles: tile t of level lev[t] at T + t * MN (row-major,
 // N columns); tiles ordered by level (largest level last).
 // C[r][c] = sum of all level tiles (tile t at T + t * MN, row-major with N columns,
@@ -1667,6 +1720,13 @@ __global__ void ozaki_combine_kernel(const float* __restrict__ T, long long MN, 
 }
 
 }  // namespace
+
+void ozaki_split_cols(const double* X, long long ldx, int N, int K, __nv_bfloat16* P,
+                      long long ldp, long long plane, cudaStream_t s) {
+  if (N <= 0 || K <= 0) return;
+  ozaki_split_cols_kernel<<<(N + 31) / 32, 256, 0, s>>>(X, ldx, N, K, P, ldp, plane);
+  A2_CHECK_LAUNCH();
+}
 
 void ozaki_split(const double* X, long long sr, long long sk, int rows, int K, __nv_bfloat16* P,
                  long long ldp, long long plane, cudaStream_t s) {

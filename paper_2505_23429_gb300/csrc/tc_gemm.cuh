@@ -83,6 +83,10 @@ constexpr int kOzBits = 7;     // bits per slice
 // planes P + i*plane, row r at P + i*plane + r*ldp (ldp % 8 == 0, 16-byte aligned P).
 void ozaki_split(const double* X, long long sr, long long sk, int rows, int K, __nv_bfloat16* P,
                  long long ldp, long long plane, cudaStream_t s);
+// The same slices for the rows of X^T, X a (K x N) row-major FP64 matrix with row stride
+// ldx (output row n holds X[k][n]): no transposed copy of X is needed.
+void ozaki_split_cols(const double* X, long long ldx, int N, int K, __nv_bfloat16* P,
+                      long long ldp, long long plane, cudaStream_t s);
 // C (FP64, M x N, row stride ldc) = sum_k A[m][k] B[n][k] to FP64 accuracy from the split
 // planes of A (row stride lda, plane stride aplane) and B; slab is FP32 scratch for the
 // double-float partial sums of the K splits, when the product is split (grown as
