@@ -55,3 +55,22 @@ def test_roofline_class_mapping():
     assert "svd" in bench.LATENCY_BOUND and "lq" in bench.LATENCY_BOUND
     for k, r in bench.DRAM_TRAFFIC_RATIO.items():
         assert 0.5 < r < 5.0, k
+
+
+def test_profile_modes_and_traffic_sources():
+    """The profiling modes parse, and every class with a DRAM traffic ratio names the
+    committed profile summary it was measured in."""
+    import bench
+    old = sys.argv
+    try:
+        sys.argv = ["bench.py", "--profile-svd", "--reps", "2"]
+        a = bench.parse()
+        assert a.profile_svd and a.reps == 2 and not a.profile_env
+        sys.argv = ["bench.py", "--profile-env", "--D", "256"]
+        a = bench.parse()
+        assert a.profile_env and a.D == 256
+    finally:
+        sys.argv = old
+    for k in bench.DRAM_TRAFFIC_RATIO:
+        src = bench.DRAM_TRAFFIC_CAPTURE[k]
+        assert os.path.isfile(os.path.join(ROOT, src)), src
