@@ -324,7 +324,7 @@ a2_status a2_env_update(a2_ctx* ctx, const a2_mpo* mpo, int j, int side, a2_prec
  * SQ_out [r][n2][Dr] (device, capacity min(Dl n1, n2 Dr) columns/rows);
  * rank_out, discarded_out (host).  Computed by this library's FP64 kernels: Householder
  * bidiagonalisation, all singular values by bisection of the Golub-Kahan tridiagonal
- * (FP32 brackets refined in FP64 to a relative width 2^-46; no Gram matrix, so small
+ * (FP32 brackets refined in FP64 to a relative width 2^-40; no Gram matrix, so small
  * singular values keep their relative accuracy), the kept left vectors by inverse
  * iteration, re-orthonormalised (block Gram-Schmidt with CholeskyQR2 panels) and
  * transformed back; SQ = P^T x.  Within an exactly degenerate multiplet any orthonormal

@@ -22,7 +22,7 @@ int hh_lq(const double* M, int rows, int cols, double* L, double* Q, FactorWork&
 // Truncated SVD step of Alg. 1 (step 2) for a row-major (rows x cols) matrix M, in FP64:
 // Golub-Kahan bidiagonalisation of M (or of M^T when rows < cols) by Householder
 // reflections, all singular values by bisection of the Golub-Kahan tridiagonal (no Gram
-// matrix; FP32 brackets refined in FP64 to a relative width 2^-46, so small singular
+// matrix; FP32 brackets refined in FP64 to a relative width 2^-40, so small singular
 // values keep their relative accuracy), the kept left singular vectors by inverse
 // iteration on the same tridiagonal, re-orthonormalised (block Gram-Schmidt, CholeskyQR2
 // panels) and transformed back.  Keeps the smallest r <= D_max with discarded 2-norm
