@@ -11,7 +11,8 @@ orthogonal decompositions (Def. orthogonal TT), environments (eqs. env_L /
 env_R), the two-site micro-iteration as the lowest eigenpair of the projected
 operator (Lemma DMRG micro-iterations), the truncated SVD step (Alg. 1 step 2),
 the LQ sweep of Alg. 2 step 1, the coarse problem of Sec. 3.1 (eq. A_reduced,
-eq. aux_eig_final_sym) and TT rounding for the compression step.
+eq. aux_eig_final_sym) and TT rounding for the compression step; `blocksparse` adds the
+particle-number preserving variants of Sec. 3.2 (bond charges, block-wise truncation).
 
 Parity status per function is listed in each module's header.
 """
