@@ -5,7 +5,8 @@ sector, the particle numbers stay exact in the truncating regime, and the charge
 (Alg. 1) and A2DMRG (Alg. 2) reach the sector's exact ground energy: exact
 diagonalisation restricted to the sector (Hubbard L = 6, U = 4, half filling) and the
 U = 0 free-fermion closed form E = sum over spins and k <= N_s of -2t cos(k pi / (L+1))
-(open chain)."""
+(open chain); and, loosely, the half-filled chain's bulk energy against the Lieb-Wu
+integral."""
 import numpy as np
 import pytest
 
@@ -150,3 +151,25 @@ def test_charged_a2dmrg_converges_in_sector():
     assert max(c.shape[2] for c in U) <= 6
     assert charge_violation(U, q) == 0.0 and sector_support(U, Nu, Nd) == 0.0
     assert abs(tt_inner(U, U) - 1.0) < 1e-12
+
+
+def test_half_filled_hubbard_bulk_energy_lieb_wu():
+    """Loose bulk check: the energy per site of the half-filled chain at U = 4 from two open
+    chains, (E(12) - E(8)) / 4 (the boundary terms cancel), against the Lieb-Wu integral
+    e = -4 int_0^inf J0(w) J1(w) / (w (1 + exp(w U / 2))) dw (t = 1), within 1 %."""
+    from scipy import integrate, special
+    Uint = 4.0
+
+    def f(w):
+        return special.j0(w) * special.j1(w) / (w * (1.0 + np.exp(min(w * Uint / 2.0, 700.0))))
+
+    e_bulk = -4.0 * integrate.quad(f, 0.0, np.inf, limit=400)[0]
+    E = {}
+    for L in (8, 12):
+        _, _, mpo = _hubbard(L, Uint)
+        U, q = random_charged_tt(L, L // 2, L // 2, 16, 1)
+        _, _, hist = charged_dmrg(U, q, mpo, 64, 1e-10, 1e-9, 8)
+        assert abs(hist[-1] - hist[-2]) < 1e-8        # converged
+        E[L] = hist[-1]
+    e_fin = (E[12] - E[8]) / 4.0
+    assert abs(e_fin - e_bulk) < 0.01 * abs(e_bulk), (e_fin, e_bulk)
